@@ -1,0 +1,220 @@
+/*
+ * propagate.h — C ABI of the GB300 (sm_103a) implementation of PROPAGATE
+ * (Amati, Cruciani, Pasquini, Vocca, Angelini: "PROPAGATE: a seed propagation
+ * framework to compute Distance-based metrics on Very Large Graphs").
+ *
+ * The method (Sec. 4): every node u carries a Boolean signature Sig(u) of s
+ * bits, bit i set iff seed x_i has reached u. One synchronous round computes
+ *     Sig'(v) = Sig(v) OR ( OR over in-neighbours u of v of Sig(u) )
+ * and the popcount of Sig'(v) XOR Sig(v) per seed gives the nodes at distance
+ * exactly t from each seed (the "collisions" of Sec. 4). PROPAGATE-P
+ * (Algorithm 1, Sec. 4.1) moves all s bits per round; PROPAGATE-S
+ * (Algorithm 2, Sec. 4.2) handles one seed per 1-bit plane, pulling only into
+ * unset nodes and stopping a node's scan at the first set in-neighbour. From
+ * the per-round counts follow the neighbourhood function, diameter,
+ * effective diameter, average distance, reachable pairs and connectivity
+ * rate (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - A graph is a CSR over IN-edges: row v lists every u with an arc u -> v
+ *    (the arcs a pull reads). Counts are balls grown forward from each seed
+ *    along arcs. An undirected graph is passed symmetrised.
+ *  - Seed i owns bit (i mod 64) of signature word floor(i / 64).
+ *  - Every call is ordered on the CUDA stream it is given (NULL = the legacy
+ *    default stream) and returns once its host outputs are written.
+ *  - Calls on one pg_graph are serialised by the library; different graphs
+ *    may be used from different host threads concurrently.
+ *  - No entry point aborts the process. Errors are returned as pg_status and
+ *    leave the graph usable; pg_strerror names them.
+ */
+#ifndef PROPAGATE_H
+#define PROPAGATE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PG_OK = 0,
+  PG_EINVAL = -1,      /* bad argument: CSR, seeds, sizes, options */
+  PG_ENOMEM = -2,      /* device or pinned host memory could not be had */
+  PG_ECUDA = -3,       /* a CUDA runtime call failed */
+  PG_ETIMEOUT = -4,    /* a bounded device-side wait expired */
+  PG_EDEVICE = -5,     /* the device reported an inconsistent state */
+  PG_ECANCELLED = -6,  /* the request was cancelled */
+  PG_ERANGE = -7       /* more rounds than the caller's max_rounds */
+} pg_status;
+
+/* Opaque graph handle: device-resident CSR (in-edges and, for directed
+ * graphs, out-edges), cached per-call workspace. Library-owned. */
+typedef struct pg_graph pg_graph;
+
+/* pg_graph_from_csr flags */
+#define PG_DEVICE_PTRS 1u /* row_ptr and col are device pointers */
+#define PG_BORROW 2u      /* with PG_DEVICE_PTRS: use the caller's arrays in
+                             place; they must outlive the graph */
+
+/*
+ * Per-round, per-seed counts. Caller-owned host buffers.
+ *  counts   [ (max_rounds+1) * s ]: counts[t*s + i] = number of nodes at
+ *           distance exactly t from seed i (row 0 is all ones). Rows
+ *           0..rounds are written.
+ *  m_active [ max_rounds + 2 ] (may be NULL): m_active[t] = sum of the
+ *           in-degrees of the nodes that round t had to revisit: nodes with
+ *           a zero bit (skip rule in the proof of Thm. 1) and an in-neighbour
+ *           that changed in round t-1. Entry 0 is 0; entry rounds+1 is the
+ *           final sweep that found no change. For PROPAGATE-S the entry is
+ *           summed over the seed passes.
+ *  rounds   out: T = the last round with a new (seed, node) pair, i.e. the
+ *           diameter lower bound Delta_LB of Algorithm 1.
+ */
+typedef struct {
+  int32_t s;          /* in: number of seeds (columns of counts) */
+  int32_t max_rounds; /* in: capacity, see above; pg_query_rounds_bound */
+  int32_t rounds;     /* out */
+  int32_t reserved;
+  uint32_t *counts;   /* out, host */
+  uint64_t *m_active; /* out, host, optional */
+} pg_counts;
+
+/* Schedule options. Every choice gives bit-identical counts; they change
+ * only how the rounds are executed. Zero-initialise and call
+ * pg_default_options, or pass NULL for defaults. */
+typedef struct {
+  int32_t direction;        /* PG_DIR_AUTO: per round, a frontier-driven
+                               (sparse) sweep when the frontier's out-arcs are
+                               few, a full (dense) sweep otherwise */
+  float dense_threshold;    /* AUTO: dense when frontier out-arcs > this * m
+                               (0 = library default) */
+  int32_t group_lanes;      /* lanes cooperating on one node row, power of two
+                               in [1, 32]; 0 = chosen from the mean degree */
+  int32_t piece_arcs;       /* arcs per work item; longer rows are split into
+                               pieces combined with atomic OR; 0 = auto */
+  int32_t gather_changed_only; /* 1: OR only in-neighbours that changed in the
+                               previous round (same result: unchanged ones
+                               were already ORed in); 0: OR all of them */
+  int32_t planes_per_pass;  /* PROPAGATE-S: seeds per pass, 1..64; 0 = 64 */
+  int32_t use_graphs;       /* 1: launch the round loop as captured CUDA
+                               graphs; 0: plain launches */
+  int32_t timing;           /* 1: record CUDA events around every kernel
+                               launch (plain launches) for pg_last_stats */
+  int32_t window_rows;      /* rows of per-round counters kept on the device
+                               before they are copied out; 0 = auto */
+} pg_options;
+
+#define PG_DIR_AUTO 0
+#define PG_DIR_DENSE 1  /* every round a full sweep over unsaturated nodes */
+#define PG_DIR_SPARSE 2 /* every round only the nodes reached by the frontier */
+
+typedef struct {
+  int32_t diameter;              /* Delta_LB = T (Alg. 1) */
+  int32_t eff_diameter;          /* min k: R[k] >= tau R[T] (Sec. 3, Alg. 1) */
+  double eff_diameter_interp;    /* (k-1) + (tau R[T]-R[k-1])/(R[k]-R[k-1]); 0 if k = 0 */
+  double avg_distance;           /* sum_r r (R[r]-R[r-1]) / (R[T] - s): pairs u != v */
+  double avg_distance_incl_self; /* same numerator / R[T] (Alg. 1's division) */
+  double connectivity_rate;      /* (R[T] - s) / (s (n-1)) (Sec. 3 alpha) */
+  double reachable_pairs;        /* (n/s) R[T] (Alg. 1), self-pairs included */
+  uint64_t R_last;               /* R[T] over the s seeds */
+  uint64_t dist_sum;             /* sum_r r (R[r]-R[r-1]) */
+} pg_metrics_out;
+
+/* Work and timing of the last propagate call on a graph (for benchmarks). */
+typedef struct {
+  int32_t sweeps;            /* rounds executed, the final empty one included */
+  int32_t passes;            /* seed passes (1 for PROPAGATE-P) */
+  int32_t dense_rounds;      /* rounds run as full sweeps */
+  int32_t launches;          /* kernels launched by the call */
+  uint64_t m_active_total;   /* sum over rounds (and passes) of m_active */
+  uint64_t arcs_scanned;     /* column indices read by the pull kernel */
+  uint64_t rows_gathered;    /* neighbour signatures ORed by the pull kernel */
+  uint64_t items;            /* row pieces visited by the pull kernel */
+  uint64_t changed_rows;     /* sum over rounds of rows that changed */
+  uint64_t frontier_arcs;    /* sum over sparse rounds of the frontier's out-arcs */
+  int32_t words_per_row;     /* 64-bit signature words per node (padded) */
+  int32_t group_lanes;
+  double ms_pull;            /* with timing=1: summed event time per kernel */
+  double ms_post;
+  double ms_init;
+  int32_t pull_launches;
+  int32_t post_launches;
+} pg_stats;
+
+/* Message for a status code (static storage). */
+const char *pg_strerror(pg_status st);
+
+/* Library version string. */
+const char *pg_version(void);
+
+/* Fills *opt with the defaults. */
+void pg_default_options(pg_options *opt);
+
+/*
+ * Builds a graph from a CSR over in-edges (Sec. 4 recurrence: row v is the
+ * set of nodes whose ball is unioned into v's).
+ *  row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *  col      int32[m], each in [0, n), strictly increasing within a row
+ *  directed 1: general digraph (the library builds the out-edge transpose);
+ *           0: the caller asserts the CSR is symmetric (in = out)
+ *  flags    PG_DEVICE_PTRS / PG_BORROW; host arrays are copied
+ *  stream   cudaStream_t for the copies and validation kernels
+ * Errors: PG_EINVAL for n < 1, n >= 2^31, m < 0, or a malformed CSR (checked
+ * on the device); PG_ENOMEM; PG_ECUDA.
+ */
+pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t m,
+                            int directed, unsigned flags, void *stream, pg_graph **out);
+
+/* Frees the graph and its cached workspace. NULL is allowed. */
+void pg_graph_free(pg_graph *g);
+
+/* n and m of a graph. */
+pg_status pg_graph_info(const pg_graph *g, int64_t *n, int64_t *m);
+
+/* A safe max_rounds: every eccentricity is at most n - 1. */
+pg_status pg_query_rounds_bound(const pg_graph *g, int32_t *max_rounds);
+
+/*
+ * PROPAGATE-P (Algorithm 1, Sec. 4.1): all s seeds diffuse synchronously, s
+ * bits per node; stops at the first round with no new bit (do ... while
+ * Count > 0). seeds: host int32[s], distinct, in [0, n). out->s must equal s;
+ * out->counts and out->m_active sized by out->max_rounds as documented.
+ * Errors: PG_EINVAL (s < 1, duplicate or out-of-range seeds, bad sizes),
+ * PG_ERANGE (more than max_rounds productive rounds; rows 0..max_rounds are
+ * written and out->rounds = max_rounds + 1), PG_ENOMEM, PG_ECUDA.
+ */
+pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,
+                         const pg_options *opt, void *stream);
+
+/*
+ * PROPAGATE-S (Algorithm 2, Sec. 4.2): seeds are processed in passes of
+ * planes_per_pass independent 1-bit planes (plane k of a node is bit k of its
+ * word); in each round only nodes with an unset plane pull, and a node stops
+ * scanning its in-neighbours as soon as all its planes are set (with one
+ * plane per pass: at the first set in-neighbour, as in Algorithm 2). The
+ * counts are per seed and identical to PROPAGATE-P's (Sec. 5, "both
+ * algorithms produce the same results"). Arguments and errors as
+ * pg_propagate_p; m_active is summed over passes.
+ */
+pg_status pg_propagate_s(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,
+                         const pg_options *opt, void *stream);
+
+/*
+ * Metrics of Sec. 3 and of the last steps of Algorithm 1 from counts
+ * (rows 0..c->rounds), for an n-node graph and threshold tau = tau_num /
+ * tau_den in (0, 1] (the paper uses 9/10). Host-only, FP64 divisions of exact
+ * 64-bit integer sums; tau is applied by integer cross-multiplication.
+ * Errors: PG_EINVAL.
+ */
+pg_status pg_metrics(const pg_counts *c, int64_t n, int32_t tau_num, int32_t tau_den,
+                     pg_metrics_out *out);
+
+/* Work counters and (with timing=1) kernel times of the last propagate call
+ * on g. */
+pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROPAGATE_H */

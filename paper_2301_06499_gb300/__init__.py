@@ -1,0 +1,191 @@
+"""PROPAGATE on GB300: exact per-seed ball sizes by Boolean seed propagation.
+
+Python binding of the C ABI in ``include/propagate.h`` (names kept). It only
+marshals arguments: graphs, seeds and result buffers go to the CUDA library,
+which runs every step (seed set-up, pull rounds, per-seed counts, frontier,
+fixpoint test). PyTorch, when present, only supplies device memory and the
+current CUDA stream.
+
+    g = Graph.from_csr(row_ptr, col, directed=True)       # CSR over in-edges
+    res = propagate_p(g, seeds)                            # Algorithm 1
+    res_s = propagate_s(g, seeds)                          # Algorithm 2
+    m = metrics(res, g.n)                                  # Sec. 3 metrics
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _abi
+from ._abi import (PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE, PropagateError)
+
+__all__ = ["Graph", "Result", "propagate_p", "propagate_s", "metrics", "options",
+           "PropagateError", "PG_DIR_AUTO", "PG_DIR_DENSE", "PG_DIR_SPARSE", "library_path"]
+
+
+def library_path() -> str:
+    from . import build
+    return build.LIB
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def options(**kw) -> _abi.Options:
+    """pg_options with the library defaults, overridden by keyword."""
+    o = _abi.Options()
+    _abi.lib().pg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """Device-resident CSR over in-edges (pg_graph)."""
+
+    def __init__(self, handle, n: int, m: int, keep=None):
+        self._h = handle
+        self.n = n
+        self.m = m
+        self._keep = keep  # borrowed device tensors must outlive the handle
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, n: int | None = None, directed: bool = True,
+                 stream=None) -> "Graph":
+        """row_ptr int64[n+1] and col int32[m] as numpy arrays (copied from the
+        host) or CUDA torch tensors (used in place)."""
+        L = _abi.lib()
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        keep = None
+        if hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda:
+            import torch
+            rp = row_ptr.to(torch.int64).contiguous()
+            cl = col.to(torch.int32).contiguous()
+            n = rp.numel() - 1 if n is None else n
+            m = cl.numel()
+            flags = _abi.PG_DEVICE_PTRS | _abi.PG_BORROW
+            rc = L.pg_graph_from_csr(rp.data_ptr(), cl.data_ptr() if m else None, n, m,
+                                     int(directed), flags, st, ctypes.byref(h))
+            keep = (rp, cl)
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            n = rp.size - 1 if n is None else n
+            m = cl.size
+            rc = L.pg_graph_from_csr(rp.ctypes.data, cl.ctypes.data if m else None, n, m,
+                                     int(directed), 0, st, ctypes.byref(h))
+        _abi.check(rc, "pg_graph_from_csr")
+        return cls(h, int(n), int(m), keep)
+
+    @classmethod
+    def from_inputs(cls, g, stream=None) -> "Graph":
+        """From a generated graph (``inputs.Graph``) held in host memory."""
+        return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream)
+
+    def rounds_bound(self) -> int:
+        r = ctypes.c_int32()
+        _abi.check(_abi.lib().pg_query_rounds_bound(self._h, ctypes.byref(r)),
+                   "pg_query_rounds_bound")
+        return int(r.value)
+
+    def last_stats(self) -> dict:
+        st = _abi.Stats()
+        _abi.check(_abi.lib().pg_last_stats(self._h, ctypes.byref(st)), "pg_last_stats")
+        return {f: getattr(st, f) for f, _ in _abi.Stats._fields_}
+
+    def close(self):
+        if self._h:
+            _abi.lib().pg_graph_free(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+@dataclass
+class Result:
+    """Output of one propagation.
+
+    counts   uint32[T+1, s]: counts[t, i] = nodes at distance exactly t from
+             seed i (row 0 all ones); T = rounds = Delta_LB of Alg. 1.
+    m_active uint64[T+2]: arcs the round-t sweep revisits (entry T+1 is the
+             final sweep that found no change).
+    """
+    rounds: int
+    counts: np.ndarray
+    m_active: np.ndarray
+    s: int
+    n: int
+
+    @property
+    def seed_edge_traversals(self) -> int:
+        """sum_t s * m_active(t): the work measure of the benchmark."""
+        return int(self.s) * int(self.m_active.astype(np.uint64).sum())
+
+
+def _run(fn, what, g: Graph, seeds, max_rounds, opts, stream) -> Result:
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    s = int(seeds.size)
+    st = stream if stream is not None else _current_stream()
+    o = opts if opts is not None else options()
+    bound = g.rounds_bound()
+    cap = min(bound, 65535) if max_rounds is None else int(max_rounds)
+    while True:
+        counts = np.zeros((cap + 1, s), dtype=np.uint32)
+        mact = np.zeros(cap + 2, dtype=np.uint64)
+        c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
+                        counts=counts.ctypes.data, m_active=mact.ctypes.data)
+        rc = fn(g._h, seeds.ctypes.data, s, ctypes.byref(c), ctypes.byref(o), st)
+        if rc == _abi.PG_ERANGE and max_rounds is None and cap < bound:
+            cap = bound
+            continue
+        _abi.check(rc, what)
+        T = int(c.rounds)
+        return Result(rounds=T, counts=counts[:T + 1].copy(), m_active=mact[:T + 2].copy(),
+                      s=s, n=g.n)
+
+
+def propagate_p(g: Graph, seeds, max_rounds: int | None = None, opts=None,
+                stream=None) -> Result:
+    """PROPAGATE-P (Alg. 1): all seeds diffuse together, s bits per node."""
+    return _run(_abi.lib().pg_propagate_p, "pg_propagate_p", g, seeds, max_rounds, opts, stream)
+
+
+def propagate_s(g: Graph, seeds, max_rounds: int | None = None, opts=None,
+                stream=None) -> Result:
+    """PROPAGATE-S (Alg. 2): seeds in passes of 1-bit planes, early break."""
+    return _run(_abi.lib().pg_propagate_s, "pg_propagate_s", g, seeds, max_rounds, opts, stream)
+
+
+def metrics(res: Result, n: int | None = None, tau=(9, 10)) -> dict:
+    """pg_metrics: diameter, effective diameter, average distance, reachable
+    pairs and connectivity rate from a Result."""
+    counts = np.ascontiguousarray(res.counts, dtype=np.uint32)
+    c = _abi.Counts(s=res.s, max_rounds=res.rounds, rounds=res.rounds, reserved=0,
+                    counts=counts.ctypes.data, m_active=None)
+    out = _abi.MetricsOut()
+    _abi.check(_abi.lib().pg_metrics(ctypes.byref(c), int(n if n is not None else res.n),
+                                     int(tau[0]), int(tau[1]), ctypes.byref(out)), "pg_metrics")
+    return {f: getattr(out, f) for f, _ in _abi.MetricsOut._fields_}

@@ -1,0 +1,102 @@
+"""ctypes declarations of the C ABI in ``include/propagate.h``.
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library. Loading fails loudly if the library cannot be built or found.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+PG_OK, PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT, PG_EDEVICE, PG_ECANCELLED, PG_ERANGE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PG_DEVICE_PTRS = 1
+PG_BORROW = 2
+PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("dense_threshold", ctypes.c_float),
+                ("group_lanes", ctypes.c_int32), ("piece_arcs", ctypes.c_int32),
+                ("gather_changed_only", ctypes.c_int32), ("planes_per_pass", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("window_rows", ctypes.c_int32)]
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("counts", ctypes.c_void_p), ("m_active", ctypes.c_void_p)]
+
+
+class MetricsOut(ctypes.Structure):
+    _fields_ = [("diameter", ctypes.c_int32), ("eff_diameter", ctypes.c_int32),
+                ("eff_diameter_interp", ctypes.c_double), ("avg_distance", ctypes.c_double),
+                ("avg_distance_incl_self", ctypes.c_double),
+                ("connectivity_rate", ctypes.c_double), ("reachable_pairs", ctypes.c_double),
+                ("R_last", ctypes.c_uint64), ("dist_sum", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("dense_rounds", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("m_active_total", ctypes.c_uint64), ("arcs_scanned", ctypes.c_uint64),
+                ("rows_gathered", ctypes.c_uint64), ("items", ctypes.c_uint64),
+                ("changed_rows", ctypes.c_uint64), ("frontier_arcs", ctypes.c_uint64),
+                ("words_per_row", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
+                ("ms_pull", ctypes.c_double), ("ms_post", ctypes.c_double),
+                ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
+                ("post_launches", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/propagate.h
+_vp, _i32, _i64, _u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+SIGNATURES = {
+    "pg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pg_version": (ctypes.c_char_p, []),
+    "pg_default_options": (None, [ctypes.POINTER(Options)]),
+    "pg_graph_from_csr": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.c_uint,
+                                         _vp, ctypes.POINTER(_vp)]),
+    "pg_graph_free": (None, [_vp]),
+    "pg_graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pg_query_rounds_bound": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    "pg_propagate_p": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(Counts),
+                                      ctypes.POINTER(Options), _vp]),
+    "pg_propagate_s": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(Counts),
+                                      ctypes.POINTER(Options), _vp]),
+    "pg_metrics": (ctypes.c_int, [ctypes.POINTER(Counts), _i64, _i32, _i32,
+                                  ctypes.POINTER(MetricsOut)]),
+    "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (built in-tree on first use if missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class PropagateError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().pg_strerror(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+def check(status: int, what: str):
+    if status != PG_OK:
+        raise PropagateError(status, what)

@@ -1,0 +1,133 @@
+// Internal declarations of the PROPAGATE library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "propagate.h"
+
+namespace pg {
+
+constexpr int kBlock = 256;
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+
+// Packed frontier append: count of rows in the high bits, running sum of
+// their out-degrees in the low kFsumBits bits (one 64-bit atomic keeps the
+// two consistent, so every frontier row gets its out-arc prefix).
+constexpr int kFsumBits = 37;
+constexpr unsigned long long kFsumMask = (1ULL << kFsumBits) - 1ULL;
+
+enum : int32_t { kModeDense = 0, kModeSparse = 1 };
+
+// Device-side control block of one propagation (one pass).
+struct Ctrl {
+  int32_t t;            // round being executed
+  int32_t done;         // 1 once the fixpoint (or an error) is reached
+  int32_t status;       // pg_status of the device side
+  int32_t mode;         // kModeDense / kModeSparse for round t
+  unsigned long long fpack;  // frontier F_t: (count << kFsumBits) | out-arc sum
+  unsigned long long nA;     // pieces in the sparse work list of round t
+  unsigned long long nA_next;
+  uint32_t blocks_done;  // last-block detection in the post kernel
+  int32_t last_round;    // T once done
+  int32_t dense_rounds;
+  int32_t row_base;      // round held in row 0 of the device counts window
+};
+
+// Per-round work counters (device), indexed by round.
+struct RoundStats {
+  unsigned long long m_active;
+  unsigned long long scanned;
+  unsigned long long gathered;
+  unsigned long long items;
+  unsigned long long changed;
+  unsigned long long fsum;
+};
+
+// Everything the round kernels need, passed by value.
+struct Params {
+  int64_t n, m;
+  const int64_t *row_ptr;  // in-CSR
+  const int32_t *col;
+  const int64_t *out_ptr;  // out-CSR (== in-CSR for symmetric graphs)
+  const int32_t *out_col;
+  uint64_t *X;  // signatures of round t-1 (read by the pull)
+  uint64_t *Y;  // signatures of round t (written by the pull)
+  int32_t Wp;   // words per row (padded)
+  int32_t s;    // seeds in this pass (valid bits)
+  uint32_t *C0, *C1;   // changed-in-round bitmaps, alternating by round parity
+  uint32_t *K0, *K1;   // claim / active bitmaps, alternating
+  uint32_t *Sat;       // saturated (all s bits set)
+  int64_t nbm;         // 32-bit words per bitmap
+  int32_t *F;          // rows changed in round t
+  int64_t *Fpre;       // out-arc prefix of F entries
+  unsigned long long *A;  // sparse work list: (row << 32) | piece
+  const unsigned long long *Pall;  // dense work list: every piece of every row with indeg > 0
+  int64_t nPall;
+  int32_t L;            // arcs per piece
+  uint32_t *counts;     // counts window [row_cap][s] of this pass
+  RoundStats *rs;       // [row_cap + 2], slot = round - row_base
+  Ctrl *ctrl;
+  int32_t max_rounds;
+  int32_t direction;
+  float dense_threshold;
+  int32_t row_cap;      // rows of the device counts window
+};
+
+// A device allocation owned by the library.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Workspace {
+  DevBuf X, Y, C0, C1, K0, K1, Sat, F, Fpre, A, counts, rs, ctrl, seeds;
+  Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> tev;  // timing events
+};
+
+struct PieceList {
+  int32_t L = 0;
+  DevBuf list;
+  int64_t count = 0;
+};
+
+}  // namespace pg
+
+struct pg_graph {
+  int64_t n = 0, m = 0;
+  int directed = 1;
+  int device = 0;
+  int64_t *row_ptr = nullptr;
+  int32_t *col = nullptr;
+  int64_t *out_ptr = nullptr;
+  int32_t *out_col = nullptr;
+  bool owns_in = true;
+  bool owns_out = true;
+  double mean_degree = 0.0;
+  int64_t max_degree = 0;
+  pg::PieceList pieces;
+  pg::Workspace ws;
+  pg_stats last{};
+  std::mutex mu;
+};
+
+namespace pg {
+
+// Grow-only device buffer; contents are not preserved on growth.
+pg_status ensure(DevBuf &b, size_t bytes);
+void release(DevBuf &b);
+pg_status cuda_status(cudaError_t e);
+int sm_count();
+// Dense piece list of g for piece length L (cached in g).
+pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st);
+// Exclusive scan of int64 in place over n entries (device).
+pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st);
+// Drops the CUDA graphs captured for g.
+void drop_graph_cache(pg_graph *g);
+
+}  // namespace pg

@@ -1,0 +1,380 @@
+// Graph construction: copy-in, on-device CSR validation, out-edge transpose,
+// and the dense work list (every row cut into pieces of at most L arcs).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pg {
+
+pg_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PG_OK;
+  if (e == cudaErrorMemoryAllocation) return PG_ENOMEM;
+  return PG_ECUDA;
+}
+
+pg_status ensure(DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return PG_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return cuda_status(e);
+  }
+  b.bytes = bytes;
+  return PG_OK;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+static int grid_for(int64_t work, int per_sm = 8) {
+  int64_t cap = (int64_t)sm_count() * per_sm;
+  int64_t need = (work + kBlock - 1) / kBlock;
+  return (int)std::max<int64_t>(1, std::min(cap, need));
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanPerThread = 8;
+constexpr int kScanTile = kBlock * kScanPerThread;
+
+__global__ void __launch_bounds__(kBlock) k_scan_tile(int64_t *data, int64_t n, int64_t *sums) {
+  __shared__ int64_t warp_tot[kBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPerThread;
+  int64_t v[kScanPerThread];
+  int64_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    int64_t i = base + k;
+    int64_t x = i < n ? data[i] : 0;
+    v[k] = run;  // exclusive within the thread
+    run += x;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t incl = run;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int64_t y = __shfl_up_sync(kFullMask, incl, off);
+    if (lane >= off) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = lane < kBlock / 32 ? warp_tot[lane] : 0;
+    int64_t ti = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      int64_t y = __shfl_up_sync(kFullMask, ti, off);
+      if (lane >= off) ti += y;
+    }
+    if (lane < kBlock / 32) warp_tot[lane] = ti - t;  // exclusive warp offsets
+    if (lane == kBlock / 32 - 1 && sums) sums[blockIdx.x] = ti;
+  }
+  __syncthreads();
+  const int64_t off = warp_tot[w] + (incl - run);
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    int64_t i = base + k;
+    if (i < n) data[i] = v[k] + off;
+  }
+}
+
+__global__ void k_scan_add(int64_t *data, int64_t n, const int64_t *sums) {
+  const int64_t tile = blockIdx.x;
+  const int64_t add = sums[tile];
+  const int64_t end = (tile + 1) * kScanTile < n ? (tile + 1) * kScanTile : n;
+  for (int64_t i = tile * kScanTile + threadIdx.x; i < end; i += blockDim.x)
+    data[i] += add;
+}
+
+pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st) {
+  if (n <= 0) return PG_OK;
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {
+    k_scan_tile<<<1, kBlock, 0, st>>>(data, n, nullptr);
+    return cuda_status(cudaGetLastError());
+  }
+  int64_t *sums = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&sums, sizeof(int64_t) * tiles, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  k_scan_tile<<<(unsigned)tiles, kBlock, 0, st>>>(data, n, sums);
+  pg_status rc = cuda_status(cudaGetLastError());
+  if (rc == PG_OK) rc = exclusive_scan_i64(sums, tiles, st);
+  if (rc == PG_OK) {
+    k_scan_add<<<(unsigned)tiles, kBlock, 0, st>>>(data, n, sums);
+    rc = cuda_status(cudaGetLastError());
+  }
+  cudaFreeAsync(sums, st);
+  return rc;
+}
+
+// ------------------------------------------------------------ validation
+// err bits: 1 row_ptr[0] != 0, 2 non-monotone / past m, 4 col out of range,
+// 8 row not strictly increasing, 16 row_ptr[n] != m.
+__global__ void __launch_bounds__(kBlock) k_validate(const int64_t *rp, const int32_t *col,
+                                                     int64_t n, int64_t m, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
+  if (warp == 0 && lane == 0) {
+    if (rp[0] != 0) atomicOr(err, 1);
+    if (rp[n] != m) atomicOr(err, 16);
+  }
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = rp[v], e = rp[v + 1];
+    if (b > e || b < 0 || e > m) {
+      if (lane == 0) atomicOr(err, 2);
+      continue;
+    }
+    int bad = 0;
+    for (int64_t j = b + lane; j < e; j += 32) {
+      int32_t c = col[j];
+      if (c < 0 || c >= n) bad |= 4;
+      if (j > b && col[j - 1] >= c) bad |= 8;
+    }
+    if (bad) atomicOr(err, bad);
+  }
+}
+
+// --------------------------------------------------------------- transpose
+__global__ void k_count_out(const int32_t *col, int64_t m, unsigned long long *cnt) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[j]], 1ULL);
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter_out(const int64_t *rp, const int32_t *col,
+                                                        int64_t n, unsigned long long *cursor,
+                                                        int32_t *out_col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps)
+    for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+      unsigned long long pos = atomicAdd(&cursor[col[j]], 1ULL);
+      out_col[pos] = (int32_t)v;
+    }
+}
+
+__global__ void k_max_degree(const int64_t *rp, int64_t n, unsigned long long *mx) {
+  unsigned long long best = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    best = max(best, (unsigned long long)(rp[v + 1] - rp[v]));
+  atomicMax(mx, best);
+}
+
+// ------------------------------------------------------------- work list
+__global__ void k_piece_count(const int64_t *rp, int64_t n, int32_t L, int64_t *np) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = rp[v + 1] - rp[v];
+    np[v] = (d + L - 1) / L;
+  }
+}
+
+__global__ void k_piece_fill(const int64_t *np_ex, int64_t n, unsigned long long *list) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = np_ex[v], e = np_ex[v + 1];
+    for (int64_t k = b; k < e; ++k)
+      list[k] = ((unsigned long long)v << 32) | (unsigned long long)(k - b);
+  }
+}
+
+pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st) {
+  if (g->pieces.L == L && g->pieces.list.p) return PG_OK;
+  int64_t *np = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&np, sizeof(int64_t) * (g->n + 1), st);
+  if (e != cudaSuccess) return cuda_status(e);
+  k_piece_count<<<grid_for(g->n), kBlock, 0, st>>>(g->row_ptr, g->n, L, np);
+  cudaMemsetAsync(np + g->n, 0, sizeof(int64_t), st);
+  pg_status rc = exclusive_scan_i64(np, g->n + 1, st);
+  int64_t total = 0;
+  if (rc == PG_OK)
+    rc = cuda_status(cudaMemcpyAsync(&total, np + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc == PG_OK) rc = ensure(g->pieces.list, sizeof(unsigned long long) * (size_t)std::max<int64_t>(total, 1));
+  if (rc == PG_OK) {
+    k_piece_fill<<<grid_for(g->n), kBlock, 0, st>>>(np, g->n, (unsigned long long *)g->pieces.list.p);
+    rc = cuda_status(cudaGetLastError());
+  }
+  cudaFreeAsync(np, st);
+  if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc == PG_OK) {
+    g->pieces.L = L;
+    g->pieces.count = total;
+  } else {
+    g->pieces.L = 0;
+  }
+  return rc;
+}
+
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" {
+
+const char *pg_version(void) { return "propagate-gb300 1.0 (sm_103a)"; }
+
+const char *pg_strerror(pg_status st) {
+  switch (st) {
+    case PG_OK: return "ok";
+    case PG_EINVAL: return "invalid argument";
+    case PG_ENOMEM: return "out of memory";
+    case PG_ECUDA: return "CUDA runtime error";
+    case PG_ETIMEOUT: return "device-side wait timed out";
+    case PG_EDEVICE: return "inconsistent device state";
+    case PG_ECANCELLED: return "cancelled";
+    case PG_ERANGE: return "more rounds than max_rounds";
+  }
+  return "unknown status";
+}
+
+static void free_graph_arrays(pg_graph *g) {
+  if (g->owns_in) {
+    if (g->row_ptr) cudaFree(g->row_ptr);
+    if (g->col) cudaFree(g->col);
+  }
+  if (g->owns_out && g->out_ptr != g->row_ptr) {
+    if (g->out_ptr) cudaFree(g->out_ptr);
+    if (g->out_col) cudaFree(g->out_col);
+  }
+  g->row_ptr = g->out_ptr = nullptr;
+  g->col = g->out_col = nullptr;
+}
+
+void pg_graph_free(pg_graph *g) {
+  if (!g) return;
+  drop_graph_cache(g);
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    free_graph_arrays(g);
+    release(g->pieces.list);
+    Workspace &w = g->ws;
+    for (DevBuf *b : {&w.X, &w.Y, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F, &w.Fpre, &w.A,
+                      &w.counts, &w.rs, &w.ctrl, &w.seeds})
+      release(*b);
+    if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
+    for (auto &e : w.ev)
+      if (e) cudaEventDestroy(e);
+    for (auto &e : w.tev)
+      if (e) cudaEventDestroy(e);
+  }
+  delete g;
+}
+
+pg_status pg_graph_info(const pg_graph *g, int64_t *n, int64_t *m) {
+  if (!g) return PG_EINVAL;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  return PG_OK;
+}
+
+pg_status pg_query_rounds_bound(const pg_graph *g, int32_t *max_rounds) {
+  if (!g || !max_rounds) return PG_EINVAL;
+  *max_rounds = (int32_t)std::min<int64_t>(g->n - 1, 0x7FFFFFF0LL);
+  return PG_OK;
+}
+
+pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t m,
+                            int directed, unsigned flags, void *stream, pg_graph **out) {
+  if (!out) return PG_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n >= 0x7FFFFFFFLL || m < 0 || m >= (1LL << kFsumBits) || !row_ptr ||
+      (m > 0 && !col))
+    return PG_EINVAL;
+  if ((flags & PG_BORROW) && !(flags & PG_DEVICE_PTRS)) return PG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  pg_graph *g = new pg_graph();
+  g->n = n;
+  g->m = m;
+  g->directed = directed ? 1 : 0;
+  cudaGetDevice(&g->device);
+  pg_status rc = PG_OK;
+  const bool dev = flags & PG_DEVICE_PTRS;
+  if (flags & PG_BORROW) {
+    g->row_ptr = const_cast<int64_t *>(row_ptr);
+    g->col = const_cast<int32_t *>(col);
+    g->owns_in = false;
+  } else {
+    rc = cuda_status(cudaMalloc((void **)&g->row_ptr, sizeof(int64_t) * (n + 1)));
+    if (rc == PG_OK) rc = cuda_status(cudaMalloc((void **)&g->col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, st));
+    if (rc == PG_OK && m > 0)
+      rc = cuda_status(cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, kind, st));
+  }
+  int *err = nullptr;
+  unsigned long long *mx = nullptr;
+  if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&err, sizeof(int) + 16, st));
+  if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&mx, sizeof(unsigned long long), st));
+  if (rc == PG_OK) {
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
+    k_validate<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, n, m, err);
+    k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, mx);
+    rc = cuda_status(cudaGetLastError());
+  }
+  int err_h = 0;
+  unsigned long long mx_h = 0;
+  if (rc == PG_OK) rc = cuda_status(cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (rc == PG_OK) rc = cuda_status(cudaMemcpyAsync(&mx_h, mx, sizeof(mx_h), cudaMemcpyDeviceToHost, st));
+  if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+  if (err) cudaFreeAsync(err, st);
+  if (mx) cudaFreeAsync(mx, st);
+  if (rc == PG_OK && err_h) rc = PG_EINVAL;
+  g->max_degree = (int64_t)mx_h;
+  g->mean_degree = (double)m / (double)n;
+  if (rc == PG_OK) {
+    if (!directed) {
+      g->out_ptr = g->row_ptr;
+      g->out_col = g->col;
+      g->owns_out = false;
+    } else {
+      rc = cuda_status(cudaMalloc((void **)&g->out_ptr, sizeof(int64_t) * (n + 1)));
+      if (rc == PG_OK) rc = cuda_status(cudaMalloc((void **)&g->out_col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+      unsigned long long *cursor = nullptr;
+      if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&cursor, sizeof(unsigned long long) * n, st));
+      if (rc == PG_OK) {
+        cudaMemsetAsync(g->out_ptr, 0, sizeof(int64_t) * (n + 1), st);
+        k_count_out<<<grid_for(m), kBlock, 0, st>>>(g->col, m, (unsigned long long *)g->out_ptr);
+        rc = cuda_status(cudaGetLastError());
+      }
+      if (rc == PG_OK) rc = exclusive_scan_i64(g->out_ptr, n + 1, st);
+      if (rc == PG_OK) {
+        cudaMemcpyAsync(cursor, g->out_ptr, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st);
+        k_scatter_out<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, n, cursor, g->out_col);
+        rc = cuda_status(cudaGetLastError());
+      }
+      if (cursor) cudaFreeAsync(cursor, st);
+      if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    }
+  }
+  if (rc != PG_OK) {
+    cudaGetLastError();
+    free_graph_arrays(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return PG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol the
+header declares; host-only entry points work on CPU. No compute call here
+touches a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2301_06499_gb300 as pg
+from paper_2301_06499_gb300 import _abi
+from paper_2301_06499_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = _abi.lib()
+    names = _declared("propagate.h")
+    assert "pg_propagate_p" in names and "pg_propagate_s" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(_abi.SIGNATURES)
+
+
+def test_version_strerror_options():
+    lib = _abi.lib()
+    assert b"sm_103a" in lib.pg_version()
+    assert lib.pg_strerror(-7) == b"more rounds than max_rounds"
+    o = pg.options()
+    assert o.direction == pg.PG_DIR_AUTO and o.gather_changed_only == 1
+    assert o.planes_per_pass == 64 and o.use_graphs == 1
+    with pytest.raises(TypeError):
+        pg.options(bogus=1)
+
+
+def _metrics_from_hist(hist, n, tau=(9, 10)):
+    counts = np.ascontiguousarray(hist.T.astype(np.uint32))
+    res = pg.Result(rounds=hist.shape[1] - 1, counts=counts,
+                    m_active=np.zeros(hist.shape[1] + 1, np.uint64), s=hist.shape[0], n=n)
+    return pg.metrics(res, n, tau)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_pg_metrics_matches_oracle(seed):
+    g = I.er(400 + 50 * seed, 2.0 + seed, seed) if seed % 2 else I.random_digraph(300, 700, seed)
+    s = 10 + 7 * seed
+    seeds = I.seeds(g.n, s, seed + 40)
+    hist, _ = oracle.seed_histograms(g, seeds)
+    want = oracle.metrics(hist, g.n)
+    got = _metrics_from_hist(hist, g.n)
+    for k in ("diameter", "eff_diameter", "R_last", "dist_sum"):
+        assert got[k] == want[k], k
+    for k in ("eff_diameter_interp", "avg_distance", "avg_distance_incl_self",
+              "connectivity_rate", "reachable_pairs"):
+        assert got[k] == pytest.approx(want[k], rel=1e-12, abs=0.0), k
+
+
+def test_pg_metrics_rejects_bad_input():
+    lib = _abi.lib()
+    counts = np.ones((1, 2), np.uint32)
+    c = _abi.Counts(s=2, max_rounds=0, rounds=0, reserved=0, counts=counts.ctypes.data,
+                    m_active=None)
+    out = _abi.MetricsOut()
+    assert lib.pg_metrics(ctypes.byref(c), 10, 11, 10, ctypes.byref(out)) == _abi.PG_EINVAL
+    assert lib.pg_metrics(ctypes.byref(c), 0, 9, 10, ctypes.byref(out)) == _abi.PG_EINVAL
+    c.rounds = 3  # more rows than the buffer claims
+    assert lib.pg_metrics(ctypes.byref(c), 10, 9, 10, ctypes.byref(out)) == _abi.PG_EINVAL
+
+
+def test_pg_metrics_p4_worked_example():
+    g = I.path(4)
+    hist, _ = oracle.seed_histograms(g, np.arange(4, dtype=np.int32))
+    m = _metrics_from_hist(hist, 4)
+    assert m["eff_diameter"] == 3 and m["diameter"] == 3
+    assert m["eff_diameter_interp"] == pytest.approx(2.2, rel=1e-14)
+    assert m["reachable_pairs"] == 16.0

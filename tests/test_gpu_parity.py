@@ -1,0 +1,274 @@
+"""CUDA path vs the CPU oracle: every per-round, per-seed count bit-exact,
+m_active exact, metrics within 1e-12 relative, PROPAGATE-P == PROPAGATE-S,
+every schedule identical. Runs through the C ABI (ctypes binding)."""
+import ctypes
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2301_06499_gb300 as pg
+from paper_2301_06499_gb300 import _abi
+from paper_2301_06499_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12  # derived FP64 metrics: both sides divide identical integer sums
+
+
+def _oracle_p(g, seeds):
+    return oracle.run(g, seeds)
+
+
+def _oracle_s_mactive(g, seeds, planes, rounds):
+    """m_active of PROPAGATE-S: the per-pass measure summed over passes."""
+    _, _, dmat = oracle.seed_histograms(g, seeds, with_distances=True)
+    total = np.zeros(rounds + 2, dtype=np.uint64)
+    for b in range(0, len(seeds), planes):
+        sub = np.ascontiguousarray(dmat[:, b:b + planes])
+        ecc = sub.max()
+        part = oracle.m_active(g, sub, int(ecc) + 1)
+        total[:part.size] += part
+    return total
+
+
+def _assert_metrics(res, want, n):
+    got = pg.metrics(res, n)
+    for k in ("diameter", "eff_diameter", "R_last", "dist_sum"):
+        assert got[k] == want[k], k
+    for k in ("eff_diameter_interp", "avg_distance", "avg_distance_incl_self",
+              "connectivity_rate", "reachable_pairs"):
+        assert got[k] == pytest.approx(want[k], rel=REL, abs=0.0), k
+
+
+def _assert_same(res, want, check_mactive=True):
+    assert res.rounds == want["rounds"]
+    assert res.counts.shape == want["counts"].shape
+    bad = np.argwhere(res.counts != want["counts"])
+    assert bad.size == 0, f"first mismatches (round, seed): {bad[:5].tolist()}"
+    if check_mactive:
+        assert np.array_equal(res.m_active, want["m_active"]), (res.m_active, want["m_active"])
+
+
+@functools.lru_cache(maxsize=None)
+def _cfg1():
+    g = I.er(10_000, 8, 0)
+    seeds = I.seeds(g.n, 64, 1)
+    return g, seeds, _oracle_p(g, seeds)
+
+
+# ---------------------------------------------------------------- config 1
+def test_cfg1_er_propagate_p_default():
+    g, seeds, want = _cfg1()
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_p(G, seeds)
+    _assert_same(res, want)
+    _assert_metrics(res, want["metrics"], g.n)
+
+
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+@pytest.mark.parametrize("lanes", [2, 8, 32])
+@pytest.mark.parametrize("chg", [0, 1])
+def test_cfg1_every_schedule_identical(direction, lanes, chg):
+    g, seeds, want = _cfg1()
+    G = pg.Graph.from_inputs(g)
+    o = pg.options(direction=direction, group_lanes=lanes, gather_changed_only=chg)
+    _assert_same(pg.propagate_p(G, seeds, opts=o), want)
+
+
+@pytest.mark.parametrize("graphs,timing", [(0, 0), (1, 0), (0, 1)])
+def test_cfg1_launch_modes_identical(graphs, timing):
+    g, seeds, want = _cfg1()
+    G = pg.Graph.from_inputs(g)
+    o = pg.options(use_graphs=graphs, timing=timing)
+    for _ in range(2):  # second call reuses the cached workspace / graph
+        _assert_same(pg.propagate_p(G, seeds, opts=o), want)
+    st = G.last_stats()
+    assert st["sweeps"] == want["rounds"] + 1
+    assert st["m_active_total"] == int(want["m_active"].sum())
+    if timing:
+        assert st["ms_pull"] > 0 and st["pull_launches"] >= st["sweeps"]
+
+
+@pytest.mark.parametrize("planes", [1, 5, 64])
+def test_cfg1_propagate_s_equals_p_and_oracle(planes):
+    g, seeds, want = _cfg1()
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_s(G, seeds, opts=pg.options(planes_per_pass=planes))
+    _assert_same(res, want, check_mactive=False)
+    assert np.array_equal(res.m_active, _oracle_s_mactive(g, seeds, planes, want["rounds"]))
+    _assert_metrics(res, want["metrics"], g.n)
+
+
+# ------------------------------------------------------ ragged seed counts
+@pytest.mark.parametrize("s", [1, 2, 3, 63, 64, 65, 100, 130, 257, 513, 700])
+def test_ragged_seed_counts(s):
+    g = I.er(3001, 5, 11)
+    seeds = I.seeds(g.n, s, 100 + s)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    _assert_same(pg.propagate_p(G, seeds), want)
+    _assert_same(pg.propagate_s(G, seeds), want, check_mactive=False)
+
+
+# ---------------------------------------------------- directed / skewed
+@pytest.mark.parametrize("scale,ef,s", [(12, 8, 64), (13, 16, 256), (11, 4, 100)])
+def test_directed_rmat(scale, ef, s):
+    g = I.rmat(scale, ef, 7, directed=True)
+    seeds = I.seeds(g.n, s, 5)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    for d in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+        _assert_same(pg.propagate_p(G, seeds, opts=pg.options(direction=d)), want)
+    res_s = pg.propagate_s(G, seeds)
+    _assert_same(res_s, want, check_mactive=False)
+
+
+@pytest.mark.parametrize("piece", [1, 3, 8, 64])
+def test_long_rows_split_into_pieces(piece):
+    # hubs of R-MAT and a star centre: rows far longer than a piece
+    g = I.rmat(12, 16, 3, directed=False)
+    seeds = I.seeds(g.n, 130, 9)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    for d in (pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+        o = pg.options(piece_arcs=piece, direction=d, group_lanes=4)
+        _assert_same(pg.propagate_p(G, seeds, opts=o), want)
+    st = I.star(5000)
+    sd = np.array([0, 17, 4999], dtype=np.int32)
+    want = _oracle_p(st, sd)
+    S = pg.Graph.from_inputs(st)
+    _assert_same(pg.propagate_p(S, sd, opts=pg.options(piece_arcs=piece)), want)
+
+
+def test_grid_small_every_direction():
+    g = I.grid(90, 70, 0.05, 3)
+    seeds = I.seeds(g.n, 128, 4)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    for d in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+        _assert_same(pg.propagate_p(G, seeds, opts=pg.options(direction=d)), want)
+
+
+# ------------------------------------------------------------ exact mode
+@pytest.mark.parametrize("kind", ["er", "digraph", "grid"])
+def test_exact_mode_all_nodes_seeds(kind):
+    g = {"er": lambda: I.er(300, 3, 2), "digraph": lambda: I.random_digraph(250, 600, 3),
+         "grid": lambda: I.grid(12, 17, 0.0, 0)}[kind]()
+    seeds = np.arange(g.n, dtype=np.int32)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_p(G, seeds)
+    _assert_same(res, want)
+    _assert_metrics(res, want["metrics"], g.n)
+    _assert_same(pg.propagate_s(G, seeds), want, check_mactive=False)
+    if kind == "grid":
+        m = pg.metrics(res, g.n)
+        assert m["reachable_pairs"] == g.n * g.n and m["diameter"] == 12 + 17 - 2
+
+
+# ------------------------------------------------------------ edge cases
+def test_single_node_no_edges():
+    g = I.from_arcs(1, np.array([], np.int32), np.array([], np.int32))
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_p(G, np.array([0], np.int32))
+    assert res.rounds == 0 and res.counts.tolist() == [[1]]
+    assert res.m_active.tolist() == [0, 0]
+    assert pg.propagate_s(G, np.array([0], np.int32)).counts.tolist() == [[1]]
+
+
+def test_isolated_nodes_and_unreachable():
+    src = np.array([0, 1, 5], np.int32)
+    dst = np.array([1, 2, 6], np.int32)
+    g = I.from_arcs(9, src, dst)  # nodes 3, 4, 7, 8 isolated
+    seeds = np.array([0, 3, 5, 8, 2], np.int32)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    _assert_same(pg.propagate_p(G, seeds), want)
+    _assert_same(pg.propagate_s(G, seeds), want, check_mactive=False)
+
+
+def test_long_path_moves_counts_window():
+    g = I.path(1500)
+    seeds = np.array([0, 700, 1499, 3], np.int32)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    for graphs in (0, 1):
+        o = pg.options(window_rows=37, use_graphs=graphs)
+        res = pg.propagate_p(G, seeds, opts=o)
+        _assert_same(res, want)
+    _assert_same(pg.propagate_s(G, seeds, opts=pg.options(window_rows=50)), want,
+                 check_mactive=False)
+
+
+def test_max_rounds_too_small_returns_erange_with_prefix():
+    g = I.path(40)
+    seeds = np.array([0], np.int32)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    L = _abi.lib()
+    cap = 10
+    counts = np.zeros((cap + 1, 1), np.uint32)
+    mact = np.zeros(cap + 2, np.uint64)
+    c = _abi.Counts(s=1, max_rounds=cap, rounds=0, reserved=0, counts=counts.ctypes.data,
+                    m_active=mact.ctypes.data)
+    rc = L.pg_propagate_p(G._h, np.array([0], np.int32).ctypes.data, 1, ctypes.byref(c),
+                          None, None)
+    assert rc == _abi.PG_ERANGE
+    assert c.rounds == cap + 1
+    assert np.array_equal(counts[:, 0], want["counts"][:cap + 1, 0])
+    # the graph stays usable
+    _assert_same(pg.propagate_p(G, seeds), want)
+
+
+def test_invalid_seeds_rejected():
+    g = I.er(100, 4, 1)
+    G = pg.Graph.from_inputs(g)
+    for bad in ([1, 1], [100], [-1], []):
+        with pytest.raises(pg.PropagateError) as e:
+            pg.propagate_p(G, np.array(bad, np.int32))
+        assert e.value.status == _abi.PG_EINVAL
+    _assert_same(pg.propagate_p(G, np.array([5, 7], np.int32)),
+                 _oracle_p(g, np.array([5, 7], np.int32)))
+
+
+@pytest.mark.parametrize("what", ["unsorted", "dup", "range", "rowptr", "last"])
+def test_invalid_csr_rejected(what):
+    rp = np.array([0, 2, 3, 5], np.int64)
+    col = np.array([1, 2, 0, 0, 1], np.int32)
+    if what == "unsorted":
+        col[0], col[1] = 2, 1
+    elif what == "dup":
+        col[1] = 1
+    elif what == "range":
+        col[2] = 3
+    elif what == "rowptr":
+        rp[1] = 4
+    else:
+        rp[3] = 4
+    with pytest.raises(pg.PropagateError) as e:
+        pg.Graph.from_csr(rp, col, 3)
+    assert e.value.status == _abi.PG_EINVAL
+
+
+def test_device_pointer_graph_equals_host_graph():
+    torch = pytest.importorskip("torch")
+    g = I.rmat(12, 8, 21, directed=True)
+    seeds = I.seeds(g.n, 96, 2)
+    want = _oracle_p(g, seeds)
+    rp = torch.from_numpy(np.array(g.row_ptr)).cuda()
+    col = torch.from_numpy(np.array(g.col)).cuda()
+    G = pg.Graph.from_csr(rp, col, g.n, directed=True)
+    _assert_same(pg.propagate_p(G, seeds), want)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        _assert_same(pg.propagate_p(G, seeds), want)
+
+
+def test_repeated_calls_different_widths_reuse_graph():
+    g = I.er(5000, 6, 8)
+    G = pg.Graph.from_inputs(g)
+    for s in (64, 512, 3, 256, 64):
+        seeds = I.seeds(g.n, s, s)
+        _assert_same(pg.propagate_p(G, seeds), _oracle_p(g, seeds))
