@@ -88,16 +88,17 @@ typedef struct {
                                few, a full (dense) sweep otherwise */
   float dense_threshold;    /* AUTO: dense when frontier out-arcs > this * m
                                (0 = library default) */
-  int32_t group_lanes;      /* lanes cooperating on one node row, power of two
-                               in [1, 32]; 0 = chosen from the mean degree */
-  int32_t piece_arcs;       /* arcs per work item; longer rows are split into
-                               pieces combined with atomic OR; 0 = auto */
-  int32_t gather_changed_only; /* 1: OR only in-neighbours that changed in the
-                               previous round (same result: unchanged ones
-                               were already ORed in); 0: OR all of them */
+  int32_t group_lanes;      /* lanes sharing one work piece (1..32, power of
+                               two); a piece is group_lanes x 8 in-arcs for
+                               s <= 128, x 4 for s <= 256, x 2 above, and
+                               longer rows are split into
+                               pieces combined with atomic OR; 0 = the
+                               smallest group whose piece covers the mean
+                               in-degree */
   int32_t planes_per_pass;  /* PROPAGATE-S: seeds per pass, 1..64; 0 = 64 */
-  int32_t use_graphs;       /* 1: launch the round loop as captured CUDA
-                               graphs; 0: plain launches */
+  int32_t use_graphs;       /* 1: the round loop is one CUDA graph with a
+                               device-driven while node (no host round trip
+                               per round); 0: plain launches in batches */
   int32_t timing;           /* 1: record CUDA events around every kernel
                                launch (plain launches) for pg_last_stats */
   int32_t window_rows;      /* rows of per-round counters kept on the device
@@ -133,7 +134,7 @@ typedef struct {
   uint64_t changed_rows;     /* sum over rounds of rows that changed */
   uint64_t frontier_arcs;    /* sum over sparse rounds of the frontier's out-arcs */
   int32_t words_per_row;     /* 64-bit signature words per node (padded) */
-  int32_t group_lanes;
+  int32_t group_lanes;       /* lanes per work piece used */
   double ms_pull;            /* with timing=1: summed event time per kernel */
   double ms_post;
   double ms_init;

@@ -19,8 +19,8 @@ PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
 
 class Options(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("dense_threshold", ctypes.c_float),
-                ("group_lanes", ctypes.c_int32), ("piece_arcs", ctypes.c_int32),
-                ("gather_changed_only", ctypes.c_int32), ("planes_per_pass", ctypes.c_int32),
+                ("group_lanes", ctypes.c_int32),
+                ("planes_per_pass", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("window_rows", ctypes.c_int32)]
 

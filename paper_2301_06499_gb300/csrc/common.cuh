@@ -31,10 +31,14 @@ struct Ctrl {
   unsigned long long fpack;  // frontier F_t: (count << kFsumBits) | out-arc sum
   unsigned long long nA;     // pieces in the sparse work list of round t
   unsigned long long nA_next;
+  unsigned long long nE;     // expansion pieces of F_t (out-arcs in pieces of LE)
   uint32_t blocks_done;  // last-block detection in the post kernel
   int32_t last_round;    // T once done
   int32_t dense_rounds;
   int32_t row_base;      // round held in row 0 of the device counts window
+  int32_t iters;         // post launches of this pass (termination guard)
+  int32_t pad;
+  unsigned long long nF_prev;  // |F_{t-1}|
 };
 
 // Per-round work counters (device), indexed by round.
@@ -56,18 +60,25 @@ struct Params {
   const int32_t *out_col;
   uint64_t *X;  // signatures of round t-1 (read by the pull)
   uint64_t *Y;  // signatures of round t (written by the pull)
+  uint64_t *D0, *D1;  // deltas: D_{t&1}[v] = bits v gained in round t (0 if unchanged)
   int32_t Wp;   // words per row (padded)
   int32_t s;    // seeds in this pass (valid bits)
   uint32_t *C0, *C1;   // changed-in-round bitmaps, alternating by round parity
   uint32_t *K0, *K1;   // claim / active bitmaps, alternating
   uint32_t *Sat;       // saturated (all s bits set)
   int64_t nbm;         // 32-bit words per bitmap
-  int32_t *F;          // rows changed in round t
-  int64_t *Fpre;       // out-arc prefix of F entries
-  unsigned long long *A;  // sparse work list: (row << 32) | piece
-  const unsigned long long *Pall;  // dense work list: every piece of every row with indeg > 0
+  int32_t *F0, *F1;    // rows changed in round t, by round parity
+  unsigned long long *E;  // out-arc pieces of F rows: (row << 32) | piece of LE arcs
+  ulonglong2 *A;        // sparse work list: in-arc pieces of the claimed rows
+  const ulonglong2 *Pall;  // every in-arc piece of every row (unused by dense rounds)
+  const ulonglong2 *sell_items;  // dense rounds: sliced-ELL copy (see SellList)
+  const int32_t *sell_col;
+  const int64_t *sell_off;
+  const int32_t *sell_len;
+  int64_t sell_chunks;
   int64_t nPall;
-  int32_t L;            // arcs per piece
+  int32_t L;            // in-arcs per work piece
+  int32_t LE;           // out-arcs per expansion piece
   uint32_t *counts;     // counts window [row_cap][s] of this pass
   RoundStats *rs;       // [row_cap + 2], slot = round - row_base
   Ctrl *ctrl;
@@ -75,7 +86,19 @@ struct Params {
   int32_t direction;
   float dense_threshold;
   int32_t row_cap;      // rows of the device counts window
+  int32_t use_cond;     // launched inside a conditional while-graph
+  int32_t iter_guard;   // post launches after which a pass is abandoned
+  unsigned long long cond;  // cudaGraphConditionalHandle of that graph
 };
+
+// Work item of the pull: one piece of a row's in-arcs. x = first arc, y =
+// (row << 32) | (whole << 31) | arcs, `whole` marking a row of one piece.
+__host__ __device__ __forceinline__ ulonglong2 make_item(int32_t v, int64_t first, int64_t len,
+                                                         bool whole) {
+  return make_ulonglong2((unsigned long long)first,
+                         ((unsigned long long)(uint32_t)v << 32) | (whole ? 0x80000000ULL : 0ULL) |
+                             (unsigned long long)len);
+}
 
 // A device allocation owned by the library.
 struct DevBuf {
@@ -84,7 +107,7 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf X, Y, C0, C1, K0, K1, Sat, F, Fpre, A, counts, rs, ctrl, seeds;
+  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -94,6 +117,21 @@ struct PieceList {
   int32_t L = 0;
   DevBuf list;
   int64_t count = 0;
+};
+
+// Sliced-ELL copy of the in-CSR for dense rounds: rows cut into pieces of at
+// most Lmax arcs, pieces sorted by length (longest first), 32 per chunk; a
+// chunk's column indices are stored column-major (arc k of lane l at
+// off[c] + 32 k + l, -1 past a piece's end), so a warp reading step k of a
+// chunk loads 128 contiguous bytes.
+struct SellList {
+  int32_t Lmax = 0;
+  DevBuf items;  // ulonglong2 make_item per lane slot, nchunks * 32
+  DevBuf col;    // int32
+  DevBuf off;    // int64 per chunk
+  DevBuf len;    // int32 per chunk (its longest piece)
+  int64_t nchunks = 0;
+  int64_t slots = 0;  // total col entries
 };
 
 }  // namespace pg
@@ -111,8 +149,10 @@ struct pg_graph {
   double mean_degree = 0.0;
   int64_t max_degree = 0;
   pg::PieceList pieces;
+  pg::SellList sell;
   pg::Workspace ws;
   pg_stats last{};
+  int hint_p = 0, hint_s = 0;  // sweeps of the last pass, first batch of the next
   std::mutex mu;
 };
 
@@ -125,6 +165,8 @@ pg_status cuda_status(cudaError_t e);
 int sm_count();
 // Dense piece list of g for piece length L (cached in g).
 pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st);
+// Sliced-ELL copy of g's in-CSR for pieces of at most Lmax arcs (cached in g).
+pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st);
 // Exclusive scan of int64 in place over n entries (device).
 pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st);
 // Drops the CUDA graphs captured for g.

@@ -187,12 +187,16 @@ __global__ void k_piece_count(const int64_t *rp, int64_t n, int32_t L, int64_t *
   }
 }
 
-__global__ void k_piece_fill(const int64_t *np_ex, int64_t n, unsigned long long *list) {
+__global__ void k_piece_fill(const int64_t *rp, const int64_t *np_ex, int64_t n, int32_t L,
+                             ulonglong2 *list) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = np_ex[v], e = np_ex[v + 1];
-    for (int64_t k = b; k < e; ++k)
-      list[k] = ((unsigned long long)v << 32) | (unsigned long long)(k - b);
+    const int64_t rb = rp[v], d = rp[v + 1] - rb;
+    for (int64_t k = b; k < e; ++k) {
+      const int64_t q = k - b;
+      list[k] = make_item((int32_t)v, rb + q * L, min((int64_t)L, d - q * L), e - b == 1);
+    }
   }
 }
 
@@ -208,9 +212,10 @@ pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st) {
   if (rc == PG_OK)
     rc = cuda_status(cudaMemcpyAsync(&total, np + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
-  if (rc == PG_OK) rc = ensure(g->pieces.list, sizeof(unsigned long long) * (size_t)std::max<int64_t>(total, 1));
+  if (rc == PG_OK) rc = ensure(g->pieces.list, sizeof(ulonglong2) * (size_t)std::max<int64_t>(total, 1));
   if (rc == PG_OK) {
-    k_piece_fill<<<grid_for(g->n), kBlock, 0, st>>>(np, g->n, (unsigned long long *)g->pieces.list.p);
+    k_piece_fill<<<grid_for(g->n), kBlock, 0, st>>>(g->row_ptr, np, g->n, L,
+                                                    (ulonglong2 *)g->pieces.list.p);
     rc = cuda_status(cudaGetLastError());
   }
   cudaFreeAsync(np, st);
@@ -220,6 +225,121 @@ pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st) {
     g->pieces.count = total;
   } else {
     g->pieces.L = 0;
+  }
+  return rc;
+}
+
+// ------------------------------------------------------------ sliced ELL
+// Piece lengths histogram (bucket Lmax - len, so that a forward scan lists
+// the longest pieces first).
+__global__ void k_sell_hist(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
+                            unsigned long long *hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int len = (int)(pieces[i].y & 0x7FFFFFFFULL);
+    atomicAdd(&hist[Lmax - len], 1ULL);
+  }
+}
+
+__global__ void k_sell_scatter(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
+                               unsigned long long *cursor, ulonglong2 *sorted) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 it = pieces[i];
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    sorted[atomicAdd(&cursor[Lmax - len], 1ULL)] = it;
+  }
+}
+
+// chunk c: longest piece is lane 0's (sorted); slots = 32 x that length
+__global__ void k_sell_chunks(const ulonglong2 *sorted, int64_t np, int64_t nchunks,
+                              int32_t *clen, int64_t *coff) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int len = (int)(sorted[c * 32].y & 0x7FFFFFFFULL);
+    clen[c] = len;
+    coff[c] = 32LL * len;
+  }
+  (void)np;
+}
+
+__global__ void k_sell_fill(const ulonglong2 *sorted, int64_t nchunks, const int32_t *clen,
+                            const int64_t *coff, const int32_t *col, int32_t *scol) {
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t w = gtid; w < nchunks * 32; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = w >> 5;
+    const int lane = (int)(w & 31);
+    const ulonglong2 it = sorted[w];
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    const int64_t first = (int64_t)it.x;
+    const int cl = clen[c];
+    int32_t *dst = scol + coff[c] + lane;
+    for (int k = 0; k < cl; ++k) dst[32LL * k] = k < len ? col[first + k] : -1;
+  }
+}
+
+pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
+  SellList &sl = g->sell;
+  if (sl.Lmax == Lmax && sl.items.p) return PG_OK;
+  // pieces of at most Lmax arcs, in row order (the cached piece list is reused
+  // as scratch and rebuilt on its next use)
+  PieceList saved;
+  std::swap(saved, g->pieces);
+  pg_status rc = ensure_pieces(g, Lmax, st);
+  PieceList tmp;
+  std::swap(tmp, g->pieces);
+  std::swap(saved, g->pieces);
+  if (rc) {
+    release(tmp.list);
+    return rc;
+  }
+  const int64_t np = tmp.count;
+  const int64_t nchunks = (np + 31) / 32;
+  unsigned long long *hist = nullptr;
+  int64_t *coff_tmp = nullptr;
+  rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * (Lmax + 2), st));
+  if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
+  if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
+  if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
+  if (rc == PG_OK) {
+    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (Lmax + 2), st);
+    // padding slots: zero-length items of row 0 (never active)
+    cudaMemsetAsync(sl.items.p, 0, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1), st);
+    k_sell_hist<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist);
+    rc = exclusive_scan_i64((int64_t *)hist, Lmax + 2, st);
+  }
+  if (rc == PG_OK) {
+    k_sell_scatter<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist,
+                                                    (ulonglong2 *)sl.items.p);
+    k_sell_chunks<<<grid_for(nchunks), kBlock, 0, st>>>((const ulonglong2 *)sl.items.p, np,
+                                                        nchunks, (int32_t *)sl.len.p,
+                                                        (int64_t *)sl.off.p);
+    cudaMemsetAsync((int64_t *)sl.off.p + nchunks, 0, sizeof(int64_t), st);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (rc == PG_OK) rc = exclusive_scan_i64((int64_t *)sl.off.p, nchunks + 1, st);
+  int64_t slots = 0;
+  if (rc == PG_OK)
+    rc = cuda_status(cudaMemcpyAsync(&slots, (int64_t *)sl.off.p + nchunks, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+  if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc == PG_OK) rc = ensure(sl.col, sizeof(int32_t) * (size_t)std::max<int64_t>(slots, 1));
+  if (rc == PG_OK) {
+    k_sell_fill<<<grid_for(nchunks * 32), kBlock, 0, st>>>(
+        (const ulonglong2 *)sl.items.p, nchunks, (const int32_t *)sl.len.p,
+        (const int64_t *)sl.off.p, g->col, (int32_t *)sl.col.p);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (hist) cudaFreeAsync(hist, st);
+  (void)coff_tmp;
+  if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+  release(tmp.list);
+  if (rc == PG_OK) {
+    sl.Lmax = Lmax;
+    sl.nchunks = nchunks;
+    sl.slots = slots;
+  } else {
+    sl.Lmax = 0;
   }
   return rc;
 }
@@ -266,8 +386,9 @@ void pg_graph_free(pg_graph *g) {
     std::lock_guard<std::mutex> lk(g->mu);
     free_graph_arrays(g);
     release(g->pieces.list);
+    for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len}) release(*b);
     Workspace &w = g->ws;
-    for (DevBuf *b : {&w.X, &w.Y, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F, &w.Fpre, &w.A,
+    for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0, &w.F1, &w.E, &w.A,
                       &w.counts, &w.rs, &w.ctrl, &w.seeds})
       release(*b);
     if (w.ctrl_h) cudaFreeHost(w.ctrl_h);

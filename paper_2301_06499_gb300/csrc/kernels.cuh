@@ -2,13 +2,20 @@
 //
 // Round t (Alg. 1's do-while body; Alg. 2's inner loop for one pass) is two
 // kernels:
-//   pull(t): for every active node v,  new = X[v] | OR_{u in in(v)} X[u];
+//   pull(t): for every active node v, new = X[v] | OR_{u in in(v)} D[u];
 //            if new != X[v]: Y[v] = new, v joins the frontier F_t.
 //   post(t): for v in F_t: per-seed popcount of X[v] ^ Y[v] (the new pairs at
-//            distance t), then X[v] = Y[v]; build the work list of t+1.
+//            distance t), then D[v] = X[v] ^ Y[v] and X[v] = Y[v]; build the
+//            work list of round t+1.
 // X holds the signatures of round t-1 and is only read by the pull, Y only
 // written, so a round never sees its own updates (the synchronous diffusion
 // of Alg. 1: Sig_next is built from Sig, then copied back).
+//
+// D[u] (the bits u gained in round t-1, zero when u did not change) replaces
+// Sig(u) in Alg. 1's inner OR: Sig_{t-1}(u) = Sig_{t-2}(u) | D[u], and
+// Sig_{t-2}(u) was already ORed into Sig_{t-1}(v) in round t-1, so both give
+// the same Sig_t(v). It also marks the active nodes for free: v can change in
+// round t only if some in-neighbour has D[u] != 0.
 #pragma once
 
 #include "common.cuh"
@@ -36,32 +43,35 @@ __device__ __forceinline__ uint64_t valid_mask(int w, int s) {
   return (1ULL << (s - lo)) - 1ULL;
 }
 
+// 32-byte read-only load (one 256-bit access; p is 32-byte aligned).
+__device__ __forceinline__ void ld_nc_256(uint64_t *a, const uint64_t *p) {
+  asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(a[0]), "=l"(a[1]), "=l"(a[2]), "=l"(a[3])
+               : "l"(p));
+}
+
+// CW consecutive signature words (CW in {1, 2, 4, 8}; rows of CW >= 4 words
+// are 32-byte aligned, rows of 2 words 16-byte aligned).
 template <int CW>
 __device__ __forceinline__ void load_words(uint64_t (&a)[CW], const uint64_t *p) {
   if constexpr (CW == 1) {
     a[0] = __ldg(reinterpret_cast<const unsigned long long *>(p));
+  } else if constexpr (CW == 2) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
   } else {
 #pragma unroll
-    for (int k = 0; k < CW; k += 2) {
-      const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p) + k / 2);
-      a[k] = v.x;
-      a[k + 1] = v.y;
-    }
+    for (int k = 0; k < CW; k += 4) ld_nc_256(a + k, p + k);
   }
 }
 
 template <int CW>
 __device__ __forceinline__ void or_words(uint64_t (&a)[CW], const uint64_t *p) {
-  if constexpr (CW == 1) {
-    a[0] |= __ldg(reinterpret_cast<const unsigned long long *>(p));
-  } else {
+  uint64_t t[CW];
+  load_words<CW>(t, p);
 #pragma unroll
-    for (int k = 0; k < CW; k += 2) {
-      const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p) + k / 2);
-      a[k] |= v.x;
-      a[k + 1] |= v.y;
-    }
-  }
+  for (int k = 0; k < CW; ++k) a[k] |= t[k];
 }
 
 template <int CW>
@@ -104,33 +114,224 @@ __device__ __forceinline__ void block_add4(unsigned long long a, unsigned long l
   }
 }
 
+__device__ __forceinline__ unsigned long long warp_excl_scan64(unsigned long long x, int lane,
+                                                               unsigned long long *total) {
+  unsigned long long incl = x;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long y = __shfl_up_sync(kFullMask, incl, off);
+    if (lane >= off) incl += y;
+  }
+  *total = __shfl_sync(kFullMask, incl, 31);
+  return incl - x;
+}
+
+// Appends `cnt` list entries (row << 32 | q), q < cnt, for every lane with
+// cnt > 0, into list[] at an offset reserved with one atomicAdd on *counter.
+__device__ __forceinline__ void warp_append_pieces(unsigned long long *list,
+                                                   unsigned long long *counter, int32_t row,
+                                                   unsigned long long cnt, int lane) {
+  unsigned long long total;
+  const unsigned long long ex = warp_excl_scan64(cnt, lane, &total);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(kFullMask, base, 0);
+  const unsigned long long at = base + ex;
+  const unsigned long long head = cnt < 4 ? cnt : 4;
+  for (unsigned long long q = 0; q < head; ++q)
+    list[at + q] = ((unsigned long long)(uint32_t)row << 32) | q;
+  unsigned big = __ballot_sync(kFullMask, cnt > 4);
+  while (big) {  // long lists are written by the whole warp
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const unsigned long long c = __shfl_sync(kFullMask, cnt, src);
+    const unsigned long long a = __shfl_sync(kFullMask, at, src);
+    const int32_t r = __shfl_sync(kFullMask, row, src);
+    for (unsigned long long q = 4 + lane; q < c; q += 32)
+      list[a + q] = ((unsigned long long)(uint32_t)r << 32) | q;
+  }
+}
+
+// Appends the in-arc pieces of `row` (cnt = ceil(indeg / L) of them, first
+// arc rb) to the 16-byte work list, one atomicAdd per warp.
+__device__ __forceinline__ void warp_append_items(ulonglong2 *list, unsigned long long *counter,
+                                                  int32_t row, int64_t rb, int64_t indeg,
+                                                  int L, unsigned long long cnt, int lane) {
+  unsigned long long total;
+  const unsigned long long ex = warp_excl_scan64(cnt, lane, &total);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(kFullMask, base, 0);
+  const unsigned long long at = base + ex;
+  const bool whole = cnt == 1;
+  const unsigned long long head = cnt < 4 ? cnt : 4;
+  for (unsigned long long q = 0; q < head; ++q) {
+    const int64_t first = rb + (int64_t)q * L;
+    list[at + q] = make_item(row, first, min((int64_t)L, indeg - (int64_t)q * L), whole);
+  }
+  unsigned big = __ballot_sync(kFullMask, cnt > 4);
+  while (big) {  // long rows are written by the whole warp
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const unsigned long long c = __shfl_sync(kFullMask, cnt, src);
+    const unsigned long long a = __shfl_sync(kFullMask, at, src);
+    const int32_t r = __shfl_sync(kFullMask, row, src);
+    const int64_t b0 = __shfl_sync(kFullMask, rb, src);
+    const int64_t d0 = __shfl_sync(kFullMask, indeg, src);
+    for (unsigned long long q = 4 + lane; q < c; q += 32)
+      list[a + q] = make_item(r, b0 + (int64_t)q * L, min((int64_t)L, d0 - (int64_t)q * L), false);
+  }
+}
+
+// Frontier append of the rows whose lane has app set: F_t (rows; the packed
+// counter also sums their out-degrees) and E (their out-arcs in pieces of LE).
+__device__ __forceinline__ void frontier_append(const Params &p, Ctrl *ctrl, int32_t *F, int32_t v,
+                                                bool app, int lane) {
+  const unsigned mask = __ballot_sync(kFullMask, app);
+  if (!mask) return;
+  unsigned long long od = 0;
+  if (app) od = (unsigned long long)(__ldg(p.out_ptr + v + 1) - __ldg(p.out_ptr + v));
+  unsigned long long odt;
+  warp_excl_scan64(od, lane, &odt);
+  unsigned long long basep = 0;
+  if (lane == 0)
+    basep = atomicAdd(&ctrl->fpack, ((unsigned long long)__popc(mask) << kFsumBits) + odt);
+  basep = __shfl_sync(kFullMask, basep, 0);
+  if (app) {
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    F[(int64_t)(basep >> kFsumBits) + rank] = v;
+  }
+  const unsigned long long ne = app ? (od + p.LE - 1) / p.LE : 0ULL;
+  warp_append_pieces(p.E, &ctrl->nE, v, ne, lane);
+}
+
+// Finishes one row piece after its deltas are ORed into acc (words
+// [c*CW, c*CW+CW) of the row): a row of one piece compares with X[v] and
+// writes Y[v] if it changed; a row cut into pieces ORs acc into Y[v] with
+// atomics and reports a change when its OR added a bit.
+template <int CW>
+__device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, bool whole,
+                                             const uint64_t (&own)[CW],
+                                             const uint64_t (&acc)[CW]) {
+  const size_t Wp = (size_t)p.Wp;
+  bool changed = false;
+  if (whole) {
+    uint64_t nw[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      nw[k] = own[k] | acc[k];
+      changed |= nw[k] != own[k];
+    }
+    if (changed) store_words<CW>(p.Y + (size_t)v * Wp + c * CW, nw);
+  } else {
+#pragma unroll
+    for (int k = 0; k < CW; ++k)
+      if (acc[k]) {
+        const unsigned long long old =
+            atomicOr(reinterpret_cast<unsigned long long *>(p.Y + (size_t)v * Wp + c * CW + k),
+                     (unsigned long long)acc[k]);
+        changed |= (old | acc[k]) != old;
+      }
+  }
+  return changed;
+}
+
+// Dense round over the sliced-ELL copy: a warp per chunk of 32 pieces, lane
+// l owns piece l; step k reads arc k of all 32 pieces in one coalesced load,
+// and the U deltas of a lane's U steps are gathered together.
+template <int CW>
+__device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const uint64_t *Dprev,
+                                           int32_t *F, uint32_t *Ccur, uint32_t *Kcur, int lane,
+                                           int64_t warp, int64_t nwarps,
+                                           unsigned long long &my_mact,
+                                           unsigned long long &my_scan,
+                                           unsigned long long &my_items) {
+  constexpr int U = CW <= 2 ? 8 : 4;
+  const size_t Wp = (size_t)p.Wp;
+  const int nch = p.Wp / CW;
+  for (int64_t c = warp; c < p.sell_chunks; c += nwarps) {
+    const ulonglong2 it = p.sell_items[c * 32 + lane];
+    const int32_t v = (int32_t)(it.y >> 32);
+    const bool whole = (it.y & 0x80000000ULL) != 0ULL;
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    bool act = len > 0 && !test_bit(p.Sat, v);
+    const int clen = __ldg(p.sell_len + c);
+    const int32_t *cc = p.sell_col + __ldg(p.sell_off + c) + lane;
+    if (act) {
+      ++my_items;
+      my_scan += (unsigned long long)len;
+    }
+    bool row_changed = false, any_delta = false;
+    for (int ch = 0; ch < nch; ++ch) {
+      uint64_t own[CW], acc[CW];
+#pragma unroll
+      for (int k = 0; k < CW; ++k) own[k] = acc[k] = 0;
+      if (act && whole) load_words<CW>(own, p.X + (size_t)v * Wp + ch * CW);
+      for (int k0 = 0; k0 < clen; k0 += U) {
+        int32_t u[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) u[q] = (act && k0 + q < len) ? __ldg(cc + 32LL * (k0 + q)) : -1;
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (u[q] >= 0) or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
+      }
+#pragma unroll
+      for (int k = 0; k < CW; ++k) any_delta |= acc[k] != 0ULL;
+      if (act) row_changed |= finish_piece<CW>(p, v, ch, whole, own, acc);
+    }
+    act = act && any_delta;  // no changed in-neighbour: not active in round t
+    if (act) {
+      if (whole)
+        my_mact += (unsigned long long)len;
+      else if (!set_bit(Kcur, v))
+        my_mact += (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+    }
+    bool app = false;
+    if (act && row_changed) {
+      if (whole) {
+        atomicOr(Ccur + (v >> 5), 1u << (v & 31));
+        app = true;
+      } else {
+        app = !set_bit(Ccur, v);
+      }
+    }
+    frontier_append(p, ctrl, F, v, app, lane);
+  }
+}
+
+// Arcs per lane per piece of the sparse rounds: all of a lane's column loads
+// and delta gathers of one piece are issued together.
+template <int CW>
+struct PullUnroll {
+  static constexpr int value = CW <= 2 ? 8 : (CW == 4 ? 4 : 2);
+};
+
 // Pull kernel of round t.
 //
-// Work items are row pieces (row v, piece k): arcs [row_ptr[v] + k L,
-// min(row_ptr[v+1], row_ptr[v] + (k+1) L)). Dense rounds walk the static list
-// of every piece and skip saturated rows; sparse rounds walk the pieces of
-// the rows claimed by the previous post kernel. A group of G lanes takes one
-// piece; each lane ORs whole neighbour signatures (CW words per load
-// sequence, several loads in flight per lane), then the group reduces with
-// shuffles. A row of a single piece is finished by the group leader (compare
-// with X[v], write Y[v]); a row cut into pieces is combined with 64-bit
-// atomicOr into Y[v], and the piece whose OR first changed it appends v.
+// Dense rounds (most nodes have a changed in-neighbour) sweep the sliced-ELL
+// copy of every unsaturated row (pull_dense). Sparse rounds walk the pieces
+// of the rows the previous post kernel claimed (rows with a changed
+// in-neighbour and a zero bit); a group of G lanes takes one piece of at most
+// L = G * UNR in-arcs and each lane handles UNR of them in one shot: UNR
+// column loads, then UNR delta gathers, all independent. The group ORs its
+// lanes with log2(G) shuffles and its leader finishes the piece.
 //
-//  CHG: OR only in-neighbours whose bit in C_{t-1} is set (they are the only
-//       ones that can add bits: the others were ORed in the round before).
-//       Dense rounds always test C_{t-1}: a node with no changed in-neighbour
-//       is not active in round t.
-//  EB:  PROPAGATE-S early exit: a lane stops scanning once X[v] | acc has
-//       every valid bit of the pass set (Alg. 2's break at the first set
-//       in-neighbour, for 1..64 planes at once).
-template <int CW, int G, bool CHG, bool EB>
-__global__ void __launch_bounds__(kBlock) k_pull(Params p) {
-  static_assert(G >= 1 && G <= 32 && (32 % G) == 0, "group size");
+// Activity (for m_active) follows the skip rule of the proof of Thm. 1: a
+// node is revisited in round t when it still has a zero bit (not saturated)
+// and some in-neighbour changed in round t-1 (a nonzero delta). Sparse rounds
+// count it when the row is claimed.
+template <int CW, int G>
+__global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
+  constexpr int UNR = PullUnroll<CW>::value;
+  constexpr int GPW = 32 / G;
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
   const int t = ctrl->t;
   const bool dense = ctrl->mode == kModeDense;
-  const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
+  const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
+  int32_t *F = (t & 1) ? p.F1 : p.F0;
   uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
   uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
   uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
@@ -140,134 +341,80 @@ __global__ void __launch_bounds__(kBlock) k_pull(Params p) {
   for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
 
   const int lane = threadIdx.x & 31;
-  const int gl = lane & (G - 1);
-  const int gw = lane / G;
-  constexpr int GPW = 32 / G;
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
-  const int64_t nitems = dense ? p.nPall : (int64_t)ctrl->nA;
-  const unsigned long long *items = dense ? p.Pall : p.A;
-  const int nch = p.Wp / CW;
-  const size_t Wp = (size_t)p.Wp;
-  unsigned long long my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0;
-
-  for (int64_t base = warp * GPW; base < nitems; base += nwarps * GPW) {
-    const int64_t item = base + gw;
-    bool act = false, whole = true;
-    int32_t v = 0;
-    int64_t b = 0, e = 0, indeg = 0;
-    if (item < nitems) {
-      const unsigned long long it = items[item];
-      v = (int32_t)(it >> 32);
-      const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
-      const int64_t rb = __ldg(p.row_ptr + v), re = __ldg(p.row_ptr + v + 1);
-      indeg = re - rb;
-      b = rb + k * p.L;
-      e = min(re, b + (int64_t)p.L);
-      whole = indeg <= p.L;
-      act = dense ? !test_bit(p.Sat, v) : true;
-      if (!act) b = e = 0;
-    }
-    if (gl == 0 && act) ++my_items;
-    bool any_chg = false, row_changed = false;
-    const uint64_t *xv = p.X + (size_t)v * Wp;
-    for (int c = 0; c < nch; ++c) {
-      uint64_t acc[CW];
+  unsigned long long my_mact = 0, my_scan = 0, my_items = 0;
+  if (dense) {
+    pull_dense<CW>(p, ctrl, Dprev, F, Ccur, Kcur, lane, warp, nwarps, my_mact, my_scan,
+                   my_items);
+  } else {
+    const int gl = lane & (G - 1);
+    const int gw = lane / G;
+    const int64_t nitems = (int64_t)ctrl->nA;
+    const int nch = p.Wp / CW;
+    const size_t Wp = (size_t)p.Wp;
+    for (int64_t base = warp * GPW; base < nitems; base += nwarps * GPW) {
+      const int64_t item = base + gw;
+      bool act = false, whole = true;
+      int32_t v = 0;
+      int64_t b = 0;
+      int len = 0;
+      if (item < nitems) {
+        const ulonglong2 it = p.A[item];
+        b = (int64_t)it.x;
+        v = (int32_t)(it.y >> 32);
+        whole = (it.y & 0x80000000ULL) != 0ULL;
+        len = (int)(it.y & 0x7FFFFFFFULL);
+        act = true;
+      }
+      if (gl == 0 && act) {
+        ++my_items;
+        my_scan += (unsigned long long)len;
+      }
+      int32_t u[UNR];
 #pragma unroll
-      for (int k = 0; k < CW; ++k) acc[k] = 0;
-      uint64_t own[CW];
+      for (int q = 0; q < UNR; ++q) {
+        const int j = gl + q * G;
+        u[q] = (act && j < len) ? __ldg(p.col + b + j) : -1;
+      }
+      bool row_changed = false;
+      for (int c = 0; c < nch; ++c) {
+        uint64_t own[CW], acc[CW];
 #pragma unroll
-      for (int k = 0; k < CW; ++k) own[k] = 0;
-      if (EB && act) load_words<CW>(own, xv + c * CW);
-      for (int64_t j = b + gl; j < e; j += G) {
-        const int32_t u = __ldg(p.col + j);
-        ++my_scan;
-        if (CHG || dense) {
-          if (!test_bit(Cprev, u)) continue;
-          any_chg = true;
+        for (int k = 0; k < CW; ++k) own[k] = acc[k] = 0;
+        if (act && gl == 0 && whole) load_words<CW>(own, p.X + (size_t)v * Wp + c * CW);
+#pragma unroll
+        for (int q = 0; q < UNR; ++q)
+          if (u[q] >= 0) or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
+#pragma unroll
+        for (int off = G >> 1; off > 0; off >>= 1) {
+#pragma unroll
+          for (int k = 0; k < CW; ++k) acc[k] |= __shfl_xor_sync(kFullMask, acc[k], off);
         }
-        or_words<CW>(acc, p.X + (size_t)u * Wp + c * CW);
-        ++my_gath;
-        if (EB) {
-          bool full = true;
-#pragma unroll
-          for (int k = 0; k < CW; ++k)
-            full &= ((acc[k] | own[k] | ~valid_mask(c * CW + k, p.s)) == ~0ULL);
-          if (full) break;
-        }
+        if (act && gl == 0) row_changed |= finish_piece<CW>(p, v, c, whole, own, acc);
       }
-#pragma unroll
-      for (int off = G >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int k = 0; k < CW; ++k) acc[k] |= __shfl_xor_sync(kFullMask, acc[k], off);
-        any_chg |= (__shfl_xor_sync(kFullMask, (int)any_chg, off) != 0);
-      }
-      if (c == 0 && dense && !any_chg) {
-        act = false;
-        b = e = 0;
-      }
-      if (act && gl == 0) {
+      bool app = false;
+      if (act && gl == 0 && row_changed) {
         if (whole) {
-          if (!EB) load_words<CW>(own, xv + c * CW);
-          uint64_t nw[CW];
-          bool ch = false;
-#pragma unroll
-          for (int k = 0; k < CW; ++k) {
-            nw[k] = own[k] | acc[k];
-            ch |= nw[k] != own[k];
-          }
-          if (ch) store_words<CW>(p.Y + (size_t)v * Wp + c * CW, nw);
-          row_changed |= ch;
+          atomicOr(Ccur + (v >> 5), 1u << (v & 31));
+          app = true;
         } else {
-#pragma unroll
-          for (int k = 0; k < CW; ++k)
-            if (acc[k]) {
-              const unsigned long long old = atomicOr(
-                  reinterpret_cast<unsigned long long *>(p.Y + (size_t)v * Wp + c * CW + k),
-                  (unsigned long long)acc[k]);
-              row_changed |= (old | acc[k]) != old;
-            }
+          app = !set_bit(Ccur, v);
         }
       }
-    }
-    if (dense && act && gl == 0) {
-      // m_active counts each active row once; pieces of a long row race for it.
-      if (whole || !set_bit(Kcur, v)) my_mact += (unsigned long long)indeg;
-    }
-    bool app = false;
-    if (act && gl == 0 && row_changed) app = !set_bit(Ccur, v) || whole;
-    const unsigned mask = __ballot_sync(kFullMask, app);
-    if (mask) {
-      unsigned long long od = 0;
-      if (app) od = (unsigned long long)(__ldg(p.out_ptr + v + 1) - __ldg(p.out_ptr + v));
-      unsigned long long incl = od;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long y = __shfl_up_sync(kFullMask, incl, off);
-        if (lane >= off) incl += y;
-      }
-      const unsigned long long total = __shfl_sync(kFullMask, incl, 31);
-      unsigned long long basep = 0;
-      if (lane == 0)
-        basep = atomicAdd(&ctrl->fpack, ((unsigned long long)__popc(mask) << kFsumBits) + total);
-      basep = __shfl_sync(kFullMask, basep, 0);
-      if (app) {
-        const int rank = __popc(mask & ((1u << lane) - 1u));
-        const int64_t pos = (int64_t)(basep >> kFsumBits) + rank;
-        p.F[pos] = v;
-        p.Fpre[pos] = (int64_t)(basep & kFsumMask) + (int64_t)(incl - od);
-      }
+      frontier_append(p, ctrl, F, v, app, lane);
     }
   }
   RoundStats *r = p.rs + (t - ctrl->row_base);
-  block_add4(my_mact, my_scan, my_gath, my_items, &r->m_active, &r->scanned, &r->gathered,
+  // every scanned arc's delta is gathered, so `gathered` equals `scanned`
+  block_add4(my_mact, my_scan, my_scan, my_items, &r->m_active, &r->scanned, &r->gathered,
              &r->items);
 }
 
 using PullFn = void (*)(Params);
-PullFn pull_fn_cw1(int G, bool chg, bool eb);
-PullFn pull_fn_cw2(int G, bool chg, bool eb);
-PullFn pull_fn_cw4(int G, bool chg, bool eb);
-PullFn pull_fn_cw8(int G, bool chg, bool eb);
+PullFn pull_fn_cw1(int G);
+PullFn pull_fn_cw2(int G);
+PullFn pull_fn_cw4(int G);
+PullFn pull_fn_cw8(int G);
 
 }  // namespace pg

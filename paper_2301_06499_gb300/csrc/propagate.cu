@@ -4,6 +4,7 @@
 // and the host round loop.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "kernels.cuh"
@@ -12,6 +13,8 @@ namespace pg {
 
 constexpr int32_t kStatusWindow = 100;  // device asks the host to move the counts window
 constexpr int kSmemCountMax = 12288;    // per-seed counters kept in shared memory up to this s
+constexpr int kExpandArcs = 8;          // out-arcs per expansion piece (LE)
+constexpr int kSellPiece = 256;         // longest piece of the dense rounds' sliced-ELL copy
 
 // ------------------------------------------------------------- k_zero
 // Zeroes both signature buffers, the bitmaps, the pass's counts window and
@@ -24,13 +27,19 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
   ulonglong2 *x2 = reinterpret_cast<ulonglong2 *>(p.X);
   ulonglong2 *y2 = reinterpret_cast<ulonglong2 *>(p.Y);
   const ulonglong2 z = make_ulonglong2(0ULL, 0ULL);
+  ulonglong2 *d0 = reinterpret_cast<ulonglong2 *>(p.D0);
+  ulonglong2 *d1 = reinterpret_cast<ulonglong2 *>(p.D1);
   for (int64_t i = gtid; i < pairs; i += nth) {
     x2[i] = z;
     y2[i] = z;
+    d0[i] = z;
+    d1[i] = z;
   }
   if ((words & 1) && gtid == 0) {
     p.X[words - 1] = 0ULL;
     p.Y[words - 1] = 0ULL;
+    p.D0[words - 1] = 0ULL;
+    p.D1[words - 1] = 0ULL;
   }
   for (int64_t i = gtid; i < p.nbm; i += nth) {
     p.C0[i] = 0u;
@@ -51,105 +60,103 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     c->fpack = 0ULL;
     c->nA = 0ULL;
     c->nA_next = 0ULL;
+    c->nE = 0ULL;
     c->blocks_done = 0u;
     c->last_round = 0;
     c->dense_rounds = 0;
     c->row_base = 0;
+    c->iters = 0;
+    c->nF_prev = 0ULL;
   }
 }
 
 // ------------------------------------------------------------- k_seed
-// One block. Seed i of the pass gets bit i (Sig(x_i)[i] = 1) in both buffers;
-// round 0's frontier F_0 is the seed set, with its out-arc prefix; count row
-// 0 is one pair (x_i, x_i) per seed.
+// One block. Round 0 of the pass: seed i gets bit i (Sig(x_i)[i] = 1) as a
+// change of round 0 (X = 0, Y = the bit), so the post kernel of round 0
+// counts the pairs (x_i, x_i), records the seeds' deltas and expands them
+// like any other frontier.
 __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds, int sp) {
-  __shared__ unsigned long long wtot[32];
-  __shared__ unsigned long long carry;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) carry = 0ULL;
+  __shared__ unsigned long long tot;
+  if (threadIdx.x == 0) tot = 0ULL;
   __syncthreads();
-  for (int base = 0; base < sp; base += blockDim.x) {
-    const int i = base + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate so that the warp-level appends see every lane
+  for (int base = (threadIdx.x & ~31); base < sp; base += blockDim.x) {
+    const int i = base + lane;
     unsigned long long od = 0;
     int32_t x = 0;
-    if (i < sp) {
+    const bool ok = i < sp;
+    if (ok) {
       x = seeds[i];
-      const uint64_t bit = 1ULL << (i & 63);
-      p.X[(size_t)x * p.Wp + (i >> 6)] = bit;
-      p.Y[(size_t)x * p.Wp + (i >> 6)] = bit;
+      p.Y[(size_t)x * p.Wp + (i >> 6)] = 1ULL << (i & 63);
       set_bit(p.C0, x);
-      p.counts[i] = 1u;
+      p.F0[i] = x;
       od = (unsigned long long)(p.out_ptr[x + 1] - p.out_ptr[x]);
+      atomicAdd(&tot, od);
     }
-    unsigned long long incl = od;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long y = __shfl_up_sync(kFullMask, incl, off);
-      if (lane >= off) incl += y;
-    }
-    if (lane == 31) wtot[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      unsigned long long t = lane < nw ? wtot[lane] : 0ULL, ti = t;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long y = __shfl_up_sync(kFullMask, ti, off);
-        if (lane >= off) ti += y;
-      }
-      if (lane < nw) wtot[lane] = ti - t;
-    }
-    __syncthreads();
-    if (i < sp) {
-      p.F[i] = x;
-      p.Fpre[i] = (int64_t)(carry + wtot[w] + incl - od);
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += wtot[w] + incl;
-    __syncthreads();
+    const unsigned long long ne = ok ? (od + p.LE - 1) / p.LE : 0ULL;
+    warp_append_pieces(p.E, &p.ctrl->nE, x, ne, lane);
   }
-  if (threadIdx.x == 0) p.ctrl->fpack = ((unsigned long long)sp << kFsumBits) | carry;
-}
-
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t *a, int64_t lo, int64_t hi,
-                                                   int64_t key) {
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(a + mid) <= key)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
+  __syncthreads();
+  if (threadIdx.x == 0) p.ctrl->fpack = ((unsigned long long)sp << kFsumBits) | tot;
 }
 
 __device__ __forceinline__ bool row_full(const uint64_t *row, int Wp, int s) {
   bool full = true;
-  for (int w = 0; w < Wp; ++w) full &= ((__ldg(reinterpret_cast<const unsigned long long *>(row) + w) | ~valid_mask(w, s)) == ~0ULL);
+  for (int w = 0; w < Wp; ++w)
+    full &= ((__ldg(reinterpret_cast<const unsigned long long *>(row) + w) | ~valid_mask(w, s)) ==
+             ~0ULL);
   return full;
+}
+
+// 32 x 32 bit transpose across a warp: on entry lane r holds row r (bit c =
+// M[r][c]); on exit lane c holds column c (bit r = M[r][c]). Five stages,
+// each swapping the off-diagonal blocks of one bit level.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int j = 16 >> st;
+    const uint32_t m = masks[st];
+    const uint32_t y = __shfl_xor_sync(kFullMask, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
 }
 
 // ------------------------------------------------------------- k_post
 // Round t, after the pull:
-//  A. for v in F_t: d = X[v] ^ Y[v]; per seed i add bit i of d into the
-//     count of round t (Alg. 1: Count += ||Sig_next(u) XOR Sig(u)||, kept per
-//     seed); X[v] = Y[v] (Alg. 1: Sig(u) = Sig_next(u)); mark v saturated when
-//     all its s bits are set (skip rule, proof of Thm. 1).
+//  A. for v in F_t (a warp per 32 rows): d = X[v] ^ Y[v]; per seed i add bit
+//     i of d over the 32 rows into the count of round t (Alg. 1:
+//     Count += ||Sig_next(u) XOR Sig(u)||, kept per seed; a 32x32 bit
+//     transpose puts each seed's bits of 32 rows in one lane for __popc);
+//     X[v] = Y[v] (Alg. 1: Sig(u) = Sig_next(u)); mark v saturated when all
+//     its s bits are set (skip rule, proof of Thm. 1).
 //  B. choose the direction of round t+1 from the frontier's out-arc count;
-//     if sparse, claim every unsaturated out-neighbour of F_t and list its
-//     pieces (the rows round t+1 must revisit), adding its in-degree to
-//     m_active[t+1].
-//  C. last block: fixpoint test (Alg. 1: do ... while Count > 0) and the
-//     hand-over to round t+1.
+//     if sparse, claim every unsaturated out-neighbour of F_t (out-arcs in
+//     pieces of LE, flattened per warp like the pull) and list its in-arc
+//     pieces, adding its in-degree to m_active[t+1].
+//  C. last block: fixpoint test (Alg. 1: do ... while Count > 0), hand-over
+//     to round t+1, and, inside a while-graph, the loop condition.
 template <bool SMEM>
 __global__ void __launch_bounds__(kBlock) k_post(Params p) {
   extern __shared__ uint32_t scnt[];
   Ctrl *ctrl = p.ctrl;
-  if (*(volatile int32_t *)&ctrl->done) return;
+  if (*(volatile int32_t *)&ctrl->done) {
+    if (p.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(p.cond, 0u);
+    return;
+  }
   const int t = ctrl->t;
   const int row = t - ctrl->row_base;  // row of round t in the counts window
   const unsigned long long fpack = ctrl->fpack;
   const int64_t nF = (int64_t)(fpack >> kFsumBits);
   const int64_t fsum = (int64_t)(fpack & kFsumMask);
+  const int64_t nE = (int64_t)ctrl->nE;
+  const int64_t nFprev = (int64_t)ctrl->nF_prev;
+  const int32_t *F = (t & 1) ? p.F1 : p.F0;
+  const int32_t *Fprev = (t & 1) ? p.F0 : p.F1;
+  uint64_t *Dcur = (t & 1) ? p.D1 : p.D0;
+  uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
   const uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
   uint32_t *Cnext = (t & 1) ? p.C0 : p.C1;
   uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
@@ -164,29 +171,51 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     for (int i = threadIdx.x; i < s; i += kBlock) scnt[i] = 0u;
     __syncthreads();
   }
-  // A. count, sync, saturation
-  for (int64_t i = gtid; i < nF; i += nth) {
-    const int32_t v = p.F[i];
+  // A. count, record deltas, sync, saturation
+  for (int64_t base = warp * 32; base < nF; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const bool valid = i < nF;
+    const int32_t v = valid ? F[i] : 0;
     uint64_t *xr = p.X + (size_t)v * Wp;
     const uint64_t *yr = p.Y + (size_t)v * Wp;
-    bool full = true;
+    uint64_t *dr = Dcur + (size_t)v * Wp;
+    bool full = valid;
     for (int w = 0; w < Wp; ++w) {
-      const uint64_t o = xr[w], nw = __ldg(reinterpret_cast<const unsigned long long *>(yr) + w);
-      full &= ((nw | ~valid_mask(w, s)) == ~0ULL);
-      uint64_t d = o ^ nw;
+      uint64_t o = 0, nw = 0;
+      if (valid) {
+        o = xr[w];
+        nw = __ldg(reinterpret_cast<const unsigned long long *>(yr) + w);
+      }
+      const uint64_t d = o ^ nw;
       if (d) {
         xr[w] = nw;
-        do {
-          const int bit = __ffsll((long long)d) - 1;
+        dr[w] = d;
+      }
+      full = full && ((nw | ~valid_mask(w, s)) == ~0ULL);
+      if (__any_sync(kFullMask, d != 0ULL)) {
+        const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+        const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+        const int c0 = w * 64 + lane;
+        if (n0) {
           if (SMEM)
-            atomicAdd(&scnt[w * 64 + bit], 1u);
+            atomicAdd(&scnt[c0], n0);
           else
-            atomicAdd(&crow[w * 64 + bit], 1u);
-          d &= d - 1ULL;
-        } while (d);
+            atomicAdd(&crow[c0], n0);
+        }
+        if (n1) {
+          if (SMEM)
+            atomicAdd(&scnt[c0 + 32], n1);
+          else
+            atomicAdd(&crow[c0 + 32], n1);
+        }
       }
     }
     if (full) set_bit(p.Sat, v);
+  }
+  // the deltas of round t-1 were read by the pull of round t: clear them
+  for (int64_t i = gtid; i < nFprev * Wp; i += nth) {
+    const int64_t r = i / Wp;
+    Dprev[(size_t)Fprev[r] * Wp + (i - r * Wp)] = 0ULL;
   }
   if (SMEM) {
     __syncthreads();
@@ -204,54 +233,45 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
   const bool expand = !next_dense && nF > 0 && t + 1 <= p.max_rounds + 1;
   unsigned long long my_mact = 0;
   if (expand) {
-    constexpr int kEPL = 4;
-    constexpr int64_t kChunk = 32 * kEPL;
-    for (int64_t c0 = warp * kChunk; c0 < fsum; c0 += nwarps * kChunk) {
-      const int64_t c1 = min(fsum, c0 + kChunk);
-      int64_t lo = 0, hi = 0;
-      if (lane == 0) {
-        lo = upper_bound_i64(p.Fpre, 0, nF, c0) - 1;
-        hi = upper_bound_i64(p.Fpre, lo, nF, c1 - 1);
+    // one thread per expansion piece of LE out-arcs, UNR arcs at a time
+    constexpr int UNR = 4;
+    for (int64_t base = warp * 32; base < nE; base += nwarps * 32) {
+      const int64_t i = base + lane;
+      int64_t ob = 0, oe = 0;
+      if (i < nE) {
+        const unsigned long long it = p.E[i];
+        const int32_t u = (int32_t)(it >> 32);
+        const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
+        const int64_t o1 = __ldg(p.out_ptr + u + 1);
+        ob = __ldg(p.out_ptr + u) + k * p.LE;
+        oe = min(o1, ob + (int64_t)p.LE);
       }
-      lo = __shfl_sync(kFullMask, lo, 0);
-      hi = __shfl_sync(kFullMask, hi, 0);
-#pragma unroll 1
-      for (int k = 0; k < kEPL; ++k) {
-        const int64_t e = c0 + k * 32 + lane;
-        bool claim = false;
-        int32_t x = 0;
-        unsigned long long np = 0;
-        if (e < c1) {
-          const int64_t i = upper_bound_i64(p.Fpre, lo, hi, e) - 1;
-          const int32_t u = __ldg(p.F + i);
-          x = __ldg(p.out_col + __ldg(p.out_ptr + u) + (e - __ldg(p.Fpre + i)));
-          if (!test_bit_live(p.Sat, x)) {
-            const bool sat_now = test_bit(Ccur, x) && row_full(p.Y + (size_t)x * Wp, Wp, s);
-            if (!sat_now && !set_bit(Knext, x)) {
-              const int64_t indeg = __ldg(p.row_ptr + x + 1) - __ldg(p.row_ptr + x);
-              my_mact += (unsigned long long)indeg;
-              np = (unsigned long long)((indeg + p.L - 1) / p.L);
-              claim = true;
-            }
-          }
-        }
-        const unsigned mask = __ballot_sync(kFullMask, claim);
-        if (mask) {
-          unsigned long long incl = np;
+      for (int h = 0; h < p.LE; h += UNR) {
+        int32_t x[UNR];
 #pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long y = __shfl_up_sync(kFullMask, incl, off);
-            if (lane >= off) incl += y;
+        for (int q = 0; q < UNR; ++q) {
+          const int64_t j = ob + h + q;
+          x[q] = j < oe ? __ldg(p.out_col + j) : -1;
+        }
+        bool cand[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; ++q)
+          cand[q] = x[q] >= 0 && !test_bit_live(p.Sat, x[q]) &&
+                    !(test_bit(Ccur, x[q]) && row_full(p.Y + (size_t)x[q] * Wp, Wp, s));
+        bool claim[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) claim[q] = cand[q] && !set_bit(Knext, x[q]);
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) {
+          unsigned long long np = 0;
+          int64_t rb = 0, indeg = 0;
+          if (claim[q]) {
+            rb = __ldg(p.row_ptr + x[q]);
+            indeg = __ldg(p.row_ptr + x[q] + 1) - rb;
+            my_mact += (unsigned long long)indeg;
+            np = (unsigned long long)((indeg + p.L - 1) / p.L);
           }
-          const unsigned long long total = __shfl_sync(kFullMask, incl, 31);
-          unsigned long long basep = 0;
-          if (lane == 0) basep = atomicAdd(&ctrl->nA_next, total);
-          basep = __shfl_sync(kFullMask, basep, 0);
-          if (claim) {
-            const unsigned long long at = basep + incl - np;
-            for (unsigned long long q = 0; q < np; ++q)
-              p.A[at + q] = ((unsigned long long)(uint32_t)x << 32) | q;
-          }
+          warp_append_items(p.A, &ctrl->nA_next, x[q], rb, indeg, p.L, np, lane);
         }
       }
     }
@@ -272,12 +292,18 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     RoundStats *r = p.rs + row;
     r->changed = (unsigned long long)nF;
     r->fsum = (unsigned long long)fsum;
+    ctrl->iters += 1;
+    ctrl->nF_prev = (unsigned long long)nF;
     if (nF == 0) {
       ctrl->last_round = t - 1;
       ctrl->done = 1;
     } else if (t >= p.max_rounds + 1) {
       ctrl->last_round = t;
       ctrl->status = PG_ERANGE;
+      ctrl->done = 1;
+    } else if (ctrl->iters > p.iter_guard) {
+      ctrl->last_round = t;
+      ctrl->status = PG_EDEVICE;
       ctrl->done = 1;
     } else {
       ctrl->t = t + 1;
@@ -286,6 +312,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
       ctrl->nA = *(volatile unsigned long long *)&ctrl->nA_next;
       ctrl->nA_next = 0ULL;
       ctrl->fpack = 0ULL;
+      ctrl->nE = 0ULL;
       if (t + 1 - ctrl->row_base >= p.row_cap) {
         ctrl->status = kStatusWindow;
         ctrl->done = 1;
@@ -293,6 +320,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     }
     ctrl->blocks_done = 0u;
     __threadfence();
+    if (p.use_cond && ctrl->done) cudaGraphSetConditional(p.cond, 0u);
   }
 }
 
@@ -322,20 +350,19 @@ __global__ void k_window_shift(Params p, int64_t count_words, int32_t rs_slots) 
 
 // ---------------------------------------------------------------- host side
 struct Plan {
-  int CW = 1, G = 8, L = 32, Wp = 1;
-  bool chg = true, eb = false;
+  int CW = 1, G = 4, UNR = 8, L = 32, Wp = 1;
   PullFn pull = nullptr;
   int grid_pull = 1, grid_post = 1;
   size_t post_smem = 0;
   bool smem_counts = true;
 };
 
-static PullFn pick_pull(int CW, int G, bool chg, bool eb) {
+static PullFn pick_pull(int CW, int G) {
   switch (CW) {
-    case 1: return pull_fn_cw1(G, chg, eb);
-    case 2: return pull_fn_cw2(G, chg, eb);
-    case 4: return pull_fn_cw4(G, chg, eb);
-    case 8: return pull_fn_cw8(G, chg, eb);
+    case 1: return pull_fn_cw1(G);
+    case 2: return pull_fn_cw2(G);
+    case 4: return pull_fn_cw4(G);
+    case 8: return pull_fn_cw8(G);
   }
   return nullptr;
 }
@@ -349,23 +376,24 @@ static int occupancy_grid(const void *fn, size_t smem, int64_t work_threads) {
   return (int)std::max<int64_t>(1, std::min(cap, need));
 }
 
-static pg_status make_plan(const pg_graph *g, int sp, const pg_options &o, bool eb, Plan &pl) {
-  const int W = eb ? 1 : (sp + 63) / 64;
+// Group size: the smallest power of two whose piece (G * UNR arcs) covers the
+// mean in-degree, so that a typical row is one piece.
+static int auto_group(double mean_degree, int unr) {
+  int G = 1;
+  while (G < 32 && (double)(G * unr) < mean_degree) G <<= 1;
+  return G;
+}
+
+static pg_status make_plan(const pg_graph *g, int sp, const pg_options &o, bool s_mode, Plan &pl) {
+  const int W = s_mode ? 1 : (sp + 63) / 64;
   pl.CW = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
   pl.Wp = (W + pl.CW - 1) / pl.CW * pl.CW;
-  int G = o.group_lanes;
-  if (G <= 0) {
-    const double d = g->mean_degree;
-    G = d <= 6 ? 4 : d <= 12 ? 8 : d <= 40 ? 16 : 32;
-  }
-  if (G < 2) G = 2;
+  pl.UNR = pl.CW <= 2 ? 8 : (pl.CW == 4 ? 4 : 2);
+  int G = o.group_lanes > 0 ? o.group_lanes : auto_group(g->mean_degree, pl.UNR);
   if (G > 32 || (G & (G - 1))) return PG_EINVAL;
   pl.G = G;
-  pl.L = o.piece_arcs > 0 ? o.piece_arcs : 4 * G;
-  if (pl.L < 1) return PG_EINVAL;
-  pl.chg = o.gather_changed_only != 0;
-  pl.eb = eb;
-  pl.pull = pick_pull(pl.CW, pl.G, pl.chg, pl.eb);
+  pl.L = G * pl.UNR;
+  pl.pull = pick_pull(pl.CW, pl.G);
   if (!pl.pull) return PG_EINVAL;
   pl.smem_counts = sp <= kSmemCountMax;
   pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)sp : 0;
@@ -399,14 +427,13 @@ struct Call {
   pg_options o;
   int32_t s_total;
   int32_t max_rounds;
-  uint32_t *counts_h;                 // caller rows x s_total
-  std::vector<RoundStats> rs_h;       // summed over passes, rows 0..max_rounds+1
+  uint32_t *counts_h;            // caller rows x s_total
+  std::vector<RoundStats> rs_h;  // summed over passes, grown as rounds complete
   int32_t row_cap = 0;
 };
 
 static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_base, int32_t rows,
                              int32_t rs_rows) {
-  // counts rows [row_base, row_base+rows) of this pass's columns
   rows = std::min(rows, cl.max_rounds + 1 - row_base);
   if (rows > 0) {
     cudaError_t e = cudaMemcpy2DAsync(cl.counts_h + (size_t)row_base * cl.s_total + col0,
@@ -422,8 +449,10 @@ static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_ba
                                     cudaMemcpyDeviceToHost, cl.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cl.st);
     if (e != cudaSuccess) return cuda_status(e);
+    if ((int64_t)cl.rs_h.size() < (int64_t)row_base + rs_rows)
+      cl.rs_h.resize((size_t)row_base + rs_rows, RoundStats{});
     for (int i = 0; i < rs_rows; ++i) {
-      RoundStats &d = cl.rs_h[row_base + i];
+      RoundStats &d = cl.rs_h[(size_t)row_base + i];
       d.m_active += tmp[i].m_active;
       d.scanned += tmp[i].scanned;
       d.gathered += tmp[i].gathered;
@@ -435,12 +464,110 @@ static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_ba
   return cuda_status(cudaStreamSynchronize(cl.st));
 }
 
-static pg_status ensure_capture(pg_graph *g, const Plan &pl, const Params &p, int K,
-                                cudaGraphExec_t *out);
+// ------------------------------------------------------ captured round loop
+// A device-driven while-loop graph whose body is one round (pull + post); the
+// post kernel ends the loop at the fixpoint, on an error or when the counts
+// window is full. Cached per graph handle while the launch parameters stay
+// the same.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  Params p{};
+  PullFn pull = nullptr;
+  int grid_pull = 0, grid_post = 0;
+  size_t smem = 0;
+  bool smem_counts = true;
+  cudaStream_t cap = nullptr;
+};
+
+static std::mutex g_cache_mu;
+static std::vector<std::pair<pg_graph *, GraphCache>> g_caches;
+
+static GraphCache &cache_for(pg_graph *g) {
+  for (auto &pr : g_caches)
+    if (pr.first == g) return pr.second;
+  g_caches.push_back({g, GraphCache{}});
+  return g_caches.back().second;
+}
+
+static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p,
+                                    cudaGraphExec_t *out) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  GraphCache &c = cache_for(g);
+  Params key = p;
+  key.use_cond = 1;
+  key.cond = c.p.cond;  // compare everything but the handle
+  if (c.exec && c.pull == pl.pull && c.grid_pull == pl.grid_pull &&
+      c.grid_post == pl.grid_post && c.smem == pl.post_smem && c.smem_counts == pl.smem_counts &&
+      std::memcmp(&c.p, &key, sizeof(Params)) == 0) {
+    *out = c.exec;
+    return PG_OK;
+  }
+  if (c.exec) {
+    cudaGraphExecDestroy(c.exec);
+    c.exec = nullptr;
+  }
+  if (!c.cap && cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking) != cudaSuccess)
+    return PG_ECUDA;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaGraphConditionalHandle h = 0;
+  e = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault);
+  // cudaGraphNodeParams has no default constructor in C++ (a union of
+  // structs); build it in zeroed raw storage, as the API requires.
+  alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+  std::memset(np_raw, 0, sizeof(np_raw));
+  cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  Params pc = p;
+  pc.use_cond = 1;
+  pc.cond = (unsigned long long)h;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c.cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_round(pl, pc, c.cap);
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(c.cap, &captured);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c.exec = nullptr;
+    return cuda_status(e);
+  }
+  c.p = pc;
+  c.pull = pl.pull;
+  c.grid_pull = pl.grid_pull;
+  c.grid_post = pl.grid_post;
+  c.smem = pl.post_smem;
+  c.smem_counts = pl.smem_counts;
+  *out = c.exec;
+  return PG_OK;
+}
+
+void drop_graph_cache(pg_graph *g) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (size_t i = 0; i < g_caches.size(); ++i)
+    if (g_caches[i].first == g) {
+      if (g_caches[i].second.exec) cudaGraphExecDestroy(g_caches[i].second.exec);
+      if (g_caches[i].second.cap) cudaStreamDestroy(g_caches[i].second.cap);
+      g_caches.erase(g_caches.begin() + i);
+      return;
+    }
+}
 
 // One pass: sp seeds of the call, columns [col0, col0+sp).
 static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bool eb,
-                          PassOut &po) {
+                          int hint, PassOut &po) {
   pg_graph *g = cl.g;
   Workspace &w = g->ws;
   cudaStream_t st = cl.st;
@@ -449,15 +576,20 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   if (rc) return rc;
   rc = ensure_pieces(g, pl.L, st);
   if (rc) return rc;
+  if (cl.o.direction != PG_DIR_SPARSE && (rc = ensure_sell(g, kSellPiece, st))) return rc;
   const int64_t n = g->n;
   const int64_t nbm = (n + 31) / 32;
   const int32_t row_cap = cl.row_cap;
+  const int64_t e_cap = n + g->m / kExpandArcs + 1;
   size_t sig_bytes = sizeof(uint64_t) * (size_t)n * pl.Wp;
-  if ((rc = ensure(w.X, sig_bytes)) || (rc = ensure(w.Y, sig_bytes))) return rc;
+  if ((rc = ensure(w.X, sig_bytes)) || (rc = ensure(w.Y, sig_bytes)) ||
+      (rc = ensure(w.D0, sig_bytes)) || (rc = ensure(w.D1, sig_bytes)))
+    return rc;
   for (DevBuf *b : {&w.C0, &w.C1, &w.K0, &w.K1, &w.Sat})
     if ((rc = ensure(*b, sizeof(uint32_t) * nbm))) return rc;
-  if ((rc = ensure(w.F, sizeof(int32_t) * n)) || (rc = ensure(w.Fpre, sizeof(int64_t) * n)) ||
-      (rc = ensure(w.A, sizeof(unsigned long long) * std::max<int64_t>(g->pieces.count, 1))) ||
+  if ((rc = ensure(w.F0, sizeof(int32_t) * n)) || (rc = ensure(w.F1, sizeof(int32_t) * n)) ||
+      (rc = ensure(w.E, sizeof(unsigned long long) * e_cap)) ||
+      (rc = ensure(w.A, sizeof(ulonglong2) * std::max<int64_t>(g->pieces.count, 1))) ||
       (rc = ensure(w.counts, sizeof(uint32_t) * (size_t)row_cap * sp)) ||
       (rc = ensure(w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2))) ||
       (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)))
@@ -479,6 +611,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.out_col = g->out_col;
   p.X = (uint64_t *)w.X.p;
   p.Y = (uint64_t *)w.Y.p;
+  p.D0 = (uint64_t *)w.D0.p;
+  p.D1 = (uint64_t *)w.D1.p;
   p.Wp = pl.Wp;
   p.s = sp;
   p.C0 = (uint32_t *)w.C0.p;
@@ -487,12 +621,19 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.K1 = (uint32_t *)w.K1.p;
   p.Sat = (uint32_t *)w.Sat.p;
   p.nbm = nbm;
-  p.F = (int32_t *)w.F.p;
-  p.Fpre = (int64_t *)w.Fpre.p;
-  p.A = (unsigned long long *)w.A.p;
-  p.Pall = (const unsigned long long *)g->pieces.list.p;
+  p.F0 = (int32_t *)w.F0.p;
+  p.F1 = (int32_t *)w.F1.p;
+  p.E = (unsigned long long *)w.E.p;
+  p.A = (ulonglong2 *)w.A.p;
+  p.Pall = (const ulonglong2 *)g->pieces.list.p;
   p.nPall = g->pieces.count;
+  p.sell_items = (const ulonglong2 *)g->sell.items.p;
+  p.sell_col = (const int32_t *)g->sell.col.p;
+  p.sell_off = (const int64_t *)g->sell.off.p;
+  p.sell_len = (const int32_t *)g->sell.len.p;
+  p.sell_chunks = cl.o.direction != PG_DIR_SPARSE ? g->sell.nchunks : 0;
   p.L = pl.L;
+  p.LE = kExpandArcs;
   p.counts = (uint32_t *)w.counts.p;
   p.rs = (RoundStats *)w.rs.p;
   p.ctrl = (Ctrl *)w.ctrl.p;
@@ -500,9 +641,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.row_cap = row_cap;
   p.direction = cl.o.direction;
   p.dense_threshold = cl.o.dense_threshold > 0 ? cl.o.dense_threshold : 0.05f;
+  p.use_cond = 0;
+  p.cond = 0ULL;
+  p.iter_guard = cl.max_rounds + 2;
 
-  // grids
-  const int64_t pull_threads = std::max<int64_t>(p.nPall * pl.G, nbm);
+  const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
   pl.grid_post = occupancy_grid(post_fn(pl), pl.post_smem, std::max<int64_t>(n, nbm));
   if (pl.post_smem > 48 * 1024)
@@ -548,26 +691,80 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   if ((rc = cuda_status(cudaGetLastError()))) return rc;
 
-  // round loop: batches of K rounds, the host reads the control block of the
-  // batch before last while the last one runs.
-  constexpr int kGraphRounds = 16;
-  int K = 2;
-  int slot = 0;
-  int pending[2];
-  int npending = 0;
-  int64_t enqueued = 0;
   int32_t row_base = 0;
-  const int64_t guard = (int64_t)cl.max_rounds + 4 + 4 * kGraphRounds;
   Ctrl fin{};
   bool finished = false;
-  cudaGraphExec_t gexec = nullptr;
-  while (!finished) {
-    if (graphs && K >= kGraphRounds) {
-      if (!gexec && (rc = ensure_capture(g, pl, p, kGraphRounds, &gexec))) return rc;
-      if ((rc = cuda_status(cudaGraphLaunch(gexec, st)))) return rc;
-      enqueued += kGraphRounds;
-      po.launches += 2 * kGraphRounds;
-    } else {
+  if (graphs) {
+    // Device-driven loop: one graph launch runs rounds until the fixpoint,
+    // an error, or a full counts window.
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = ensure_while_graph(g, pl, p, &exec))) return rc;
+    int64_t launches_guard = (int64_t)cl.max_rounds / std::max<int32_t>(row_cap, 1) + 4;
+    while (!finished) {
+      if (launches_guard-- < 0) return PG_EDEVICE;
+      if ((rc = cuda_status(cudaGraphLaunch(exec, st)))) return rc;
+      cudaMemcpyAsync(&w.ctrl_h[0], p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+      if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+      const Ctrl c = w.ctrl_h[0];
+      if (!c.done) return PG_EDEVICE;
+      if (c.status == kStatusWindow) {
+        if ((rc = copy_window(cl, p, col0, row_base, row_cap, row_cap))) return rc;
+        k_window_shift<<<occupancy_grid((const void *)&k_window_shift, 0, count_words), kBlock,
+                         0, st>>>(p, count_words, row_cap + 2);
+        row_base += row_cap;
+        if ((rc = cuda_status(cudaGetLastError()))) return rc;
+        continue;
+      }
+      fin = c;
+      finished = true;
+    }
+    // every round of the loop is one pull and one post launch; iters counts
+    // the post launches of the pass, post(0) included
+    po.launches = 2 + 2 * std::max(0, fin.iters) - 1;
+  } else {
+    // Host-driven loop: batches of K rounds; the host reads the control
+    // block of the batch before last while the last one runs. A first batch
+    // of `hint` rounds (the sweeps of the previous call on this graph) is
+    // checked on its own, so a repeated call launches no idle rounds.
+    int K = 2;
+    if (hint > 0) {
+      for (int k = 0; k < hint; ++k) {
+        if (timing) {
+          int a = ntev++, b = ntev++, c = ntev++;
+          cudaEventRecord(tev(a), st);
+          pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
+          cudaEventRecord(tev(b), st);
+          if (pl.smem_counts)
+            k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
+          else
+            k_post<false><<<pl.grid_post, kBlock, 0, st>>>(p);
+          cudaEventRecord(tev(c), st);
+          pull_ev.push_back({a, b});
+          post_ev.push_back({b, c});
+        } else {
+          launch_round(pl, p, st);
+        }
+      }
+      po.launches += 2 * hint;
+      if ((rc = cuda_status(cudaGetLastError()))) return rc;
+      Ctrl cnow;
+      if ((rc = cuda_status(cudaMemcpyAsync(&w.ctrl_h[0], p.ctrl, sizeof(Ctrl),
+                                            cudaMemcpyDeviceToHost, st))) ||
+          (rc = cuda_status(cudaStreamSynchronize(st))))
+        return rc;
+      cnow = w.ctrl_h[0];
+      if (cnow.done && cnow.status != kStatusWindow) {
+        fin = cnow;
+        finished = true;
+      }
+      K = 4;
+    }
+    int slot = 0;
+    int pending[2];
+    int npending = 0;
+    int64_t enqueued = 0;
+    const int64_t guard = (int64_t)cl.max_rounds + 4 + 64;
+    while (!finished) {
       for (int k = 0; k < K; ++k) {
         if (timing) {
           int a = ntev++, b = ntev++, c = ntev++;
@@ -588,42 +785,42 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       enqueued += K;
       po.launches += 2 * K;
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
-    }
-    cudaMemcpyAsync(&w.ctrl_h[slot], p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(w.ev[slot], st);
-    pending[npending++] = slot;
-    slot ^= 1;
-    K = std::min(K * 2, kGraphRounds);
-    if (npending == 2 || enqueued > guard) {
-      const int s0 = pending[0];
-      if ((rc = cuda_status(cudaEventSynchronize(w.ev[s0])))) return rc;
-      pending[0] = pending[1];
-      npending--;
-      Ctrl c = w.ctrl_h[s0];
-      if (c.done) {
-        if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-        npending = 0;
-        Ctrl cnow;
-        if ((rc = cuda_status(cudaMemcpy(&cnow, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost))))
-          return rc;
-        if (cnow.status == kStatusWindow) {
-          if ((rc = copy_window(cl, p, col0, row_base, row_cap, row_cap))) return rc;
-          k_window_shift<<<occupancy_grid((const void *)&k_window_shift, 0, count_words), kBlock,
-                           0, st>>>(p, count_words, row_cap + 2);
-          po.launches += 1;
-          row_base += row_cap;
-          enqueued = 0;  // each shift is progress: the guard counts rounds since it
-          if ((rc = cuda_status(cudaGetLastError()))) return rc;
-          continue;
+      cudaMemcpyAsync(&w.ctrl_h[slot], p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+      cudaEventRecord(w.ev[slot], st);
+      pending[npending++] = slot;
+      slot ^= 1;
+      K = std::min(K * 2, 16);
+      if (npending == 2 || enqueued > guard) {
+        const int s0 = pending[0];
+        if ((rc = cuda_status(cudaEventSynchronize(w.ev[s0])))) return rc;
+        pending[0] = pending[1];
+        npending--;
+        const Ctrl c = w.ctrl_h[s0];
+        if (c.done) {
+          if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+          npending = 0;
+          Ctrl cnow;
+          if ((rc = cuda_status(cudaMemcpy(&cnow, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost))))
+            return rc;
+          if (cnow.status == kStatusWindow) {
+            if ((rc = copy_window(cl, p, col0, row_base, row_cap, row_cap))) return rc;
+            k_window_shift<<<occupancy_grid((const void *)&k_window_shift, 0, count_words),
+                             kBlock, 0, st>>>(p, count_words, row_cap + 2);
+            po.launches += 1;
+            row_base += row_cap;
+            enqueued = 0;  // each shift is progress: the guard counts rounds since it
+            if ((rc = cuda_status(cudaGetLastError()))) return rc;
+            continue;
+          }
+          fin = cnow;
+          finished = true;
+        } else if (enqueued > guard) {
+          return PG_EDEVICE;
         }
-        fin = cnow;
-        finished = true;
-      } else if (enqueued > guard) {
-        return PG_EDEVICE;
       }
     }
   }
-  // final window: rows row_base .. last_round (+1 for the stats of the empty sweep)
+  if (fin.status == PG_EDEVICE) return PG_EDEVICE;
   const int32_t last = fin.status == PG_ERANGE ? cl.max_rounds : fin.last_round;
   const int32_t rows = last - row_base + 1;
   if ((rc = copy_window(cl, p, col0, row_base, rows, rows + 1))) return rc;
@@ -646,78 +843,6 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     po.post_launches += (int)post_ev.size();
   }
   return PG_OK;
-}
-
-// Captures K rounds (pull + post each) into a CUDA graph on a private stream;
-// cached on the graph handle while the launch parameters stay the same.
-struct GraphCache {
-  cudaGraphExec_t exec = nullptr;
-  Params p{};
-  PullFn pull = nullptr;
-  int grid_pull = 0, grid_post = 0, K = 0;
-  size_t smem = 0;
-  bool smem_counts = true;
-  cudaStream_t cap = nullptr;
-};
-
-static std::mutex g_cache_mu;
-static std::vector<std::pair<pg_graph *, GraphCache>> g_caches;
-
-static GraphCache &cache_for(pg_graph *g) {
-  for (auto &pr : g_caches)
-    if (pr.first == g) return pr.second;
-  g_caches.push_back({g, GraphCache{}});
-  return g_caches.back().second;
-}
-
-static pg_status ensure_capture(pg_graph *g, const Plan &pl, const Params &p, int K,
-                                cudaGraphExec_t *out) {
-  std::lock_guard<std::mutex> lk(g_cache_mu);
-  GraphCache &c = cache_for(g);
-  if (c.exec && c.pull == pl.pull && c.grid_pull == pl.grid_pull && c.grid_post == pl.grid_post &&
-      c.K == K && c.smem == pl.post_smem && c.smem_counts == pl.smem_counts &&
-      std::memcmp(&c.p, &p, sizeof(Params)) == 0) {
-    *out = c.exec;
-    return PG_OK;
-  }
-  if (c.exec) {
-    cudaGraphExecDestroy(c.exec);
-    c.exec = nullptr;
-  }
-  if (!c.cap && cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking) != cudaSuccess)
-    return PG_ECUDA;
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return cuda_status(e);
-  for (int k = 0; k < K; ++k) launch_round(pl, p, c.cap);
-  e = cudaStreamEndCapture(c.cap, &graph);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaGraphInstantiate(&c.exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    c.exec = nullptr;
-    return cuda_status(e);
-  }
-  c.p = p;
-  c.pull = pl.pull;
-  c.grid_pull = pl.grid_pull;
-  c.grid_post = pl.grid_post;
-  c.K = K;
-  c.smem = pl.post_smem;
-  c.smem_counts = pl.smem_counts;
-  *out = c.exec;
-  return PG_OK;
-}
-
-void drop_graph_cache(pg_graph *g) {
-  std::lock_guard<std::mutex> lk(g_cache_mu);
-  for (size_t i = 0; i < g_caches.size(); ++i)
-    if (g_caches[i].first == g) {
-      if (g_caches[i].second.exec) cudaGraphExecDestroy(g_caches[i].second.exec);
-      if (g_caches[i].second.cap) cudaStreamDestroy(g_caches[i].second.cap);
-      g_caches.erase(g_caches.begin() + i);
-      return;
-    }
 }
 
 static pg_status check_seeds(const pg_graph *g, const int32_t *seeds, int32_t s) {
@@ -749,27 +874,36 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
   cl.counts_h = out->counts;
-  cl.rs_h.assign((size_t)out->max_rounds + 2, RoundStats{});
-  const int planes = s_mode ? (cl.o.planes_per_pass > 0 ? std::min(cl.o.planes_per_pass, 64) : 64) : s;
+  const int planes =
+      s_mode ? (cl.o.planes_per_pass > 0 ? std::min(cl.o.planes_per_pass, 64) : 64) : s;
   const int widest = std::min(planes, s);
   // counts window: up to max_rounds+1 rows, at most ~256 MB of counters
   int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * widest));
   if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
   cl.row_cap = (int32_t)std::min<int64_t>((int64_t)out->max_rounds + 1, cap_rows);
   if (cl.row_cap < 1) cl.row_cap = 1;
-  std::memset(out->counts, 0, sizeof(uint32_t) * ((size_t)out->max_rounds + 1) * s);
   pg_stats st{};
   int32_t T = 0, status = PG_OK;
   int passes = 0;
+  int &hint = s_mode ? g->hint_s : g->hint_p;
   for (int b = 0; b < s; b += planes) {
     const int sp = std::min(planes, s - b);
     PassOut po;
-    rc = run_pass(cl, seeds + b, sp, b, s_mode, po);
+    rc = run_pass(cl, seeds + b, sp, b, s_mode, hint, po);
+    if (rc == PG_OK && po.status == PG_OK) hint = std::min(po.rounds + 1, 64);
     if (rc) {
       cudaGetLastError();
       return rc;
     }
     ++passes;
+    // rows that only some passes reached: the others' columns are zero there
+    if (po.rounds < T) {
+      for (int32_t t = po.rounds + 1; t <= std::min(T, out->max_rounds); ++t)
+        std::memset(out->counts + (size_t)t * s + b, 0, sizeof(uint32_t) * sp);
+    } else if (po.rounds > T && b > 0) {
+      for (int32_t t = T + 1; t <= std::min(po.rounds, out->max_rounds); ++t)
+        std::memset(out->counts + (size_t)t * s, 0, sizeof(uint32_t) * b);
+    }
     T = std::max(T, po.rounds);
     if (po.status == PG_ERANGE) status = PG_ERANGE;
     st.dense_rounds += po.dense_rounds;
@@ -782,9 +916,9 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   }
   out->rounds = T;
   const int32_t last_stats = std::min(T + 1, out->max_rounds + 1);
+  if (cl.rs_h.size() < (size_t)last_stats + 1) cl.rs_h.resize((size_t)last_stats + 1, RoundStats{});
   if (out->m_active)
-    for (int32_t t = 0; t <= out->max_rounds + 1; ++t)
-      out->m_active[t] = t <= last_stats ? cl.rs_h[t].m_active : 0ULL;
+    for (int32_t t = 0; t <= last_stats; ++t) out->m_active[t] = cl.rs_h[t].m_active;
   for (int32_t t = 0; t <= last_stats; ++t) {
     const RoundStats &r = cl.rs_h[t];
     st.m_active_total += r.m_active;
@@ -816,8 +950,6 @@ void pg_default_options(pg_options *o) {
   o->direction = PG_DIR_AUTO;
   o->dense_threshold = 0.05f;
   o->group_lanes = 0;
-  o->piece_arcs = 0;
-  o->gather_changed_only = 1;
   o->planes_per_pass = 64;
   o->use_graphs = 1;
   o->timing = 0;

@@ -1,16 +1,16 @@
-// Pull kernels with 4 signature word(s) per lane load sequence.
+// Pull kernels with 4 signature word(s) per gather.
 #include "kernels.cuh"
 
 namespace pg {
 
-PullFn pull_fn_cw4(int G, bool chg, bool eb) {
-  if (eb) return nullptr;
+PullFn pull_fn_cw4(int G) {
   switch (G) {
-    case 2: return chg ? &k_pull<4, 2, true, false> : &k_pull<4, 2, false, false>;
-    case 4: return chg ? &k_pull<4, 4, true, false> : &k_pull<4, 4, false, false>;
-    case 8: return chg ? &k_pull<4, 8, true, false> : &k_pull<4, 8, false, false>;
-    case 16: return chg ? &k_pull<4, 16, true, false> : &k_pull<4, 16, false, false>;
-    case 32: return chg ? &k_pull<4, 32, true, false> : &k_pull<4, 32, false, false>;
+    case 1: return &k_pull<4, 1>;
+    case 2: return &k_pull<4, 2>;
+    case 4: return &k_pull<4, 4>;
+    case 8: return &k_pull<4, 8>;
+    case 16: return &k_pull<4, 16>;
+    case 32: return &k_pull<4, 32>;
   }
   return nullptr;
 }

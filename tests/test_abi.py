@@ -36,7 +36,7 @@ def test_version_strerror_options():
     assert b"sm_103a" in lib.pg_version()
     assert lib.pg_strerror(-7) == b"more rounds than max_rounds"
     o = pg.options()
-    assert o.direction == pg.PG_DIR_AUTO and o.gather_changed_only == 1
+    assert o.direction == pg.PG_DIR_AUTO and o.group_lanes == 0
     assert o.planes_per_pass == 64 and o.use_graphs == 1
     with pytest.raises(TypeError):
         pg.options(bogus=1)

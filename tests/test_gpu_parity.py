@@ -68,16 +68,15 @@ def test_cfg1_er_propagate_p_default():
 
 
 @pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
-@pytest.mark.parametrize("lanes", [2, 8, 32])
-@pytest.mark.parametrize("chg", [0, 1])
-def test_cfg1_every_schedule_identical(direction, lanes, chg):
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_cfg1_every_schedule_identical(direction, lanes):
     g, seeds, want = _cfg1()
     G = pg.Graph.from_inputs(g)
-    o = pg.options(direction=direction, group_lanes=lanes, gather_changed_only=chg)
+    o = pg.options(direction=direction, group_lanes=lanes)
     _assert_same(pg.propagate_p(G, seeds, opts=o), want)
 
 
-@pytest.mark.parametrize("graphs,timing", [(0, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("graphs,timing", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_cfg1_launch_modes_identical(graphs, timing):
     g, seeds, want = _cfg1()
     G = pg.Graph.from_inputs(g)
@@ -125,21 +124,21 @@ def test_directed_rmat(scale, ef, s):
     _assert_same(res_s, want, check_mactive=False)
 
 
-@pytest.mark.parametrize("piece", [1, 3, 8, 64])
-def test_long_rows_split_into_pieces(piece):
+@pytest.mark.parametrize("lanes", [1, 2, 8, 32])
+def test_long_rows_split_into_pieces(lanes):
     # hubs of R-MAT and a star centre: rows far longer than a piece
     g = I.rmat(12, 16, 3, directed=False)
     seeds = I.seeds(g.n, 130, 9)
     want = _oracle_p(g, seeds)
     G = pg.Graph.from_inputs(g)
     for d in (pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
-        o = pg.options(piece_arcs=piece, direction=d, group_lanes=4)
+        o = pg.options(group_lanes=lanes, direction=d)
         _assert_same(pg.propagate_p(G, seeds, opts=o), want)
     st = I.star(5000)
     sd = np.array([0, 17, 4999], dtype=np.int32)
     want = _oracle_p(st, sd)
     S = pg.Graph.from_inputs(st)
-    _assert_same(pg.propagate_p(S, sd, opts=pg.options(piece_arcs=piece)), want)
+    _assert_same(pg.propagate_p(S, sd, opts=pg.options(group_lanes=lanes)), want)
 
 
 def test_grid_small_every_direction():
