@@ -44,7 +44,9 @@ typedef enum {
   PG_ETIMEOUT = -4,    /* a bounded device-side wait expired */
   PG_EDEVICE = -5,     /* the device reported an inconsistent state */
   PG_ECANCELLED = -6,  /* the request was cancelled */
-  PG_ERANGE = -7       /* more rounds than the caller's max_rounds */
+  PG_ERANGE = -7,      /* more rounds than the caller's max_rounds */
+  PG_ETOOBIG = -8      /* problem larger than the fixed scratch of
+                          pg_propagate_p_noalloc */
 } pg_status;
 
 /* Opaque graph handle: device-resident CSR (in-edges and, for directed
@@ -213,6 +215,37 @@ pg_status pg_metrics(const pg_counts *c, int64_t n, int32_t tau_num, int32_t tau
 /* Work counters and (with timing=1) kernel times of the last propagate call
  * on g. */
 pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
+
+/*
+ * Allocation-free PROPAGATE-P. The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while they
+ * run (for example a serving process that reserves all of its device memory
+ * at start-up, or a latency-critical loop that cannot take the device-wide
+ * synchronisation an allocation may cause). It computes the same counts as
+ * pg_propagate_p, with every dense-round intermediate held in one fixed
+ * file-scope device array of PG_NOALLOC_SCRATCH_BYTES that each GPU loading
+ * the library keeps until the process exits; it calls no cudaMalloc or
+ * cudaFree.
+ *  row_ptr, col  device pointers, CSR over in-edges as for pg_graph_from_csr
+ *                (checked on the device; sortedness is not required)
+ *  seeds         host int32[s], distinct, in [0, n); s <= PG_NOALLOC_MAX_SEEDS
+ *  counts        device uint32[(max_rounds+1) * s], caller-allocated; zeroed
+ *                and filled like pg_counts.counts
+ *  rounds        host out: T as in pg_counts.rounds
+ *  stream        cudaStream_t; the call returns when the counts are written
+ * Limits: 4 * n * ceil(s/64) 64-bit words plus a small header must fit the
+ * scratch (with s <= 64, n up to about one million); larger problems return
+ * PG_ETOOBIG. Errors: PG_EINVAL (arguments, seeds, CSR), PG_ERANGE, PG_ECUDA.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the array and each clears what it uses; calls whose GPU work overlaps (on
+ * different streams) race on it, so order them on one stream.
+ */
+#define PG_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define PG_NOALLOC_MAX_SEEDS 1024
+pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_t *col, int64_t n,
+                                 int64_t m, const int32_t *seeds, int32_t s, uint32_t *counts,
+                                 int32_t max_rounds, int32_t *rounds, void *stream);
 
 #ifdef __cplusplus
 }

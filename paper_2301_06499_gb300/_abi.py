@@ -12,6 +12,9 @@ from . import build as _build
 
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT, PG_EDEVICE, PG_ECANCELLED, PG_ERANGE = (
     0, -1, -2, -3, -4, -5, -6, -7)
+PG_ETOOBIG = -8
+PG_NOALLOC_SCRATCH_BYTES = 32 << 20
+PG_NOALLOC_MAX_SEEDS = 1024
 PG_DEVICE_PTRS = 1
 PG_BORROW = 2
 PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
@@ -69,6 +72,8 @@ SIGNATURES = {
     "pg_metrics": (ctypes.c_int, [ctypes.POINTER(Counts), _i64, _i32, _i32,
                                   ctypes.POINTER(MetricsOut)]),
     "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "pg_propagate_p_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _i32,
+                                              ctypes.POINTER(_i32), _vp]),
 }
 
 _lock = threading.Lock()

@@ -362,6 +362,7 @@ const char *pg_strerror(pg_status st) {
     case PG_EDEVICE: return "inconsistent device state";
     case PG_ECANCELLED: return "cancelled";
     case PG_ERANGE: return "more rounds than max_rounds";
+    case PG_ETOOBIG: return "problem larger than the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }
