@@ -48,9 +48,18 @@ WORKLOADS = {
                       "4096x4096 grid, 5% edges deleted, s=128"),
     "rmat26_undirected_s512": (dict(kind="rmat", scale=26, ef=16, seed=2, directed=False), 512,
                                "undirected R-MAT scale 26, edge factor 16, s=512"),
+    "rmat23_undirected_s512": (dict(kind="rmat", scale=23, ef=16, seed=2, directed=False), 512,
+                               "undirected R-MAT scale 23, edge factor 16, s=512 (profiling "
+                               "stand-in for scale 26)"),
+}
+# Batched workload: 512 graphs, n log-uniform in [1e3, 1e6], ER / R-MAT / grid
+# with RNG seed 4, s per graph from eps in {0.1, 0.2} (see inputs.mix).
+BATCH_WORKLOADS = {
+    "mix512_batched": (512, 1e3, 1e6, 4),
+    "mix64_batched": (64, 1e3, 1e5, 4),
 }
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
-            "rmat26_undirected_s512": 2}
+            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2}
 
 
 def make_graph(spec):
@@ -152,12 +161,22 @@ class Clocks:
 
 def pull_bytes(st: dict) -> float:
     """Algorithmic bytes of the pull kernel summed over a call's launches:
-    per work item 8 B (list entry) + 16 B (row_ptr pair) + 8 Wp B (own
-    signature); per arc scanned 4 B (column index); per neighbour signature
-    ORed 8 Wp B; per changed row 8 Wp B (signature write)."""
+    per work item 16 B (item) + 8 B (row bounds) + 8 Wp B (own signature); per
+    in-arc scanned 4 B (column index), plus 1/8 B (its changed bit) when bits
+    are tested; per delta gathered 8 Wp B; per changed row 8 Wp B (signature
+    write)."""
     w = 8.0 * st["words_per_row"]
-    return (st["items"] * (24.0 + w) + st["arcs_scanned"] * 4.0 + st["rows_gathered"] * w
-            + st["changed_rows"] * w)
+    bit = 0.125 if st.get("test_changed") else 0.0
+    return (st["items"] * (24.0 + w) + st["arcs_scanned"] * (4.0 + bit)
+            + st["rows_gathered"] * w + st["changed_rows"] * w)
+
+
+def kernel_name(st: dict) -> str:
+    """Name of the pull kernel instantiation a call used (words per gather,
+    lanes per group), as ncu prints it."""
+    wp = st["words_per_row"]
+    cw = 1 if wp <= 1 else 2 if wp <= 2 else 4 if wp <= 4 else 8
+    return f"k_pull<{cw}, {st['group_lanes']}>"
 
 
 def run_ours(args):
@@ -200,7 +219,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    times, pull_ms, pull_launches, pull_b, post_ms, launches = [], 0.0, 0, 0.0, 0.0, 0
+    times, post_ms, launches = [], 0.0, 0
+    per_kernel = {}  # pull kernel name -> [ms, launches, bytes]
     p_ms, s_ms = [], []
     with Clocks(torch.cuda.current_device()) as clk:
         for _ in range(args.steps):
@@ -219,9 +239,10 @@ def run_ours(args):
             p_ms.append(e0.elapsed_time(e1))
             s_ms.append(e1.elapsed_time(e2))
             for st in (stp, sts):
-                pull_ms += st["ms_pull"]
-                pull_launches += st["pull_launches"]
-                pull_b += pull_bytes(st)
+                k = per_kernel.setdefault(kernel_name(st), [0.0, 0, 0.0])
+                k[0] += st["ms_pull"]
+                k[1] += st["pull_launches"]
+                k[2] += pull_bytes(st)
                 post_ms += st["ms_post"]
                 launches += st["launches"]
     torch.cuda.synchronize()
@@ -236,11 +257,14 @@ def run_ours(args):
     # propagations, counts back to the host, metrics, graph freed
     h2d = g.row_ptr.nbytes + g.col.nbytes + 2 * seeds.nbytes
     d2h = rp.counts.nbytes + rp.m_active.nbytes + rs.counts.nbytes + rs.m_active.nbytes
+    # the user's CSR, held in pinned host memory (allocated outside the timing)
+    rp_pinned = torch.from_numpy(np.array(g.row_ptr)).pin_memory().numpy()
+    col_pinned = torch.from_numpy(np.array(g.col)).pin_memory().numpy()
     e2e_ms = []
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G2 = pg.Graph.from_inputs(g, stream=sptr)
+        G2 = pg.Graph.from_csr(rp_pinned, col_pinned, g.n, directed=g.directed, stream=sptr)
         r1 = pg.propagate_p(G2, seeds, opts=opts_run, stream=sptr)
         r2 = pg.propagate_s(G2, seeds, opts=opts_run, stream=sptr)
         pg.metrics(r1, g.n)
@@ -253,13 +277,28 @@ def run_ours(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = (pull_b / max(pull_launches, 1)) / ((pull_ms / max(pull_launches, 1)) / 1e3) / 1e9
-    traffic = None
+    peak_src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                else "fallback 6.8 TB/s (profiling recipe)")
+    traffic_table = {}
     tpath = os.path.join(ROOT, "profiles", "pull_traffic.json")
     if os.path.exists(tpath):
         tr = json.load(open(tpath))
         if tr.get("workload") == args.workload and tr.get("kernel_hash") == kernel_hash():
-            traffic = tr.get("bytes_per_launch")
+            traffic_table = tr.get("bytes_per_launch", {})
+
+    def roofline_of(name):
+        ms, nl, byt = per_kernel[name]
+        ach = (byt / max(nl, 1)) / ((ms / max(nl, 1)) / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic_table.get(name), "kernel": name,
+                "algorithmic_bytes_per_launch": byt / max(nl, 1),
+                "ms_per_launch": ms / max(nl, 1), "launches": nl,
+                "share_of_step": ms / max(sum(times), 1e-9), "peak_source": peak_src}
+
+    ranked = sorted(per_kernel, key=lambda k: -per_kernel[k][0])
+    roofline = roofline_of(ranked[0])
+    roofline["post_share_of_step"] = post_ms / max(sum(times), 1e-9)
+    others = [roofline_of(k) for k in ranked[1:]]
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -273,12 +312,8 @@ def run_ours(args):
         "parts": {"propagate_p_ms": statistics.mean(p_ms), "propagate_s_ms": statistics.mean(s_ms),
                   "propagate_p_seed_edges_per_s": work_p / (statistics.mean(p_ms) / 1e3),
                   "propagate_s_seed_edges_per_s": work_p / (statistics.mean(s_ms) / 1e3)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_pull", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                     "pull_ms_per_launch": pull_ms / max(pull_launches, 1),
-                     "pull_share_of_step": pull_ms / max(sum(times), 1e-9),
-                     "post_share_of_step": post_ms / max(sum(times), 1e-9)},
+        "roofline": roofline,
+        "roofline_other_kernels": others,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / len(e2e_ms)},
         "gpu_launches": int(launches),
@@ -288,6 +323,140 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(g, seeds, s, args.cpu_seeds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_batch(args):
+    """Batched PROPAGATE-P over the mixed workload against the plain loop
+    (one pg_propagate_p per graph on the same resident graphs): value is the
+    batched seed-edge traversals/s, with the plain loop's beside it; every
+    graph's counts must be identical both ways."""
+    import ctypes
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2301_06499_gb300 as pg
+    from paper_2301_06499_gb300 import inputs as I
+
+    count, n_lo, n_hi, seed = BATCH_WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    items = I.mix(count, n_lo, n_hi, seed + 1000 * rank)  # each rank its own replica
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    graphs = [pg.Graph.from_inputs(it.graph, stream=sptr) for it in items]
+    batch = pg.Batch()
+    for it in items:
+        batch.add_inputs(it.graph, it.seeds)
+    opts = pg.options()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def plain():
+        res, work, launches = [], 0, 0
+        for G, it in zip(graphs, items):
+            res.append(pg.propagate_p(G, it.seeds, opts=opts, stream=sptr))
+            st = G.last_stats()
+            work += st["seed_edge_traversals"]
+            launches += st["launches"]
+        return res, work, launches
+
+    def batched():
+        batch.run(opts=opts, stream=sptr)
+        return batch.stats()
+
+    t0 = time.perf_counter()
+    batched()  # packs the graphs (host union + upload), untimed
+    pack_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        res_p, work, plain_launches = plain()
+        bst = batched()
+    for k, r in enumerate(res_p):
+        rb = batch.result(k)
+        assert rb.rounds == r.rounds and np.array_equal(rb.counts, r.counts), items[k].graph.name
+    assert bst["seed_edge_traversals"] == work, (bst["seed_edge_traversals"], work)
+
+    def timed(fn):
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        b_ms = timed(batched)
+        p_ms = timed(plain)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    b_total = reduce_max(sum(b_ms), world, dev)
+    p_total = reduce_max(sum(p_ms), world, dev)
+    total_work = reduce_sum(float(work * args.steps), world, dev)
+    value = total_work / (b_total / 1e3)
+    plain_value = total_work / (p_total / 1e3)
+
+    # end to end with host buffers: pack, upload, run, read every result back
+    h2d = sum(it.graph.row_ptr.nbytes + it.graph.col.nbytes + it.seeds.nbytes for it in items)
+    d2h = sum(r.counts.nbytes for r in res_p)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with pg.Batch() as b2:
+            for it in items:
+                b2.add_inputs(it.graph, it.seeds)
+            b2.run(opts=opts, stream=sptr)
+            out = [b2.result(k) for k in range(len(items))]
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    assert all(np.array_equal(o.counts, r.counts) for o, r in zip(out, res_p))
+    e2e_total = reduce_max(sum(e2e_ms), world, dev)
+    e2e_value = reduce_sum(float(work * len(e2e_ms)), world, dev) / (e2e_total / 1e3)
+
+    widths = sorted({(it.s + 63) // 64 for it in items})
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": b_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "description": f"{count} graphs, n log-uniform in [{n_lo:g}, {n_hi:g}], "
+                                  f"ER/R-MAT/grid (RNG {seed}), s from eps in {{0.1, 0.2}}",
+                   "sum_n": int(sum(it.graph.n for it in items)),
+                   "sum_m": int(sum(it.graph.m for it in items)),
+                   "sum_s": int(sum(it.s for it in items)), "signature_words": widths,
+                   "groups": bst["groups"], "batched_rounds": bst["sweeps"],
+                   "seed_edge_traversals_per_step": int(work),
+                   "generate_s": gen_s, "pack_s": pack_s,
+                   "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world} (independent mixes)"},
+        "plain": {"value": plain_value, "ms_per_step": p_total / args.steps,
+                  "gpu_launches": int(plain_launches)},
+        "batched_over_plain": plain_value and value / plain_value,
+        "roofline": None,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / len(e2e_ms)},
+        "gpu_launches": int(bst["launches"]),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    batch.close()
+    for G in graphs:
+        G.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -356,21 +525,50 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def profile_run(args):
+    """Builds the workload and calls PROPAGATE-P or -S twice with plain
+    launches (no CUDA graph), the program profiled by ncu: its pull launches
+    are the first call's, then the second call's (one per round)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2301_06499_gb300 as pg
+    from paper_2301_06499_gb300 import inputs as I
+    spec, s, _ = WORKLOADS[args.workload]
+    g = make_graph(spec)
+    seeds = I.seeds(g.n, s, seed_stream(args.workload, 0))
+    G = pg.Graph.from_inputs(g)
+    fn = pg.propagate_p if args.profile_run == "p" else pg.propagate_s
+    for _ in range(2):
+        res = fn(G, seeds, opts=pg.options(use_graphs=0))
+    print(json.dumps({"workload": args.workload, "rounds": res.rounds, **G.last_stats()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22_directed_s256")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS),
+                    default="rmat22_directed_s256")
     ap.add_argument("--cpu-seeds", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch every round kernel on the stream (no CUDA graph), e.g. under ncu")
+    ap.add_argument("--profile-run", choices=["p", "s"],
+                    help="only build the workload and run PROPAGATE-P/-S twice (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_run:
+        profile_run(args)
+    elif args.workload in BATCH_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the "
+                              "single-graph workloads; run it without --workload"}))
+        else:
+            run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -97,6 +97,12 @@ typedef struct {
                                pieces combined with atomic OR; 0 = the
                                smallest group whose piece covers the mean
                                in-degree */
+  int32_t test_changed;     /* an in-neighbour u adds to v only the bits u
+                               gained in the previous round (its delta, zero
+                               if u did not change). 1: test u's changed bit
+                               before reading its delta; 2: always read the
+                               delta; 0 (auto): test when the deltas exceed
+                               64 MiB (n x words per row x 8 bytes) */
   int32_t planes_per_pass;  /* PROPAGATE-S: seeds per pass, 1..64; 0 = 64 */
   int32_t use_graphs;       /* 1: the round loop is one CUDA graph with a
                                device-driven while node (no host round trip
@@ -142,6 +148,11 @@ typedef struct {
   double ms_init;
   int32_t pull_launches;
   int32_t post_launches;
+  int32_t test_changed;      /* 1 if changed bits were tested before gathers */
+  int32_t reserved;
+  uint64_t seed_edge_traversals; /* sum over rounds and active rows of
+                               s x in-degree (the benchmark's work measure;
+                               s of the row's own graph in a batch) */
 } pg_stats;
 
 /* Message for a status code (static storage). */
@@ -246,6 +257,65 @@ pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
 pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_t *col, int64_t n,
                                  int64_t m, const int32_t *seeds, int32_t s, uint32_t *counts,
                                  int32_t max_rounds, int32_t *rounds, void *stream);
+
+/*
+ * Batched PROPAGATE-P over many independent graphs. Sec. 4 notes that the
+ * work of a round splits over nodes without interaction; graphs that share
+ * nothing split the same way, so a batch packs the graphs of one signature
+ * width class (ceil(s/64) words rounded to 1, 2, 4 or a multiple of 8) into
+ * one disjoint union and runs each class as a single PROPAGATE-P: one pull
+ * and one post launch per round for all of its graphs. Each graph's counts
+ * equal what pg_propagate_p gives for it alone (its bits never leave its own
+ * nodes); only m_active is not kept per graph (pg_batch_result zero-fills
+ * it). The paper runs one graph per call; batching is this library's
+ * addition for workloads of many small graphs.
+ */
+typedef struct pg_batch pg_batch;
+
+typedef struct {
+  int32_t graphs;                /* graphs in the batch */
+  int32_t groups;                /* width classes, one PROPAGATE-P each */
+  int32_t sweeps;                /* rounds of the longest class */
+  int32_t launches;              /* kernels launched over all classes */
+  uint64_t seed_edge_traversals; /* sum over graphs of their own
+                                    pg_stats.seed_edge_traversals */
+} pg_batch_stats;
+
+/* New empty batch. Errors: PG_EINVAL (out NULL). */
+pg_status pg_batch_create(pg_batch **out);
+
+/* Frees the batch, its packed device graphs and stored results. NULL is
+ * allowed. */
+void pg_batch_free(pg_batch *b);
+
+/*
+ * Adds a graph (host CSR over in-edges as for pg_graph_from_csr, copied) and
+ * its seeds (host int32[s], distinct, in [0, n)). *index (may be NULL)
+ * receives the graph's position, used by pg_batch_result. Adding after a run
+ * repacks the batch on the next run. Errors: PG_EINVAL (arguments, seeds,
+ * row_ptr ends); the CSR's columns are checked on the device at the run.
+ */
+pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, int64_t n,
+                       int64_t m, int directed, const int32_t *seeds, int32_t s,
+                       int32_t *index);
+
+/*
+ * Runs every graph of the batch to its last productive round and keeps each
+ * graph's counts on the host. opt as for pg_propagate_p (planes_per_pass is
+ * ignored). Errors: PG_EINVAL (empty batch, malformed CSR), PG_ENOMEM,
+ * PG_ECUDA; on error no result of this run is kept.
+ */
+pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream);
+
+/*
+ * Copies graph index's counts of the last run into out (out->s must equal
+ * the graph's s; rows 0..min(T, out->max_rounds)). Errors: PG_EINVAL (no run,
+ * bad index or s), PG_ERANGE (T > out->max_rounds; out->rounds = T).
+ */
+pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out);
+
+/* Work counters of the last pg_batch_run. */
+pg_status pg_batch_get_stats(pg_batch *b, pg_batch_stats *out);
 
 #ifdef __cplusplus
 }

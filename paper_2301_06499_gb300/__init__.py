@@ -10,6 +10,9 @@ current CUDA stream.
     res = propagate_p(g, seeds)                            # Algorithm 1
     res_s = propagate_s(g, seeds)                          # Algorithm 2
     m = metrics(res, g.n)                                  # Sec. 3 metrics
+
+    b = Batch(); i = b.add(row_ptr, col, seeds); b.run()   # many graphs at once
+    res_i = b.result(i)
 """
 from __future__ import annotations
 
@@ -21,7 +24,7 @@ import numpy as np
 from . import _abi
 from ._abi import (PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE, PropagateError)
 
-__all__ = ["Graph", "Result", "propagate_p", "propagate_s", "metrics", "options",
+__all__ = ["Graph", "Result", "Batch", "propagate_p", "propagate_s", "metrics", "options",
            "PropagateError", "PG_DIR_AUTO", "PG_DIR_DENSE", "PG_DIR_SPARSE", "library_path"]
 
 
@@ -177,6 +180,79 @@ def propagate_s(g: Graph, seeds, max_rounds: int | None = None, opts=None,
                 stream=None) -> Result:
     """PROPAGATE-S (Alg. 2): seeds in passes of 1-bit planes, early break."""
     return _run(_abi.lib().pg_propagate_s, "pg_propagate_s", g, seeds, max_rounds, opts, stream)
+
+
+class Batch:
+    """pg_batch: PROPAGATE-P over many independent graphs, packed by
+    signature width into disjoint unions that each run as one propagation.
+    Host CSR arrays (over in-edges) and seeds are copied at add()."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().pg_batch_create(ctypes.byref(h)), "pg_batch_create")
+        self._h = h
+        self._n = []
+        self._s = []
+
+    def add(self, row_ptr, col, seeds, n: int | None = None, directed: bool = True) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        sd = np.ascontiguousarray(seeds, dtype=np.int32)
+        n = int(rp.size - 1 if n is None else n)
+        idx = ctypes.c_int32(-1)
+        _abi.check(_abi.lib().pg_batch_add(self._h, rp.ctypes.data, cl.ctypes.data, n,
+                                           int(cl.size), int(bool(directed)), sd.ctypes.data,
+                                           int(sd.size), ctypes.byref(idx)), "pg_batch_add")
+        self._n.append(n)
+        self._s.append(int(sd.size))
+        return int(idx.value)
+
+    def add_inputs(self, g, seeds) -> int:
+        return self.add(g.row_ptr, g.col, seeds, n=g.n, directed=g.directed)
+
+    def __len__(self):
+        return len(self._n)
+
+    def run(self, opts=None, stream=None):
+        st = stream if stream is not None else _current_stream()
+        o = opts if opts is not None else options()
+        _abi.check(_abi.lib().pg_batch_run(self._h, ctypes.byref(o), st), "pg_batch_run")
+
+    def result(self, index: int) -> Result:
+        """Counts of graph `index` from the last run (m_active is not kept
+        per graph in a batch and reads as zeros)."""
+        s, n = self._s[index], self._n[index]
+        cap = max(n - 1, 0)
+        counts = np.zeros((cap + 1, s), dtype=np.uint32)
+        c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
+                        counts=counts.ctypes.data, m_active=None)
+        _abi.check(_abi.lib().pg_batch_result(self._h, int(index), ctypes.byref(c)),
+                   "pg_batch_result")
+        T = int(c.rounds)
+        return Result(rounds=T, counts=counts[:T + 1].copy(),
+                      m_active=np.zeros(T + 2, dtype=np.uint64), s=s, n=n)
+
+    def stats(self) -> dict:
+        st = _abi.BatchStats()
+        _abi.check(_abi.lib().pg_batch_get_stats(self._h, ctypes.byref(st)), "pg_batch_get_stats")
+        return {f: getattr(st, f) for f, _ in _abi.BatchStats._fields_}
+
+    def close(self):
+        if self._h:
+            _abi.lib().pg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def metrics(res: Result, n: int | None = None, tau=(9, 10)) -> dict:

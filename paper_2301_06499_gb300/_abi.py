@@ -23,7 +23,7 @@ PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
 class Options(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("dense_threshold", ctypes.c_float),
                 ("group_lanes", ctypes.c_int32),
-                ("planes_per_pass", ctypes.c_int32),
+                ("test_changed", ctypes.c_int32), ("planes_per_pass", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("window_rows", ctypes.c_int32)]
 
@@ -51,7 +51,14 @@ class Stats(ctypes.Structure):
                 ("words_per_row", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("ms_pull", ctypes.c_double), ("ms_post", ctypes.c_double),
                 ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
-                ("post_launches", ctypes.c_int32)]
+                ("post_launches", ctypes.c_int32), ("test_changed", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("graphs", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("seed_edge_traversals", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/propagate.h
@@ -74,6 +81,13 @@ SIGNATURES = {
     "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "pg_propagate_p_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _i32,
                                               ctypes.POINTER(_i32), _vp]),
+    "pg_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
+    "pg_batch_free": (None, [_vp]),
+    "pg_batch_add": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, ctypes.c_int, _vp, _i32,
+                                    ctypes.POINTER(_i32)]),
+    "pg_batch_run": (ctypes.c_int, [_vp, ctypes.POINTER(Options), _vp]),
+    "pg_batch_result": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Counts)]),
+    "pg_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(BatchStats)]),
 }
 
 _lock = threading.Lock()

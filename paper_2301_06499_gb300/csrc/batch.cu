@@ -1,0 +1,272 @@
+// Batched PROPAGATE-P over many graphs (pg_batch_*).
+//
+// Graphs of the same signature width are packed into one disjoint union — a
+// CSR over in-edges with each graph's nodes and arcs shifted by its node
+// offset — and that union runs through the same round kernels as a single
+// graph: one pull and one post launch per round for every graph of the
+// group, the round loop being one device-driven CUDA graph. No arc joins two
+// graphs, so bit i of a node only ever means its own graph's seed i; the
+// post kernel looks up each changed node's graph to add its new bits to that
+// graph's count columns and to test saturation against that graph's seeds.
+// A graph whose propagation ended simply has no frontier in later rounds.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+struct pg_batch {
+  struct Item {
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<int32_t> seeds;
+    int64_t n = 0, m = 0;
+    int directed = 0;
+    int32_t rounds = -1;
+    std::vector<uint32_t> counts;  // (rounds+1) x s after a run
+    bool open = true;              // still receiving rows during a run
+  };
+  struct Group {
+    std::vector<int32_t> members;
+    pg_graph *g = nullptr;
+    pg::DevBuf node_graph, graph_s, graph_col0;
+    std::vector<int32_t> seeds, seed_bit, col0;
+    int32_t ncols = 0, s_bits = 0, max_rounds = 0;
+  };
+  std::vector<Item> items;
+  std::vector<Group> groups;
+  bool built = false;
+  pg_batch_stats stats{};
+  std::mutex mu;
+};
+
+namespace {
+
+using namespace pg;
+
+int width_class(int32_t s) {
+  const int W = (s + 63) / 64;
+  return W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : ((W + 7) / 8) * 8;
+}
+
+void free_groups(pg_batch *b) {
+  for (auto &gr : b->groups) {
+    if (gr.g) pg_graph_free(gr.g);
+    release(gr.node_graph);
+    release(gr.graph_s);
+    release(gr.graph_col0);
+  }
+  b->groups.clear();
+  b->built = false;
+}
+
+pg_status build_groups(pg_batch *b, cudaStream_t st) {
+  std::vector<int> classes;
+  for (auto &it : b->items) {
+    const int c = width_class((int32_t)it.seeds.size());
+    if (std::find(classes.begin(), classes.end(), c) == classes.end()) classes.push_back(c);
+  }
+  std::sort(classes.begin(), classes.end());
+  for (int c : classes) {
+    pg_batch::Group gr;
+    int64_t n = 0, m = 0;
+    int directed = 0;
+    for (int32_t i = 0; i < (int32_t)b->items.size(); ++i) {
+      const auto &it = b->items[i];
+      if (width_class((int32_t)it.seeds.size()) != c) continue;
+      gr.members.push_back(i);
+      n += it.n;
+      m += it.m;
+      directed |= it.directed;
+    }
+    if (n >= 0x7FFFFFFFLL) return PG_EINVAL;
+    std::vector<int64_t> rp((size_t)n + 1);
+    std::vector<int32_t> col((size_t)std::max<int64_t>(m, 1));
+    std::vector<int32_t> node_graph((size_t)n), graph_s, graph_col0;
+    int64_t v0 = 0, a0 = 0;
+    int32_t ncols = 0, s_bits = 0, maxr = 0;
+    for (size_t k = 0; k < gr.members.size(); ++k) {
+      const auto &it = b->items[gr.members[k]];
+      for (int64_t v = 0; v < it.n; ++v) {
+        rp[(size_t)(v0 + v)] = a0 + it.row_ptr[(size_t)v];
+        node_graph[(size_t)(v0 + v)] = (int32_t)k;
+      }
+      for (int64_t j = 0; j < it.m; ++j) col[(size_t)(a0 + j)] = (int32_t)(it.col[(size_t)j] + v0);
+      const int32_t s = (int32_t)it.seeds.size();
+      for (int32_t i = 0; i < s; ++i) {
+        gr.seeds.push_back((int32_t)(it.seeds[(size_t)i] + v0));
+        gr.seed_bit.push_back(i);
+      }
+      graph_s.push_back(s);
+      graph_col0.push_back(ncols);
+      ncols += s;
+      s_bits = std::max(s_bits, s);
+      maxr = std::max<int32_t>(maxr, (int32_t)std::min<int64_t>(it.n - 1, 0x3FFFFFFF));
+      v0 += it.n;
+      a0 += it.m;
+    }
+    rp[(size_t)n] = a0;
+    pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, 0, st, &gr.g);
+    if (rc) return rc;
+    rc = ensure(gr.node_graph, sizeof(int32_t) * (size_t)n);
+    if (!rc) rc = ensure(gr.graph_s, sizeof(int32_t) * graph_s.size());
+    if (!rc) rc = ensure(gr.graph_col0, sizeof(int32_t) * graph_col0.size());
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.node_graph.p, node_graph.data(),
+                                              sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_s.p, graph_s.data(),
+                                              sizeof(int32_t) * graph_s.size(), cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_col0.p, graph_col0.data(),
+                                              sizeof(int32_t) * graph_col0.size(),
+                                              cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    gr.col0 = graph_col0;
+    gr.ncols = ncols;
+    gr.s_bits = s_bits;
+    gr.max_rounds = maxr;
+    b->groups.push_back(std::move(gr));
+    if (rc) return rc;
+  }
+  b->built = true;
+  return PG_OK;
+}
+
+// Appends each graph's count columns, round by round, until the graph's first
+// round without a new pair (its BFS layers are contiguous, so every later
+// round is empty too).
+struct SinkCtx {
+  pg_batch *b;
+  pg_batch::Group *gr;
+};
+
+void take_window(void *vctx, int32_t row_base, int32_t rows, const uint32_t *data, int32_t ncols) {
+  SinkCtx *ctx = static_cast<SinkCtx *>(vctx);
+  for (size_t k = 0; k < ctx->gr->members.size(); ++k) {
+    auto &it = ctx->b->items[ctx->gr->members[k]];
+    if (!it.open) continue;
+    const int32_t s = (int32_t)it.seeds.size(), c0 = ctx->gr->col0[k];
+    for (int32_t r = 0; r < rows && it.open; ++r) {
+      const uint32_t *row = data + (size_t)r * ncols + c0;
+      bool any = false;
+      for (int32_t i = 0; i < s; ++i) any |= row[i] != 0u;
+      if (!any && row_base + r > 0) {
+        it.open = false;
+        break;
+      }
+      it.counts.insert(it.counts.end(), row, row + s);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+pg_status pg_batch_create(pg_batch **out) {
+  if (!out) return PG_EINVAL;
+  *out = new pg_batch();
+  return PG_OK;
+}
+
+void pg_batch_free(pg_batch *b) {
+  if (!b) return;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    free_groups(b);
+  }
+  delete b;
+}
+
+pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, int64_t n,
+                       int64_t m, int directed, const int32_t *seeds, int32_t s,
+                       int32_t *index) {
+  if (!b || !row_ptr || (m > 0 && !col) || !seeds || n < 1 || m < 0 || s < 1 || s > n ||
+      n >= 0x7FFFFFFFLL || row_ptr[0] != 0 || row_ptr[n] != m)
+    return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  pg_batch::Item it;
+  it.row_ptr.assign(row_ptr, row_ptr + n + 1);
+  it.col.assign(col, col + m);
+  it.seeds.assign(seeds, seeds + s);
+  for (int32_t x : it.seeds)
+    if (x < 0 || x >= n) return PG_EINVAL;
+  std::vector<int32_t> sorted(it.seeds);
+  std::sort(sorted.begin(), sorted.end());
+  for (size_t i = 1; i < sorted.size(); ++i)
+    if (sorted[i] == sorted[i - 1]) return PG_EINVAL;
+  it.n = n;
+  it.m = m;
+  it.directed = directed ? 1 : 0;
+  b->items.push_back(std::move(it));
+  if (b->built) free_groups(b);  // regrouped on the next run
+  if (index) *index = (int32_t)b->items.size() - 1;
+  return PG_OK;
+}
+
+pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
+  if (!b) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->items.empty()) return PG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  pg_status rc = PG_OK;
+  if (!b->built && (rc = build_groups(b, st))) {
+    free_groups(b);
+    return rc;
+  }
+  pg_batch_stats bs{};
+  bs.graphs = (int32_t)b->items.size();
+  bs.groups = (int32_t)b->groups.size();
+  for (auto &gr : b->groups) {
+    for (int32_t k : gr.members) {
+      auto &it = b->items[k];
+      it.counts.clear();
+      it.rounds = -1;
+      it.open = true;
+    }
+    SinkCtx ctx{b, &gr};
+    int32_t T = 0;
+    pg_stats st1{};
+    rc = propagate_batch_group(gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
+                               (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
+                               (const int32_t *)gr.graph_col0.p, gr.ncols, gr.s_bits,
+                               gr.max_rounds, &take_window, &ctx, &T, opt, stream, &st1);
+    if (rc) {
+      for (auto &it : b->items) {
+        it.counts.clear();
+        it.rounds = -1;
+      }
+      return rc;
+    }
+    bs.seed_edge_traversals += st1.seed_edge_traversals;
+    bs.sweeps = std::max(bs.sweeps, st1.sweeps);
+    bs.launches += st1.launches;
+    for (int32_t k : gr.members) {
+      auto &it = b->items[k];
+      it.rounds = (int32_t)(it.counts.size() / it.seeds.size()) - 1;
+    }
+  }
+  b->stats = bs;
+  return PG_OK;
+}
+
+pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out) {
+  if (!b || !out || !out->counts) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (index < 0 || index >= (int32_t)b->items.size()) return PG_EINVAL;
+  const auto &it = b->items[index];
+  if (it.rounds < 0 || out->s != (int32_t)it.seeds.size()) return PG_EINVAL;
+  const int32_t rows = std::min(it.rounds, out->max_rounds) + 1;
+  std::memcpy(out->counts, it.counts.data(), sizeof(uint32_t) * (size_t)rows * out->s);
+  out->rounds = it.rounds;
+  if (out->m_active) std::memset(out->m_active, 0, sizeof(uint64_t) * ((size_t)out->max_rounds + 2));
+  return it.rounds > out->max_rounds ? PG_ERANGE : PG_OK;
+}
+
+pg_status pg_batch_get_stats(pg_batch *b, pg_batch_stats *out) {
+  if (!b || !out) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  *out = b->stats;
+  return PG_OK;
+}
+
+}  // extern "C"

@@ -43,6 +43,7 @@ struct Ctrl {
 
 // Per-round work counters (device), indexed by round.
 struct RoundStats {
+  unsigned long long work;     // sum over active rows of s_graph(v) * indeg(v)
   unsigned long long m_active;
   unsigned long long scanned;
   unsigned long long gathered;
@@ -79,13 +80,18 @@ struct Params {
   int64_t nPall;
   int32_t L;            // in-arcs per work piece
   int32_t LE;           // out-arcs per expansion piece
-  uint32_t *counts;     // counts window [row_cap][s] of this pass
+  uint32_t *counts;     // counts window [row_cap][ncols] of this pass
+  int32_t ncols;        // count columns per round (s, or the batch's sum of s_g)
+  const int32_t *node_graph;  // batch of disjoint graphs: graph of each node (else null)
+  const int32_t *graph_s;     // batch: seeds of each graph
+  const int32_t *graph_col0;  // batch: first count column of each graph
   RoundStats *rs;       // [row_cap + 2], slot = round - row_base
   Ctrl *ctrl;
   int32_t max_rounds;
   int32_t direction;
   float dense_threshold;
   int32_t row_cap;      // rows of the device counts window
+  int32_t test_changed; // test C_{t-1} before gathering an in-neighbour's delta
   int32_t use_cond;     // launched inside a conditional while-graph
   int32_t iter_guard;   // post launches after which a pass is abandoned
   unsigned long long cond;  // cudaGraphConditionalHandle of that graph
@@ -107,7 +113,7 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds;
+  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds, seed_bits;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -171,5 +177,14 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st);
 pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st);
 // Drops the CUDA graphs captured for g.
 void drop_graph_cache(pg_graph *g);
+// Receives each copied-out counts window of a batch run.
+typedef void (*WindowSink)(void *ctx, int32_t row_base, int32_t rows, const uint32_t *data,
+                           int32_t ncols);
+pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
+                                int32_t nseeds, const int32_t *node_graph_d,
+                                const int32_t *graph_s_d, const int32_t *graph_col0_d,
+                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
+                                WindowSink sink, void *sink_ctx, int32_t *rounds,
+                                const pg_options *opt, void *stream, pg_stats *st_out);
 
 }  // namespace pg

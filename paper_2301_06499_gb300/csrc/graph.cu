@@ -390,7 +390,7 @@ void pg_graph_free(pg_graph *g) {
     for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len}) release(*b);
     Workspace &w = g->ws;
     for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0, &w.F1, &w.E, &w.A,
-                      &w.counts, &w.rs, &w.ctrl, &w.seeds})
+                      &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits})
       release(*b);
     if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
     for (auto &e : w.ev)

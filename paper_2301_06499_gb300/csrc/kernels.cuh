@@ -43,9 +43,10 @@ __device__ __forceinline__ uint64_t valid_mask(int w, int s) {
   return (1ULL << (s - lo)) - 1ULL;
 }
 
-// 32-byte read-only load (one 256-bit access; p is 32-byte aligned).
+// 32-byte read-only load (one 256-bit access; p is 32-byte aligned). Random
+// gathers do not allocate in L1: they are almost never reused from there.
 __device__ __forceinline__ void ld_nc_256(uint64_t *a, const uint64_t *p) {
-  asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u64 {%0, %1, %2, %3}, [%4];"
                : "=l"(a[0]), "=l"(a[1]), "=l"(a[2]), "=l"(a[3])
                : "l"(p));
 }
@@ -85,33 +86,30 @@ __device__ __forceinline__ void store_words(uint64_t *p, const uint64_t (&a)[CW]
   }
 }
 
-// Block-wide sum of up to 4 counters, then one atomicAdd per counter.
-__device__ __forceinline__ void block_add4(unsigned long long a, unsigned long long b,
-                                           unsigned long long c, unsigned long long d,
-                                           unsigned long long *pa, unsigned long long *pb,
-                                           unsigned long long *pc, unsigned long long *pd) {
-  __shared__ unsigned long long red[4][kBlock / 32];
+// Block-wide sums of N counters, then one atomicAdd per nonzero counter.
+template <int N>
+__device__ __forceinline__ void block_add(const unsigned long long (&v)[N],
+                                          unsigned long long *const (&dst)[N]) {
+  __shared__ unsigned long long red[N][kBlock / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    a += __shfl_xor_sync(kFullMask, a, off);
-    b += __shfl_xor_sync(kFullMask, b, off);
-    c += __shfl_xor_sync(kFullMask, c, off);
-    d += __shfl_xor_sync(kFullMask, d, off);
-  }
-  if (lane == 0) {
-    red[0][w] = a;
-    red[1][w] = b;
-    red[2][w] = c;
-    red[3][w] = d;
+  for (int k = 0; k < N; ++k) {
+    unsigned long long x = v[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFullMask, x, off);
+    if (lane == 0) red[k][w] = x;
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < N) {
     unsigned long long s = 0;
     for (int k = 0; k < kBlock / 32; ++k) s += red[threadIdx.x][k];
-    unsigned long long *dst = threadIdx.x == 0 ? pa : threadIdx.x == 1 ? pb : threadIdx.x == 2 ? pc : pd;
-    if (s && dst) atomicAdd(dst, s);
+    if (s && dst[threadIdx.x]) atomicAdd(dst[threadIdx.x], s);
   }
+}
+
+// Seeds of the graph node v belongs to (a batch of disjoint graphs), else s.
+__device__ __forceinline__ int seeds_of(const Params &p, int32_t v) {
+  return p.node_graph ? __ldg(p.graph_s + __ldg(p.node_graph + v)) : p.s;
 }
 
 __device__ __forceinline__ unsigned long long warp_excl_scan64(unsigned long long x, int lane,
@@ -238,17 +236,32 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
   return changed;
 }
 
+// Tuning knobs (compile-time): minimum resident blocks per SM for the pull
+// kernel (caps registers) and arcs per lane per step of the dense sweep.
+#ifndef PG_PULL_MIN_BLOCKS
+#define PG_PULL_MIN_BLOCKS 3
+#endif
+#ifndef PG_DENSE_UNROLL_NARROW
+#define PG_DENSE_UNROLL_NARROW 8
+#endif
+#ifndef PG_DENSE_UNROLL_WIDE
+#define PG_DENSE_UNROLL_WIDE 4
+#endif
+
 // Dense round over the sliced-ELL copy: a warp per chunk of 32 pieces, lane
 // l owns piece l; step k reads arc k of all 32 pieces in one coalesced load,
 // and the U deltas of a lane's U steps are gathered together.
 template <int CW>
 __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const uint64_t *Dprev,
-                                           int32_t *F, uint32_t *Ccur, uint32_t *Kcur, int lane,
+                                           const uint32_t *Cprev, int32_t *F, uint32_t *Ccur,
+                                           uint32_t *Kcur, int lane,
                                            int64_t warp, int64_t nwarps,
                                            unsigned long long &my_mact,
+                                           unsigned long long &my_work,
                                            unsigned long long &my_scan,
+                                           unsigned long long &my_gath,
                                            unsigned long long &my_items) {
-  constexpr int U = CW <= 2 ? 8 : 4;
+  constexpr int U = CW <= 2 ? PG_DENSE_UNROLL_NARROW : PG_DENSE_UNROLL_WIDE;
   const size_t Wp = (size_t)p.Wp;
   const int nch = p.Wp / CW;
   for (int64_t c = warp; c < p.sell_chunks; c += nwarps) {
@@ -273,9 +286,17 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
         int32_t u[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) u[q] = (act && k0 + q < len) ? __ldg(cc + 32LL * (k0 + q)) : -1;
+        if (p.test_changed) {
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+            if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
+        }
 #pragma unroll
         for (int q = 0; q < U; ++q)
-          if (u[q] >= 0) or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
+          if (u[q] >= 0) {
+            or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
+            if (ch == 0) ++my_gath;
+          }
       }
 #pragma unroll
       for (int k = 0; k < CW; ++k) any_delta |= acc[k] != 0ULL;
@@ -283,10 +304,13 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
     }
     act = act && any_delta;  // no changed in-neighbour: not active in round t
     if (act) {
+      unsigned long long deg = 0;
       if (whole)
-        my_mact += (unsigned long long)len;
+        deg = (unsigned long long)len;
       else if (!set_bit(Kcur, v))
-        my_mact += (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        deg = (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+      my_mact += deg;
+      my_work += deg * (unsigned long long)seeds_of(p, v);
     }
     bool app = false;
     if (act && row_changed) {
@@ -322,8 +346,12 @@ struct PullUnroll {
 // node is revisited in round t when it still has a zero bit (not saturated)
 // and some in-neighbour changed in round t-1 (a nonzero delta). Sparse rounds
 // count it when the row is claimed.
+//
+// With p.test_changed, an in-neighbour's changed bit (C_{t-1}, n bits, kept in
+// L2) is tested before its delta is gathered, so unchanged neighbours cost no
+// signature-sized read: worth it when the deltas are far larger than L2.
 template <int CW, int G>
-__global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
+__global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
   constexpr int UNR = PullUnroll<CW>::value;
   constexpr int GPW = 32 / G;
   Ctrl *ctrl = p.ctrl;
@@ -331,6 +359,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
   const int t = ctrl->t;
   const bool dense = ctrl->mode == kModeDense;
   const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
+  const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
   int32_t *F = (t & 1) ? p.F1 : p.F0;
   uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
   uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
@@ -343,10 +372,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
-  unsigned long long my_mact = 0, my_scan = 0, my_items = 0;
+  unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
   if (dense) {
-    pull_dense<CW>(p, ctrl, Dprev, F, Ccur, Kcur, lane, warp, nwarps, my_mact, my_scan,
-                   my_items);
+    pull_dense<CW>(p, ctrl, Dprev, Cprev, F, Ccur, Kcur, lane, warp, nwarps, my_mact, my_work,
+                   my_scan, my_gath, my_items);
   } else {
     const int gl = lane & (G - 1);
     const int gw = lane / G;
@@ -377,6 +406,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
         const int j = gl + q * G;
         u[q] = (act && j < len) ? __ldg(p.col + b + j) : -1;
       }
+      if (p.test_changed) {
+#pragma unroll
+        for (int q = 0; q < UNR; ++q)
+          if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
+      }
       bool row_changed = false;
       for (int c = 0; c < nch; ++c) {
         uint64_t own[CW], acc[CW];
@@ -385,7 +419,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
         if (act && gl == 0 && whole) load_words<CW>(own, p.X + (size_t)v * Wp + c * CW);
 #pragma unroll
         for (int q = 0; q < UNR; ++q)
-          if (u[q] >= 0) or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
+          if (u[q] >= 0) {
+            or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
+            if (c == 0) ++my_gath;
+          }
 #pragma unroll
         for (int off = G >> 1; off > 0; off >>= 1) {
 #pragma unroll
@@ -406,9 +443,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_pull(Params p) {
     }
   }
   RoundStats *r = p.rs + (t - ctrl->row_base);
-  // every scanned arc's delta is gathered, so `gathered` equals `scanned`
-  block_add4(my_mact, my_scan, my_scan, my_items, &r->m_active, &r->scanned, &r->gathered,
-             &r->items);
+  const unsigned long long vals[5] = {my_mact, my_work, my_scan, my_gath, my_items};
+  unsigned long long *const dsts[5] = {&r->m_active, &r->work, &r->scanned, &r->gathered,
+                                       &r->items};
+  block_add<5>(vals, dsts);
 }
 
 using PullFn = void (*)(Params);

@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
 // change of round 0 (X = 0, Y = the bit), so the post kernel of round 0
 // counts the pairs (x_i, x_i), records the seeds' deltas and expands them
 // like any other frontier.
-__global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds, int sp) {
+__global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
+                                               const int32_t *seed_bit, int sp) {
   __shared__ unsigned long long tot;
   if (threadIdx.x == 0) tot = 0ULL;
   __syncthreads();
@@ -88,7 +89,8 @@ __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds, i
     const bool ok = i < sp;
     if (ok) {
       x = seeds[i];
-      p.Y[(size_t)x * p.Wp + (i >> 6)] = 1ULL << (i & 63);
+      const int bit = seed_bit ? seed_bit[i] : i;  // a batch: the seed's index in its graph
+      p.Y[(size_t)x * p.Wp + (bit >> 6)] = 1ULL << (bit & 63);
       set_bit(p.C0, x);
       p.F0[i] = x;
       od = (unsigned long long)(p.out_ptr[x + 1] - p.out_ptr[x]);
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5, nwarps = nth >> 5;
   const int Wp = p.Wp, s = p.s;
-  uint32_t *crow = p.counts + (size_t)row * (size_t)s;
+  uint32_t *crow = p.counts + (size_t)row * (size_t)p.ncols;
 
   if (SMEM) {
     for (int i = threadIdx.x; i < s; i += kBlock) scnt[i] = 0u;
@@ -179,6 +181,17 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     uint64_t *xr = p.X + (size_t)v * Wp;
     const uint64_t *yr = p.Y + (size_t)v * Wp;
     uint64_t *dr = Dcur + (size_t)v * Wp;
+    // a batch of disjoint graphs: bit i of a node is its own graph's seed i
+    int sv = s, c0v = 0, gid = -1;
+    if (p.node_graph && valid) {
+      gid = p.node_graph[v];
+      sv = p.graph_s[gid];
+      c0v = p.graph_col0[gid];
+    }
+    const int gid0 = __shfl_sync(kFullMask, gid, 0);
+    const bool one_graph = !p.node_graph || __all_sync(kFullMask, !valid || gid == gid0);
+    const int c0w = __shfl_sync(kFullMask, c0v, 0);
+    const int sw = __shfl_sync(kFullMask, sv, 0);
     bool full = valid;
     for (int w = 0; w < Wp; ++w) {
       uint64_t o = 0, nw = 0;
@@ -191,25 +204,32 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
         xr[w] = nw;
         dr[w] = d;
       }
-      full = full && ((nw | ~valid_mask(w, s)) == ~0ULL);
-      if (__any_sync(kFullMask, d != 0ULL)) {
-        const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
-        const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
-        const int c0 = w * 64 + lane;
-        if (n0) {
-          if (SMEM)
-            atomicAdd(&scnt[c0], n0);
-          else
-            atomicAdd(&crow[c0], n0);
+      full = full && ((nw | ~valid_mask(w, sv)) == ~0ULL);
+      if (one_graph) {
+        if (__any_sync(kFullMask, d != 0ULL)) {
+          const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+          const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+          const int c0 = w * 64 + lane;
+          if (n0) {
+            if (SMEM)
+              atomicAdd(&scnt[c0], n0);
+            else
+              atomicAdd(&crow[c0w + c0], n0);
+          }
+          if (n1) {
+            if (SMEM)
+              atomicAdd(&scnt[c0 + 32], n1);
+            else
+              atomicAdd(&crow[c0w + c0 + 32], n1);
+          }
         }
-        if (n1) {
-          if (SMEM)
-            atomicAdd(&scnt[c0 + 32], n1);
-          else
-            atomicAdd(&crow[c0 + 32], n1);
-        }
+      } else {
+        // rows of several graphs in this warp: count bit by bit
+        for (uint64_t r = d; r; r &= r - 1ULL)
+          atomicAdd(&crow[c0v + w * 64 + __ffsll((long long)r) - 1], 1u);
       }
     }
+    (void)sw;
     if (full) set_bit(p.Sat, v);
   }
   // the deltas of round t-1 were read by the pull of round t: clear them
@@ -231,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
       p.direction == PG_DIR_DENSE ||
       (p.direction == PG_DIR_AUTO && (double)fsum > (double)p.dense_threshold * (double)p.m);
   const bool expand = !next_dense && nF > 0 && t + 1 <= p.max_rounds + 1;
-  unsigned long long my_mact = 0;
+  unsigned long long my_mact = 0, my_work = 0;
   if (expand) {
     // one thread per expansion piece of LE out-arcs, UNR arcs at a time
     constexpr int UNR = 4;
@@ -257,7 +277,9 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
 #pragma unroll
         for (int q = 0; q < UNR; ++q)
           cand[q] = x[q] >= 0 && !test_bit_live(p.Sat, x[q]) &&
-                    !(test_bit(Ccur, x[q]) && row_full(p.Y + (size_t)x[q] * Wp, Wp, s));
+                    !(test_bit(Ccur, x[q]) &&
+                      row_full(p.Y + (size_t)x[q] * Wp, Wp,
+                               p.node_graph ? p.graph_s[p.node_graph[x[q]]] : s));
         bool claim[UNR];
 #pragma unroll
         for (int q = 0; q < UNR; ++q) claim[q] = cand[q] && !set_bit(Knext, x[q]);
@@ -269,6 +291,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
             rb = __ldg(p.row_ptr + x[q]);
             indeg = __ldg(p.row_ptr + x[q] + 1) - rb;
             my_mact += (unsigned long long)indeg;
+            my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
             np = (unsigned long long)((indeg + p.L - 1) / p.L);
           }
           warp_append_items(p.A, &ctrl->nA_next, x[q], rb, indeg, p.L, np, lane);
@@ -277,7 +300,11 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     }
   }
   RoundStats *rnext = p.rs + row + 1;
-  block_add4(my_mact, 0ULL, 0ULL, 0ULL, &rnext->m_active, nullptr, nullptr, nullptr);
+  {
+    const unsigned long long vals[2] = {my_mact, my_work};
+    unsigned long long *const dsts[2] = {&rnext->m_active, &rnext->work};
+    block_add<2>(vals, dsts);
+  }
 
   // C. last block hands over
   __shared__ int am_last;
@@ -430,15 +457,26 @@ struct Call {
   uint32_t *counts_h;            // caller rows x s_total
   std::vector<RoundStats> rs_h;  // summed over passes, grown as rounds complete
   int32_t row_cap = 0;
+  WindowSink sink = nullptr;
+  void *sink_ctx = nullptr;
+  std::vector<uint32_t> stage;
 };
 
 static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_base, int32_t rows,
                              int32_t rs_rows) {
   rows = std::min(rows, cl.max_rounds + 1 - row_base);
-  if (rows > 0) {
+  if (rows > 0 && cl.sink) {
+    cl.stage.resize((size_t)rows * p.ncols);
+    cudaError_t e = cudaMemcpyAsync(cl.stage.data(), p.counts,
+                                    sizeof(uint32_t) * (size_t)rows * p.ncols,
+                                    cudaMemcpyDeviceToHost, cl.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cl.st);
+    if (e != cudaSuccess) return cuda_status(e);
+    cl.sink(cl.sink_ctx, row_base, rows, cl.stage.data(), p.ncols);
+  } else if (rows > 0) {
     cudaError_t e = cudaMemcpy2DAsync(cl.counts_h + (size_t)row_base * cl.s_total + col0,
                                       sizeof(uint32_t) * cl.s_total, p.counts,
-                                      sizeof(uint32_t) * p.s, sizeof(uint32_t) * p.s, rows,
+                                      sizeof(uint32_t) * p.ncols, sizeof(uint32_t) * p.ncols, rows,
                                       cudaMemcpyDeviceToHost, cl.st);
     if (e != cudaSuccess) return cuda_status(e);
   }
@@ -453,6 +491,7 @@ static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_ba
       cl.rs_h.resize((size_t)row_base + rs_rows, RoundStats{});
     for (int i = 0; i < rs_rows; ++i) {
       RoundStats &d = cl.rs_h[(size_t)row_base + i];
+      d.work += tmp[i].work;
       d.m_active += tmp[i].m_active;
       d.scanned += tmp[i].scanned;
       d.gathered += tmp[i].gathered;
@@ -565,15 +604,32 @@ void drop_graph_cache(pg_graph *g) {
     }
 }
 
-// One pass: sp seeds of the call, columns [col0, col0+sp).
+// A batch of disjoint graphs packed into one graph (see pg_batch_run).
+struct BatchSeg {
+  const int32_t *node_graph;  // device, graph of each node
+  const int32_t *graph_s;     // device, seeds of each graph
+  const int32_t *graph_col0;  // device, first count column of each graph
+  const int32_t *seed_bit;    // host, each seed's index within its graph
+  int32_t ncols;              // count columns (sum of the graphs' seeds)
+  int32_t s_bits;             // most seeds of one graph (bits per node)
+};
+
+// One pass: sp seeds of the call, columns [col0, col0+sp); or, with bs, all
+// seeds of a packed batch.
 static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bool eb,
-                          int hint, PassOut &po) {
+                          int hint, PassOut &po, const BatchSeg *bs = nullptr) {
   pg_graph *g = cl.g;
   Workspace &w = g->ws;
   cudaStream_t st = cl.st;
   Plan pl;
-  pg_status rc = make_plan(g, sp, cl.o, eb, pl);
+  const int s_bits = bs ? bs->s_bits : sp;
+  const int ncols = bs ? bs->ncols : sp;
+  pg_status rc = make_plan(g, s_bits, cl.o, eb, pl);
   if (rc) return rc;
+  if (bs) {
+    pl.smem_counts = false;  // a batch's columns exceed one block's counters
+    pl.post_smem = 0;
+  }
   rc = ensure_pieces(g, pl.L, st);
   if (rc) return rc;
   if (cl.o.direction != PG_DIR_SPARSE && (rc = ensure_sell(g, kSellPiece, st))) return rc;
@@ -590,9 +646,10 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   if ((rc = ensure(w.F0, sizeof(int32_t) * n)) || (rc = ensure(w.F1, sizeof(int32_t) * n)) ||
       (rc = ensure(w.E, sizeof(unsigned long long) * e_cap)) ||
       (rc = ensure(w.A, sizeof(ulonglong2) * std::max<int64_t>(g->pieces.count, 1))) ||
-      (rc = ensure(w.counts, sizeof(uint32_t) * (size_t)row_cap * sp)) ||
+      (rc = ensure(w.counts, sizeof(uint32_t) * (size_t)row_cap * ncols)) ||
       (rc = ensure(w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2))) ||
-      (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)))
+      (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)) ||
+      (bs && (rc = ensure(w.seed_bits, sizeof(int32_t) * sp))))
     return rc;
   if (!w.ctrl_h) {
     if (cudaMallocHost((void **)&w.ctrl_h, 2 * sizeof(Ctrl)) != cudaSuccess) {
@@ -614,7 +671,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.D0 = (uint64_t *)w.D0.p;
   p.D1 = (uint64_t *)w.D1.p;
   p.Wp = pl.Wp;
-  p.s = sp;
+  p.s = s_bits;
   p.C0 = (uint32_t *)w.C0.p;
   p.C1 = (uint32_t *)w.C1.p;
   p.K0 = (uint32_t *)w.K0.p;
@@ -635,12 +692,20 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.L = pl.L;
   p.LE = kExpandArcs;
   p.counts = (uint32_t *)w.counts.p;
+  p.ncols = ncols;
+  p.node_graph = bs ? bs->node_graph : nullptr;
+  p.graph_s = bs ? bs->graph_s : nullptr;
+  p.graph_col0 = bs ? bs->graph_col0 : nullptr;
   p.rs = (RoundStats *)w.rs.p;
   p.ctrl = (Ctrl *)w.ctrl.p;
   p.max_rounds = cl.max_rounds;
   p.row_cap = row_cap;
   p.direction = cl.o.direction;
   p.dense_threshold = cl.o.dense_threshold > 0 ? cl.o.dense_threshold : 0.05f;
+  // gather deltas unconditionally while they stay mostly in L2; beyond that,
+  // test the (L2-resident) changed bitmap first
+  const int64_t delta_bytes = n * (int64_t)pl.Wp * 8;
+  p.test_changed = cl.o.test_changed == 1 || (cl.o.test_changed == 0 && delta_bytes > (64LL << 20));
   p.use_cond = 0;
   p.cond = 0ULL;
   p.iter_guard = cl.max_rounds + 2;
@@ -673,13 +738,17 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   rc = cuda_status(cudaMemcpyAsync(w.seeds.p, seeds_h, sizeof(int32_t) * sp,
                                    cudaMemcpyHostToDevice, st));
+  if (rc == PG_OK && bs)
+    rc = cuda_status(cudaMemcpyAsync(w.seed_bits.p, bs->seed_bit, sizeof(int32_t) * sp,
+                                     cudaMemcpyHostToDevice, st));
   if (rc) return rc;
-  const int64_t count_words = (int64_t)row_cap * sp;
+  const int64_t count_words = (int64_t)row_cap * ncols;
   const int64_t rs_words = (int64_t)(row_cap + 2) * (int64_t)(sizeof(RoundStats) / 8);
   const int64_t zero_work = std::max<int64_t>({n * pl.Wp / 2, nbm, count_words, rs_words, 1});
   k_zero<<<occupancy_grid((const void *)&k_zero, 0, zero_work), kBlock, 0, st>>>(p, count_words,
                                                                                 rs_words);
-  k_seed<<<1, 1024, 0, st>>>(p, (const int32_t *)w.seeds.p, sp);
+  k_seed<<<1, 1024, 0, st>>>(p, (const int32_t *)w.seeds.p,
+                             bs ? (const int32_t *)w.seed_bits.p : nullptr, sp);
   if (pl.smem_counts)
     k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
   else
@@ -922,6 +991,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   for (int32_t t = 0; t <= last_stats; ++t) {
     const RoundStats &r = cl.rs_h[t];
     st.m_active_total += r.m_active;
+    st.seed_edge_traversals += r.work;
     st.arcs_scanned += r.scanned;
     st.rows_gathered += r.gathered;
     st.items += r.items;
@@ -934,8 +1004,65 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   make_plan(g, std::min(planes, s), cl.o, s_mode, pl);
   st.words_per_row = pl.Wp;
   st.group_lanes = pl.G;
+  st.test_changed = cl.o.test_changed == 1 ||
+                    (cl.o.test_changed == 0 && g->n * (int64_t)pl.Wp * 8 > (64LL << 20));
   g->last = st;
   return status == PG_ERANGE ? PG_ERANGE : PG_OK;
+}
+
+// Runs one packed batch (see batch.cu): all seeds of all graphs in one pass;
+// each copied counts window goes to the caller's sink.
+pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
+                                int32_t nseeds, const int32_t *node_graph_d,
+                                const int32_t *graph_s_d, const int32_t *graph_col0_d,
+                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
+                                WindowSink sink, void *sink_ctx, int32_t *rounds,
+                                const pg_options *opt, void *stream, pg_stats *st_out) {
+  if (!g || !seeds || !seed_bit || nseeds < 1 || ncols < 1 || s_bits < 1 || max_rounds < 0 ||
+      !sink)
+    return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(g->mu);
+  Call cl;
+  cl.g = g;
+  cl.st = (cudaStream_t)stream;
+  pg_default_options(&cl.o);
+  if (opt) cl.o = *opt;
+  cl.s_total = ncols;
+  cl.max_rounds = max_rounds;
+  cl.counts_h = nullptr;
+  cl.sink = sink;
+  cl.sink_ctx = sink_ctx;
+  int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ncols));
+  if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
+  cl.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
+  BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits};
+  PassOut po;
+  pg_status rc = run_pass(cl, seeds, nseeds, 0, false, g->hint_p, po, &bs);
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  if (po.status == PG_OK) g->hint_p = std::min(po.rounds + 1, 64);
+  *rounds = po.rounds;
+  pg_stats st{};
+  const int32_t last_stats = std::min(po.rounds + 1, max_rounds + 1);
+  if (cl.rs_h.size() < (size_t)last_stats + 1) cl.rs_h.resize((size_t)last_stats + 1, RoundStats{});
+  for (int32_t t = 0; t <= last_stats; ++t) {
+    const RoundStats &r = cl.rs_h[t];
+    st.m_active_total += r.m_active;
+    st.seed_edge_traversals += r.work;
+    st.arcs_scanned += r.scanned;
+    st.rows_gathered += r.gathered;
+    st.items += r.items;
+    st.changed_rows += r.changed;
+  }
+  st.sweeps = po.rounds + 1;
+  st.passes = 1;
+  st.launches = po.launches;
+  st.dense_rounds = po.dense_rounds;
+  g->last = st;
+  if (st_out) *st_out = st;
+  return po.status == PG_ERANGE ? PG_ERANGE : PG_OK;
 }
 
 }  // namespace pg
@@ -950,6 +1077,7 @@ void pg_default_options(pg_options *o) {
   o->direction = PG_DIR_AUTO;
   o->dense_threshold = 0.05f;
   o->group_lanes = 0;
+  o->test_changed = 0;
   o->planes_per_pass = 64;
   o->use_graphs = 1;
   o->timing = 0;

@@ -1,0 +1,137 @@
+"""Batched PROPAGATE-P (pg_batch_*): every graph's per-round, per-seed counts
+in a batch are bit-exact with the oracle and with the same graph run alone
+through pg_propagate_p; the batch is credited exactly the work of the plain
+runs (the work measure is defined by the method, not the schedule)."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2301_06499_gb300 as pg
+from paper_2301_06499_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def _mix():
+    # sizes log-uniform in [500, 20000], every generator and width class
+    return I.mix(24, 500, 20_000, 4)
+
+
+def _width_class(s):
+    w = (s + 63) // 64
+    return w if w <= 2 else 4 if w <= 4 else -(-w // 8) * 8
+
+
+def _plain(item):
+    G = pg.Graph.from_inputs(item.graph)
+    res = pg.propagate_p(G, item.seeds)
+    st = G.last_stats()
+    G.close()
+    return res, st["seed_edge_traversals"]
+
+
+def test_mix_covers_every_width_class():
+    widths = {(it.s + 63) // 64 for it in _mix()}
+    assert {1, 2}.issubset(widths) and any(w > 2 for w in widths)
+    kinds = {it.graph.name.split("_")[0].rstrip("du") for it in _mix()}
+    assert len(kinds) == 3, kinds
+
+
+def test_batch_equals_plain_and_oracle():
+    items = _mix()
+    with pg.Batch() as b:
+        idx = [b.add_inputs(it.graph, it.seeds) for it in items]
+        b.run()
+        st = b.stats()
+        plain_work = 0
+        for k, it in zip(idx, items):
+            got = b.result(k)
+            want, work = _plain(it)
+            plain_work += work
+            assert got.rounds == want.rounds, (it.graph.name, got.rounds, want.rounds)
+            assert np.array_equal(got.counts, want.counts), it.graph.name
+        assert st["graphs"] == len(items)
+        assert st["groups"] == len({_width_class(it.s) for it in items})
+        assert st["seed_edge_traversals"] == plain_work
+    for it in items[:6]:  # the oracle directly, on a few graphs
+        want = oracle.run(it.graph, it.seeds)
+        with pg.Batch() as b1:
+            b1.add_inputs(it.graph, it.seeds)
+            b1.run()
+            got = b1.result(0)
+        assert got.rounds == want["rounds"]
+        assert np.array_equal(got.counts, want["counts"])
+
+
+def test_batch_result_independent_of_company():
+    """A graph's counts are the same alone, in a batch, and in a batch in a
+    different order (no bit crosses between packed graphs)."""
+    items = _mix()[:10]
+    runs = []
+    for order in (list(range(10)), list(range(9, -1, -1))):
+        with pg.Batch() as b:
+            pos = {k: b.add_inputs(items[k].graph, items[k].seeds) for k in order}
+            b.run()
+            runs.append({k: b.result(pos[k]) for k in order})
+    for k in range(10):
+        assert runs[0][k].rounds == runs[1][k].rounds
+        assert np.array_equal(runs[0][k].counts, runs[1][k].counts)
+
+
+def test_batch_edge_cases():
+    """Isolated nodes, a single-node graph, a long path (many more rounds
+    than its company), s = n, and a rerun after adding a graph."""
+    p = I.path(300, directed=True)
+    lone = I.from_arcs(1, [], [])
+    iso = I.from_arcs(50, [0, 1], [1, 2])
+    k5 = I.complete(5)
+    cases = [(p, np.array([0, 150, 299], np.int32)), (lone, np.array([0], np.int32)),
+             (iso, I.seeds(50, 50, 9)), (k5, np.arange(5, dtype=np.int32))]
+    with pg.Batch() as b:
+        for g, sd in cases:
+            b.add_inputs(g, sd)
+        b.run()
+        for k, (g, sd) in enumerate(cases):
+            want = oracle.run(g, sd)
+            got = b.result(k)
+            assert got.rounds == want["rounds"], g.name
+            assert np.array_equal(got.counts, want["counts"]), g.name
+        g2 = I.cycle(40)
+        k2 = b.add_inputs(g2, np.array([3, 17], np.int32))
+        b.run()
+        want = oracle.run(g2, np.array([3, 17], np.int32))
+        assert np.array_equal(b.result(k2).counts, want["counts"])
+        assert np.array_equal(b.result(0).counts, oracle.run(p, cases[0][1])["counts"])
+
+
+def test_batch_wide_signatures():
+    """A width class above 8 words (s = 600 -> 10 words, padded to 16)."""
+    g = I.er(3000, 6, 11)
+    sd = I.seeds(g.n, 600, 12)
+    g2 = I.grid(40, 40, 0.05, 13)
+    sd2 = I.seeds(g2.n, 520, 14)
+    with pg.Batch() as b:
+        b.add_inputs(g, sd)
+        b.add_inputs(g2, sd2)
+        b.run()
+        assert b.stats()["groups"] == 1
+        for k, (gg, ss) in enumerate(((g, sd), (g2, sd2))):
+            want = oracle.run(gg, ss)
+            assert np.array_equal(b.result(k).counts, want["counts"])
+
+
+def test_batch_rejects_bad_input():
+    with pg.Batch() as b:
+        g = I.er(100, 4, 1)
+        with pytest.raises(pg.PropagateError):
+            b.add_inputs(g, np.array([1, 1], np.int32))  # duplicate seed
+        with pytest.raises(pg.PropagateError):
+            b.add_inputs(g, np.array([100], np.int32))  # out of range
+        with pytest.raises(pg.PropagateError):
+            b.run()  # empty batch
+        k = b.add_inputs(g, np.array([0, 5], np.int32))
+        with pytest.raises(pg.PropagateError):
+            b.result(k)  # no run yet

@@ -69,10 +69,11 @@ def test_cfg1_er_propagate_p_default():
 
 @pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
-def test_cfg1_every_schedule_identical(direction, lanes):
+@pytest.mark.parametrize("test_changed", [1, 2])
+def test_cfg1_every_schedule_identical(direction, lanes, test_changed):
     g, seeds, want = _cfg1()
     G = pg.Graph.from_inputs(g)
-    o = pg.options(direction=direction, group_lanes=lanes)
+    o = pg.options(direction=direction, group_lanes=lanes, test_changed=test_changed)
     _assert_same(pg.propagate_p(G, seeds, opts=o), want)
 
 
@@ -119,7 +120,9 @@ def test_directed_rmat(scale, ef, s):
     want = _oracle_p(g, seeds)
     G = pg.Graph.from_inputs(g)
     for d in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
-        _assert_same(pg.propagate_p(G, seeds, opts=pg.options(direction=d)), want)
+        for tc in (1, 2):
+            o = pg.options(direction=d, test_changed=tc)
+            _assert_same(pg.propagate_p(G, seeds, opts=o), want)
     res_s = pg.propagate_s(G, seeds)
     _assert_same(res_s, want, check_mactive=False)
 
