@@ -58,6 +58,15 @@ BATCH_WORKLOADS = {
     "mix512_batched": (512, 1e3, 1e6, 4),
     "mix64_batched": (64, 1e3, 1e5, 4),
 }
+# Serving workload: a resident pool of 64 graphs of the batched mix plus ER
+# graphs uploaded while serving (n = 2e6 and 1e6); per request eps in
+# {0.05, 0.1, 0.2} sets s = ceil(ln n / eps^2) rounded up to a multiple of 64.
+SERVE_WORKLOADS = {
+    "serve_mix64": dict(pool=64, n_lo=1e3, n_hi=1e6, seed=4,
+                        uploads=((2_000_000, 8.0, 5), (1_000_000, 16.0, 6)),
+                        rates=(200.0, 2000.0), duration=4.0, max_requests=1000, burst=600,
+                        variants=4),
+}
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
             "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2}
 
@@ -368,12 +377,22 @@ def run_batch(args):
         return res, work, launches
 
     def batched():
-        batch.run(opts=opts, stream=sptr)
+        batch.run(opts=None if args.tune else opts, stream=sptr)
         return batch.stats()
 
     t0 = time.perf_counter()
-    batched()  # packs the graphs (host union + upload), untimed
+    batch.run(opts=opts, stream=sptr)  # packs the graphs (host union + upload), untimed
     pack_s = time.perf_counter() - t0
+    tune = None
+    if args.tune:  # the autotuner picks each width class's schedule, untimed
+        t0 = time.perf_counter()
+        tune = batch.tune(max_trials=args.tune_trials, stream=sptr)
+        tune["tune_s"] = time.perf_counter() - t0
+        tune["classes"] = [{"graphs": ng, "words_per_thread": o["words_per_thread"],
+                            "group_lanes": o["group_lanes"],
+                            "dense_threshold": round(o["dense_threshold"], 3),
+                            "test_changed": o["test_changed"]}
+                           for ng, o in batch.group_options()]
     for _ in range(args.warmup):
         res_p, work, plain_launches = plain()
         bst = batched()
@@ -446,6 +465,7 @@ def run_batch(args):
         "plain": {"value": plain_value, "ms_per_step": p_total / args.steps,
                   "gpu_launches": int(plain_launches)},
         "batched_over_plain": plain_value and value / plain_value,
+        "autotune": tune,
         "roofline": None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / len(e2e_ms)},
@@ -456,6 +476,204 @@ def run_batch(args):
         print(json.dumps(out), flush=True)
     batch.close()
     for G in graphs:
+        G.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _serve_requests(count, n_graphs, seed, variants, upload_at=None):
+    """count requests: (graph index, eps, variant), graph uniform over the
+    graphs available (uploaded graphs join at their index in upload_at)."""
+    from paper_2301_06499_gb300 import inputs as I
+    out = []
+    for k in range(count):
+        avail = n_graphs if upload_at is None else upload_at(k)
+        gi = int(I.rand(seed, 40, k) % avail)
+        eps = (0.05, 0.1, 0.2)[I.rand(seed, 41, k) % 3]
+        v = int(I.rand(seed, 42, k) % variants)
+        out.append((gi, eps, v))
+    return out
+
+
+def run_serve(args):
+    """Serving loop (pg_server) against the plain one-request-at-a-time loop
+    (pg_propagate_p per request on resident graphs) over the same request
+    sequence; then open-loop Poisson arrivals with p50/p99 latency. Every
+    served answer is checked against the request run alone. Wall-clock
+    timing (the work spans several streams and threads), bracketed by device
+    synchronisation."""
+    import ctypes
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2301_06499_gb300 as pg
+    from paper_2301_06499_gb300 import inputs as I
+
+    W = SERVE_WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    graphs = [it.graph for it in I.mix(W["pool"], W["n_lo"], W["n_hi"], W["seed"] + 1000 * rank)]
+    uploads = [I.er(n, d, sd + 1000 * rank) for n, d, sd in W["uploads"]]
+    gen_s = time.perf_counter() - t0
+    allg = graphs + uploads
+    V = W["variants"]
+    seed_cache = {}
+
+    def seeds_of(gi, eps, v):
+        key = (gi, eps, v)
+        if key not in seed_cache:
+            n = allg[gi].n
+            s = min(n, I.s_rounded_64(n, eps))
+            seed_cache[key] = I.seeds(n, s, 7_000_003 * gi + 1009 * int(eps * 100) + v)
+        return seed_cache[key]
+
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    handles = [pg.Graph.from_inputs(g, stream=sptr) for g in allg]
+    alone = {}  # (gi, eps, v) -> (counts, rounds, work)
+
+    def run_alone(key):
+        gi, eps, v = key
+        r = pg.propagate_p(handles[gi], seeds_of(*key), stream=sptr)
+        w = handles[gi].last_stats()["seed_edge_traversals"]
+        return r, w
+
+    # closed loop: the same `burst` requests, plain loop vs server
+    burst = _serve_requests(W["burst"], len(allg), W["seed"] + 7, V)
+    for key in set(burst):
+        r, w = run_alone(key)
+        alone[key] = (r.counts, r.rounds, w)
+    for key in burst[:8]:  # warm-up of the plain loop
+        run_alone(key)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_work = 0
+    for key in burst:
+        _, w = run_alone(key)
+        plain_work += w
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+
+    srv = pg.Server(slots=args.slots)
+    gids = [srv.add_inputs(g) for g in graphs]  # the uploads join while serving
+    upload_s = []
+
+    def served(reqs, arrivals=None, uploads_at=()):
+        """Submits reqs (at the given arrival offsets, else at once) from a
+        producer thread, which also registers uploads[j] just before request
+        uploads_at[j]; returns per-request latencies (ms), mismatches, wall s."""
+        import threading
+        rids = [None] * len(reqs)
+        sem = threading.Semaphore(0)
+        start = time.perf_counter()
+
+        def produce():
+            for k, key in enumerate(reqs):
+                if arrivals is not None:
+                    d = start + arrivals[k] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                for j, at in enumerate(uploads_at):
+                    if at == k:
+                        t = time.perf_counter()
+                        gids.append(srv.add_inputs(uploads[j]))
+                        upload_s.append(time.perf_counter() - t)
+                rids[k] = srv.submit(gids[key[0]], seeds_of(*key))
+                sem.release()
+
+        th = threading.Thread(target=produce)
+        th.start()
+        lat, bad = [], 0
+        for k, key in enumerate(reqs):
+            sem.acquire()
+            res, info = srv.result(rids[k])
+            lat.append((info["done_ns"] - info["submit_ns"]) / 1e6)
+            c, T, _ = alone[key]
+            bad += int(res.rounds != T or not np.array_equal(res.counts, c))
+        th.join()
+        torch.cuda.synchronize()
+        return lat, bad, time.perf_counter() - start
+
+    def ensure_alone(reqs):
+        for key in set(reqs):
+            if key not in alone:
+                r, w = run_alone(key)
+                alone[key] = (r.counts, r.rounds, w)
+
+    def open_loop_run(rate, uploads_at=()):
+        count = min(int(rate * W["duration"]), W["max_requests"])
+        rng = np.random.default_rng(W["seed"] + int(rate))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        first = len(graphs)
+
+        def avail(k):  # graphs registered by the time request k is submitted
+            return first + sum(1 for at in uploads_at if at <= k) if uploads_at else len(allg)
+
+        reqs = _serve_requests(count, len(allg), W["seed"] + int(rate), V, upload_at=avail)
+        ensure_alone(reqs)
+        lat, bad, wall = served(reqs, arrivals, uploads_at)
+        assert bad == 0, f"{bad} served answers differ from the request alone"
+        rwork = sum(alone[k][2] for k in reqs)
+        return {"offered_req_per_s": rate, "requests": count, "wall_s": wall,
+                "achieved_req_per_s": count / wall,
+                "seed_edge_traversals_per_s": rwork / wall,
+                "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(max(lat))}
+
+    warm = [k for k in burst if k[0] < len(graphs)][:16]
+    served(warm)  # warm-up: views, workspaces, captured loops
+    open_loop = []
+    n0 = min(int(W["rates"][0] * W["duration"]), W["max_requests"])
+    open_loop.append(open_loop_run(W["rates"][0], uploads_at=(n0 // 3, 2 * n0 // 3)))
+    st0 = srv.stats()
+    lat_b, bad_b, served_s = served(burst)
+    st1 = srv.stats()
+    assert bad_b == 0, f"{bad_b} served answers differ from the request alone"
+    work = sum(alone[k][2] for k in burst)
+    assert work == plain_work
+    value = work / served_s
+    plain_value = work / plain_s
+    for rate in W["rates"][1:]:
+        open_loop.append(open_loop_run(rate))
+    stats = srv.stats()
+    srv.close()
+
+    h2d = sum(seeds_of(*k).nbytes for k in burst)
+    d2h = sum(alone[k][0].nbytes for k in burst)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": served_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "description": f"pool of {W['pool']} mixed graphs (n log-uniform "
+                                  f"[{W['n_lo']:g}, {W['n_hi']:g}]) + uploaded ER "
+                                  f"{[u[0] for u in W['uploads']]}; eps in {{0.05, 0.1, 0.2}}",
+                   "burst_requests": len(burst), "slots": args.slots,
+                   "distinct_requests": len(alone), "generate_s": gen_s,
+                   "timing": "wall clock between device synchronisations",
+                   "parallelism": f"replicas x{world}"},
+        "plain": {"value": plain_value, "ms_per_step": plain_s * 1e3},
+        "served_over_plain": value / plain_value,
+        "burst_latency_ms": {"p50": float(np.percentile(lat_b, 50)),
+                             "p99": float(np.percentile(lat_b, 99))},
+        "burst_propagations": st1["propagations"] - st0["propagations"],
+        "open_loop": open_loop,
+        "upload_while_serving_s": upload_s,
+        "server": {k: stats[k] for k in ("peak_bytes", "budget_bytes", "resident_bytes",
+                                          "completed", "propagations")},
+        "roofline": None,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": served_s * 1e3},
+        "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for G in handles:
         G.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -549,8 +767,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS),
-                    default="rmat22_directed_s256")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) +
+                    sorted(SERVE_WORKLOADS), default="rmat22_directed_s256")
+    ap.add_argument("--slots", type=int, default=4, help="server slots (serving workload)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="batched workload: 1 = autotune each width class before timing")
+    ap.add_argument("--tune-trials", type=int, default=16)
     ap.add_argument("--cpu-seeds", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-launches", action="store_true",
@@ -562,6 +784,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.profile_run:
         profile_run(args)
+    elif args.workload in SERVE_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the "
+                              "single-graph workloads; run it without --workload"}))
+        else:
+            run_serve(args)
     elif args.workload in BATCH_WORKLOADS:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the "

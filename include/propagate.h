@@ -111,6 +111,15 @@ typedef struct {
                                launch (plain launches) for pg_last_stats */
   int32_t window_rows;      /* rows of per-round counters kept on the device
                                before they are copied out; 0 = auto */
+  int32_t words_per_thread; /* signature words one lane gathers per in-arc
+                               (1, 2, 4 or 8; a row of more words is swept in
+                               chunks of this many); 0 = the row's words
+                               rounded up to 1, 2, 4 or 8 */
+  int32_t wide_rows;        /* rows of more than 8 words (s > 512): 0 or 1 =
+                               a warp per row piece, its lanes spread over
+                               the words (one contiguous read per gathered
+                               neighbour); 2 = lanes over 8-word chunks as
+                               for narrower rows (words_per_thread applies) */
 } pg_options;
 
 #define PG_DIR_AUTO 0
@@ -228,6 +237,30 @@ pg_status pg_metrics(const pg_counts *c, int64_t n, int32_t tau_num, int32_t tau
 pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
 
 /*
+ * Autotuner. The paper fixes no schedule (its loops are sequential Java);
+ * the GPU's free parameters are the lanes per work piece (group_lanes), the
+ * signature words a lane gathers per arc (words_per_thread) and the
+ * frontier density at which a round becomes a full sweep (dense_threshold),
+ * plus whether changed bits are tested before delta gathers. pg_autotune
+ * times PROPAGATE-P on g with these seeds under candidate values, one
+ * parameter at a time starting from *inout (coordinate descent; a candidate
+ * replaces the current value when it is at least 2% faster), and writes the
+ * fastest options back to *inout. Every candidate's counts are compared
+ * with the first run's; a difference returns PG_EDEVICE. max_trials bounds
+ * the timed propagations (each candidate is run twice, the faster kept).
+ * Errors: as pg_propagate_p.
+ */
+typedef struct {
+  int32_t trials;       /* propagations run */
+  int32_t improved;     /* accepted changes */
+  double default_ms;    /* best time of the starting options */
+  double best_ms;       /* best time of the returned options */
+} pg_tune_report;
+
+pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t max_trials,
+                      pg_options *inout, pg_tune_report *report, void *stream);
+
+/*
  * Allocation-free PROPAGATE-P. The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory while they
  * run (for example a serving process that reserves all of its device memory
@@ -302,7 +335,7 @@ pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, 
 /*
  * Runs every graph of the batch to its last productive round and keeps each
  * graph's counts on the host. opt as for pg_propagate_p (planes_per_pass is
- * ignored). Errors: PG_EINVAL (empty batch, malformed CSR), PG_ENOMEM,
+ * ignored); NULL = the options pg_batch_tune chose, else the defaults. Errors: PG_EINVAL (empty batch, malformed CSR), PG_ENOMEM,
  * PG_ECUDA; on error no result of this run is kept.
  */
 pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream);
@@ -316,6 +349,153 @@ pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out);
 
 /* Work counters of the last pg_batch_run. */
 pg_status pg_batch_get_stats(pg_batch *b, pg_batch_stats *out);
+
+/*
+ * Tunes each width class of the batch as pg_autotune does (each timed run
+ * is a full run of that class; counts compared across candidates) and keeps
+ * the chosen options per class; pg_batch_run with opt == NULL then uses
+ * them. report (may be NULL) receives the sums over classes.
+ */
+pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report, void *stream);
+
+/* pg_stats of width class `group` in the last pg_batch_run (kernel times
+ * with opt->timing = 1). Errors: PG_EINVAL (no such class or no run). */
+pg_status pg_batch_group_stats(pg_batch *b, int32_t group, pg_stats *out);
+
+/* Options a width class of the batch runs with (tuned, else the defaults);
+ * classes are numbered by increasing width after the first run or tune;
+ * *graphs (may be NULL) receives the class's graph count. Errors: PG_EINVAL
+ * (no such class). */
+pg_status pg_batch_get_options(pg_batch *b, int32_t group, pg_options *out, int32_t *graphs);
+
+/*
+ * Serving loop. The paper runs one query per call; this is the library's
+ * request loop for many metric queries on resident graphs (the Sec. 4
+ * remark that seeds are independent is what lets queries share a run).
+ *
+ * The server keeps registered graphs on the device. A request names a graph
+ * and a seed set and is answered with the counts pg_propagate_p would give
+ * for it alone (m_active is not kept per request). `slots` worker threads,
+ * each with its own CUDA stream and workspace, take queued requests as soon
+ * as a slot and device memory are free (continuous batching): a free slot
+ * takes the oldest request that fits the memory budget and merges into the
+ * same propagation the other queued requests on that graph (up to merge_max
+ * requests and merge_max_seeds seeds; seeds of different requests are
+ * independent bit columns and may coincide). Propagations on different
+ * slots run concurrently on the device.
+ *
+ * Memory admission: resident graphs (CSR, out-CSR, sliced-ELL copy) plus
+ * every slot's workspace and cached piece lists stay within hbm_budget.
+ * A request is charged its workspace, about 32 bytes per node per 64 seeds
+ * (four signature buffers) plus the frontier lists and its counts window. A
+ * request that cannot fit an idle server is refused at submission
+ * (PG_ENOMEM); others wait until memory frees up, idle slots first dropping
+ * their caches.
+ *
+ * All calls are thread-safe. Requests run on the device current when the
+ * server was created; the server's calls must be made with that device
+ * current.
+ */
+typedef struct pg_server pg_server;
+
+typedef struct {
+  int32_t slots;            /* concurrent propagations (1..64; default 4) */
+  int32_t merge_max;        /* most requests merged into one propagation (16) */
+  int32_t merge_max_seeds;  /* most seeds of a merged propagation (8192) */
+  int32_t reserved;
+  int64_t hbm_budget;       /* device bytes for graphs + workspaces; 0 = 90% of
+                               the memory free at creation */
+  pg_options opt;           /* options of every propagation (timing ignored;
+                               window_rows 0 = 256) */
+} pg_server_config;
+
+typedef enum {
+  PG_REQ_QUEUED = 0,
+  PG_REQ_RUNNING = 1,
+  PG_REQ_DONE = 2,
+  PG_REQ_FAILED = 3,
+  PG_REQ_CANCELLED = 4
+} pg_request_state;
+
+typedef struct {
+  int32_t state;      /* pg_request_state */
+  int32_t status;     /* PG_OK, or the error of a failed / cancelled request */
+  int32_t rounds;     /* T once done */
+  int32_t s;          /* seeds of the request */
+  int32_t graph;      /* graph id */
+  int32_t merged;     /* requests in the propagation that served it */
+  int64_t footprint;  /* device bytes its slot was charged */
+  int64_t submit_ns;  /* steady-clock times of submission, start, end */
+  int64_t start_ns;
+  int64_t done_ns;
+} pg_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled;
+  int64_t propagations;           /* runs on the device (merged requests share one) */
+  int64_t resident_bytes;         /* registered graphs */
+  int64_t inflight_bytes;         /* slots' workspaces and caches now */
+  int64_t peak_bytes;             /* most resident + slot bytes charged at once */
+  int64_t budget_bytes;           /* the admission budget */
+  int32_t graphs, queued, running, reserved;
+  uint64_t seed_edge_traversals;  /* summed over propagations */
+} pg_server_stats;
+
+/* Fills *cfg with the defaults. */
+void pg_server_default_config(pg_server_config *cfg);
+
+/* Starts a server on the current device (cfg NULL = defaults). Errors:
+ * PG_EINVAL (config), PG_ECUDA. */
+pg_status pg_server_create(const pg_server_config *cfg, pg_server **out);
+
+/* Cancels queued requests, lets running ones finish, frees everything.
+ * NULL is allowed. */
+void pg_server_destroy(pg_server *srv);
+
+/*
+ * Registers a graph (host CSR over in-edges, as for pg_graph_from_csr; copied
+ * to the device). *graph_id receives its id. Errors: PG_EINVAL (CSR),
+ * PG_ENOMEM (budget or device memory), PG_ECUDA.
+ */
+pg_status pg_server_add_graph(pg_server *srv, const int64_t *row_ptr, const int32_t *col,
+                              int64_t n, int64_t m, int directed, int32_t *graph_id);
+
+/* Unregisters a graph with no queued or running request (else PG_EINVAL). */
+pg_status pg_server_remove_graph(pg_server *srv, int32_t graph_id);
+
+/*
+ * Queues a request: seeds host int32[s], distinct, in [0, n) of the graph;
+ * copied. Returns at once with *request_id. Errors: PG_EINVAL (graph, seeds),
+ * PG_ENOMEM (cannot fit the budget even alone).
+ */
+pg_status pg_server_submit(pg_server *srv, int32_t graph_id, const int32_t *seeds, int32_t s,
+                           int64_t *request_id);
+
+/* State and times of a request (info required). */
+pg_status pg_server_poll(pg_server *srv, int64_t request_id, pg_request_info *info);
+
+/* Blocks until the request is done, failed or cancelled, or timeout_ms
+ * passes (< 0: no limit; PG_ETIMEOUT then). info may be NULL. */
+pg_status pg_server_wait(pg_server *srv, int64_t request_id, int32_t timeout_ms,
+                         pg_request_info *info);
+
+/*
+ * Copies a finished request's counts into out (out->s must equal its s; rows
+ * 0..min(T, out->max_rounds); m_active zero-filled) and releases the request.
+ * A failed or cancelled request returns its status and is released. Errors:
+ * PG_EINVAL (unknown or unfinished request, bad out), PG_ERANGE (T >
+ * out->max_rounds; the request is kept so that a larger buffer can be
+ * offered).
+ */
+pg_status pg_server_result(pg_server *srv, int64_t request_id, pg_counts *out,
+                           pg_request_info *info);
+
+/* Cancels a queued request; a running one completes on the device and its
+ * result is dropped (state PG_REQ_CANCELLED). */
+pg_status pg_server_cancel(pg_server *srv, int64_t request_id);
+
+/* Counters of the server. */
+pg_status pg_server_get_stats(pg_server *srv, pg_server_stats *out);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,9 @@ current CUDA stream.
 
     b = Batch(); i = b.add(row_ptr, col, seeds); b.run()   # many graphs at once
     res_i = b.result(i)
+
+    srv = Server(slots=4); gid = srv.add_graph(row_ptr, col)  # serving loop
+    rid = srv.submit(gid, seeds); res = srv.result(rid)
 """
 from __future__ import annotations
 
@@ -24,7 +27,7 @@ import numpy as np
 from . import _abi
 from ._abi import (PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE, PropagateError)
 
-__all__ = ["Graph", "Result", "Batch", "propagate_p", "propagate_s", "metrics", "options",
+__all__ = ["Graph", "Result", "Batch", "Server", "autotune", "options_dict", "propagate_p", "propagate_s", "metrics", "options",
            "PropagateError", "PG_DIR_AUTO", "PG_DIR_DENSE", "PG_DIR_SPARSE", "library_path"]
 
 
@@ -52,6 +55,10 @@ def options(**kw) -> _abi.Options:
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
     return o
+
+
+def options_dict(o: _abi.Options) -> dict:
+    return {f: getattr(o, f) for f, _ in _abi.Options._fields_}
 
 
 class Graph:
@@ -182,6 +189,19 @@ def propagate_s(g: Graph, seeds, max_rounds: int | None = None, opts=None,
     return _run(_abi.lib().pg_propagate_s, "pg_propagate_s", g, seeds, max_rounds, opts, stream)
 
 
+def autotune(g: "Graph", seeds, max_trials: int = 24, opts=None, stream=None):
+    """pg_autotune: fastest schedule options for PROPAGATE-P on g with these
+    seeds (counts checked identical across candidates). Returns
+    (options, report dict)."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    st = stream if stream is not None else _current_stream()
+    o = opts if opts is not None else options()
+    rep = _abi.TuneReport()
+    _abi.check(_abi.lib().pg_autotune(g._h, seeds.ctypes.data, int(seeds.size), int(max_trials),
+                                      ctypes.byref(o), ctypes.byref(rep), st), "pg_autotune")
+    return o, {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
+
+
 class Batch:
     """pg_batch: PROPAGATE-P over many independent graphs, packed by
     signature width into disjoint unions that each run as one propagation.
@@ -214,23 +234,59 @@ class Batch:
         return len(self._n)
 
     def run(self, opts=None, stream=None):
+        """Runs every graph; opts None = the tuned options (else defaults)."""
         st = stream if stream is not None else _current_stream()
-        o = opts if opts is not None else options()
-        _abi.check(_abi.lib().pg_batch_run(self._h, ctypes.byref(o), st), "pg_batch_run")
+        o = ctypes.byref(opts) if opts is not None else None
+        _abi.check(_abi.lib().pg_batch_run(self._h, o, st), "pg_batch_run")
 
     def result(self, index: int) -> Result:
         """Counts of graph `index` from the last run (m_active is not kept
         per graph in a batch and reads as zeros)."""
         s, n = self._s[index], self._n[index]
-        cap = max(n - 1, 0)
-        counts = np.zeros((cap + 1, s), dtype=np.uint32)
-        c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
-                        counts=counts.ctypes.data, m_active=None)
-        _abi.check(_abi.lib().pg_batch_result(self._h, int(index), ctypes.byref(c)),
-                   "pg_batch_result")
+        cap = min(max(n - 1, 0), 64)
+        while True:
+            counts = np.zeros((cap + 1, s), dtype=np.uint32)
+            c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
+                            counts=counts.ctypes.data, m_active=None)
+            rc = _abi.lib().pg_batch_result(self._h, int(index), ctypes.byref(c))
+            if rc == _abi.PG_ERANGE and c.rounds > cap:
+                cap = int(c.rounds)  # the exact size, known now
+                continue
+            _abi.check(rc, "pg_batch_result")
+            break
         T = int(c.rounds)
         return Result(rounds=T, counts=counts[:T + 1].copy(),
                       m_active=np.zeros(T + 2, dtype=np.uint64), s=s, n=n)
+
+    def tune(self, max_trials: int = 24, stream=None) -> dict:
+        """pg_batch_tune: picks schedule options per width class; later
+        run() calls without opts use them."""
+        st = stream if stream is not None else _current_stream()
+        rep = _abi.TuneReport()
+        _abi.check(_abi.lib().pg_batch_tune(self._h, int(max_trials), ctypes.byref(rep), st),
+                   "pg_batch_tune")
+        return {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
+
+    def group_stats(self) -> list:
+        """pg_stats dict per width class of the last run, narrowest first."""
+        out, k = [], 0
+        while True:
+            st = _abi.Stats()
+            if _abi.lib().pg_batch_group_stats(self._h, k, ctypes.byref(st)) != _abi.PG_OK:
+                return out
+            out.append({f: getattr(st, f) for f, _ in _abi.Stats._fields_})
+            k += 1
+
+    def group_options(self) -> list:
+        """(graphs, options dict) per width class, narrowest first."""
+        out, k = [], 0
+        while True:
+            o, ng = _abi.Options(), ctypes.c_int32(0)
+            if _abi.lib().pg_batch_get_options(self._h, k, ctypes.byref(o),
+                                               ctypes.byref(ng)) != _abi.PG_OK:
+                return out
+            out.append((int(ng.value), options_dict(o)))
+            k += 1
 
     def stats(self) -> dict:
         st = _abi.BatchStats()
@@ -240,6 +296,124 @@ class Batch:
     def close(self):
         if self._h:
             _abi.lib().pg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """pg_server: resident graphs and asynchronous PROPAGATE-P requests with
+    continuous batching (merging of queued requests on one graph, concurrent
+    slots, admission by device-memory budget). Results are the counts
+    pg_propagate_p gives for each request alone."""
+
+    def __init__(self, slots: int = 4, merge_max: int = 16, merge_max_seeds: int = 8192,
+                 hbm_budget: int = 0, opts=None):
+        c = _abi.ServerConfig()
+        _abi.lib().pg_server_default_config(ctypes.byref(c))
+        c.slots, c.merge_max, c.merge_max_seeds, c.hbm_budget = (
+            int(slots), int(merge_max), int(merge_max_seeds), int(hbm_budget))
+        if opts is not None:
+            c.opt = opts
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().pg_server_create(ctypes.byref(c), ctypes.byref(h)),
+                   "pg_server_create")
+        self._h = h
+        self._graph_n = {}
+        self._req = {}  # request id -> (graph id, s)
+
+    def add_graph(self, row_ptr, col, n: int | None = None, directed: bool = True) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        n = int(rp.size - 1 if n is None else n)
+        gid = ctypes.c_int32(-1)
+        _abi.check(_abi.lib().pg_server_add_graph(self._h, rp.ctypes.data, cl.ctypes.data, n,
+                                                  int(cl.size), int(bool(directed)),
+                                                  ctypes.byref(gid)), "pg_server_add_graph")
+        self._graph_n[int(gid.value)] = n
+        return int(gid.value)
+
+    def add_inputs(self, g) -> int:
+        return self.add_graph(g.row_ptr, g.col, n=g.n, directed=g.directed)
+
+    def remove_graph(self, graph_id: int):
+        _abi.check(_abi.lib().pg_server_remove_graph(self._h, int(graph_id)),
+                   "pg_server_remove_graph")
+        self._graph_n.pop(int(graph_id), None)
+
+    def submit(self, graph_id: int, seeds) -> int:
+        sd = np.ascontiguousarray(seeds, dtype=np.int32)
+        rid = ctypes.c_int64(0)
+        _abi.check(_abi.lib().pg_server_submit(self._h, int(graph_id), sd.ctypes.data,
+                                               int(sd.size), ctypes.byref(rid)),
+                   "pg_server_submit")
+        self._req[int(rid.value)] = (int(graph_id), int(sd.size))
+        return int(rid.value)
+
+    @staticmethod
+    def _info(i: _abi.RequestInfo) -> dict:
+        return {f: getattr(i, f) for f, _ in _abi.RequestInfo._fields_}
+
+    def poll(self, request_id: int) -> dict:
+        info = _abi.RequestInfo()
+        _abi.check(_abi.lib().pg_server_poll(self._h, int(request_id), ctypes.byref(info)),
+                   "pg_server_poll")
+        return self._info(info)
+
+    def wait(self, request_id: int, timeout_ms: int = -1) -> dict | None:
+        """Info once finished; None on timeout."""
+        info = _abi.RequestInfo()
+        rc = _abi.lib().pg_server_wait(self._h, int(request_id), int(timeout_ms),
+                                       ctypes.byref(info))
+        if rc == _abi.PG_ETIMEOUT:
+            return None
+        _abi.check(rc, "pg_server_wait")
+        return self._info(info)
+
+    def result(self, request_id: int, timeout_ms: int = -1):
+        """Waits for the request and returns (Result, info); releases it."""
+        info = self.wait(request_id, timeout_ms)
+        if info is None:
+            raise TimeoutError(f"request {request_id} not finished")
+        gid, s = self._req[int(request_id)]
+        n = self._graph_n[gid]
+        cap = max(int(info["rounds"]), 0)  # T is known once the request is done
+        counts = np.zeros((cap + 1, s), dtype=np.uint32)
+        c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
+                        counts=counts.ctypes.data, m_active=None)
+        out = _abi.RequestInfo()
+        rc = _abi.lib().pg_server_result(self._h, int(request_id), ctypes.byref(c),
+                                         ctypes.byref(out))
+        if rc != _abi.PG_ERANGE:
+            del self._req[int(request_id)]
+        _abi.check(rc, "pg_server_result")
+        T = int(c.rounds)
+        res = Result(rounds=T, counts=counts[:T + 1].copy(),
+                     m_active=np.zeros(T + 2, dtype=np.uint64), s=s, n=n)
+        return res, self._info(out)
+
+    def cancel(self, request_id: int):
+        _abi.check(_abi.lib().pg_server_cancel(self._h, int(request_id)), "pg_server_cancel")
+
+    def stats(self) -> dict:
+        st = _abi.ServerStats()
+        _abi.check(_abi.lib().pg_server_get_stats(self._h, ctypes.byref(st)),
+                   "pg_server_get_stats")
+        return {f: getattr(st, f) for f, _ in _abi.ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _abi.lib().pg_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -25,7 +25,8 @@ class Options(ctypes.Structure):
                 ("group_lanes", ctypes.c_int32),
                 ("test_changed", ctypes.c_int32), ("planes_per_pass", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("window_rows", ctypes.c_int32)]
+                ("window_rows", ctypes.c_int32), ("words_per_thread", ctypes.c_int32),
+                ("wide_rows", ctypes.c_int32)]
 
 
 class Counts(ctypes.Structure):
@@ -55,10 +56,42 @@ class Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("improved", ctypes.c_int32),
+                ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
+
+
 class BatchStats(ctypes.Structure):
     _fields_ = [("graphs", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("sweeps", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("seed_edge_traversals", ctypes.c_uint64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("merge_max", ctypes.c_int32),
+                ("merge_max_seeds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("opt", Options)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("s", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("merged", ctypes.c_int32), ("footprint", ctypes.c_int64),
+                ("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("propagations", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("inflight_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("graphs", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
+
+
+PG_REQ_QUEUED, PG_REQ_RUNNING, PG_REQ_DONE, PG_REQ_FAILED, PG_REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
 # name -> (restype, argtypes); every symbol declared in include/propagate.h
@@ -81,6 +114,8 @@ SIGNATURES = {
     "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "pg_propagate_p_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _i32,
                                               ctypes.POINTER(_i32), _vp]),
+    "pg_autotune": (ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.POINTER(Options),
+                                   ctypes.POINTER(TuneReport), _vp]),
     "pg_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "pg_batch_free": (None, [_vp]),
     "pg_batch_add": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, ctypes.c_int, _vp, _i32,
@@ -88,6 +123,23 @@ SIGNATURES = {
     "pg_batch_run": (ctypes.c_int, [_vp, ctypes.POINTER(Options), _vp]),
     "pg_batch_result": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Counts)]),
     "pg_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(BatchStats)]),
+    "pg_batch_tune": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(TuneReport), _vp]),
+    "pg_batch_group_stats": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Stats)]),
+    "pg_batch_get_options": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Options),
+                                            ctypes.POINTER(_i32)]),
+    "pg_server_default_config": (None, [ctypes.POINTER(ServerConfig)]),
+    "pg_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
+    "pg_server_destroy": (None, [_vp]),
+    "pg_server_add_graph": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, ctypes.c_int,
+                                           ctypes.POINTER(_i32)]),
+    "pg_server_remove_graph": (ctypes.c_int, [_vp, _i32]),
+    "pg_server_submit": (ctypes.c_int, [_vp, _i32, _vp, _i32, ctypes.POINTER(_i64)]),
+    "pg_server_poll": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(RequestInfo)]),
+    "pg_server_wait": (ctypes.c_int, [_vp, _i64, _i32, ctypes.POINTER(RequestInfo)]),
+    "pg_server_result": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(Counts),
+                                        ctypes.POINTER(RequestInfo)]),
+    "pg_server_cancel": (ctypes.c_int, [_vp, _i64]),
+    "pg_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
 }
 
 _lock = threading.Lock()

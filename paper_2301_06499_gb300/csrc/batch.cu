@@ -10,6 +10,7 @@
 // graph's count columns and to test saturation against that graph's seeds.
 // A graph whose propagation ended simply has no frontier in later rounds.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -33,6 +34,10 @@ struct pg_batch {
     pg::DevBuf node_graph, graph_s, graph_col0;
     std::vector<int32_t> seeds, seed_bit, col0;
     int32_t ncols = 0, s_bits = 0, max_rounds = 0;
+    bool tuned = false;
+    pg_options opt{};  // chosen by pg_batch_tune
+    pg_stats last{};   // of the last run
+    bool ran = false;
   };
   std::vector<Item> items;
   std::vector<Group> groups;
@@ -110,6 +115,10 @@ pg_status build_groups(pg_batch *b, cudaStream_t st) {
     pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, 0, st, &gr.g);
     if (rc) return rc;
     rc = ensure(gr.node_graph, sizeof(int32_t) * (size_t)n);
+    if (!rc) {  // the packed graph knows its parts (sliced-ELL chunks per graph)
+      gr.g->seg_of = (const int32_t *)gr.node_graph.p;
+      gr.g->nseg = (int32_t)gr.members.size();
+    }
     if (!rc) rc = ensure(gr.graph_s, sizeof(int32_t) * graph_s.size());
     if (!rc) rc = ensure(gr.graph_col0, sizeof(int32_t) * graph_col0.size());
     if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.node_graph.p, node_graph.data(),
@@ -156,6 +165,16 @@ void take_window(void *vctx, int32_t row_base, int32_t rows, const uint32_t *dat
       it.counts.insert(it.counts.end(), row, row + s);
     }
   }
+}
+
+struct HashCtx {
+  uint64_t h = 1469598103934665603ULL;
+};
+
+void hash_window(void *vctx, int32_t row_base, int32_t rows, const uint32_t *data, int32_t ncols) {
+  HashCtx *c = static_cast<HashCtx *>(vctx);
+  c->h = fnv1a(c->h, &row_base, sizeof(row_base));
+  c->h = fnv1a(c->h, data, sizeof(uint32_t) * (size_t)rows * ncols);
 }
 
 }  // namespace
@@ -226,10 +245,11 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
     SinkCtx ctx{b, &gr};
     int32_t T = 0;
     pg_stats st1{};
+    const pg_options *o = opt ? opt : (gr.tuned ? &gr.opt : nullptr);
     rc = propagate_batch_group(gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
                                (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
                                (const int32_t *)gr.graph_col0.p, gr.ncols, gr.s_bits,
-                               gr.max_rounds, &take_window, &ctx, &T, opt, stream, &st1);
+                               gr.max_rounds, &take_window, &ctx, &T, o, stream, &st1);
     if (rc) {
       for (auto &it : b->items) {
         it.counts.clear();
@@ -237,6 +257,8 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
       }
       return rc;
     }
+    gr.last = st1;
+    gr.ran = true;
     bs.seed_edge_traversals += st1.seed_edge_traversals;
     bs.sweeps = std::max(bs.sweeps, st1.sweeps);
     bs.launches += st1.launches;
@@ -246,6 +268,68 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
     }
   }
   b->stats = bs;
+  return PG_OK;
+}
+
+pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report, void *stream) {
+  if (!b || max_trials < 1) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->items.empty()) return PG_EINVAL;
+  pg_status rc = PG_OK;
+  if (!b->built && (rc = build_groups(b, (cudaStream_t)stream))) {
+    free_groups(b);
+    return rc;
+  }
+  pg_tune_report sum{};
+  for (auto &gr : b->groups) {
+    TuneRun run = [&](const pg_options &o, double *ms, uint64_t *hash) -> pg_status {
+      HashCtx hc;
+      int32_t T = 0;
+      const auto t0 = std::chrono::steady_clock::now();
+      pg_status e = propagate_batch_group(
+          gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
+          (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
+          (const int32_t *)gr.graph_col0.p, gr.ncols, gr.s_bits, gr.max_rounds, &hash_window, &hc,
+          &T, &o, stream, nullptr);
+      const auto t1 = std::chrono::steady_clock::now();
+      if (e) return e;
+      *ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+      *hash = fnv1a(hc.h, &T, sizeof(T));
+      return PG_OK;
+    };
+    pg_options o;
+    pg_default_options(&o);
+    pg_tune_report r{};
+    if ((rc = tune_options(run, gr.s_bits, max_trials, &o, &r))) return rc;
+    gr.opt = o;
+    gr.tuned = true;
+    sum.trials += r.trials;
+    sum.improved += r.improved;
+    sum.default_ms += r.default_ms;
+    sum.best_ms += r.best_ms;
+  }
+  if (report) *report = sum;
+  return PG_OK;
+}
+
+pg_status pg_batch_group_stats(pg_batch *b, int32_t group, pg_stats *out) {
+  if (!b || !out) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (group < 0 || group >= (int32_t)b->groups.size() || !b->groups[group].ran) return PG_EINVAL;
+  *out = b->groups[group].last;
+  return PG_OK;
+}
+
+pg_status pg_batch_get_options(pg_batch *b, int32_t group, pg_options *out, int32_t *graphs) {
+  if (!b || !out) return PG_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (group < 0 || group >= (int32_t)b->groups.size()) return PG_EINVAL;
+  const auto &gr = b->groups[group];
+  if (gr.tuned)
+    *out = gr.opt;
+  else
+    pg_default_options(out);
+  if (graphs) *graphs = (int32_t)gr.members.size();
   return PG_OK;
 }
 

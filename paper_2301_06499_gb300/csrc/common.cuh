@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -85,6 +86,8 @@ struct Params {
   const int32_t *node_graph;  // batch of disjoint graphs: graph of each node (else null)
   const int32_t *graph_s;     // batch: seeds of each graph
   const int32_t *graph_col0;  // batch: first count column of each graph
+  const int32_t *sell_seg;    // batch: graph of each sliced-ELL chunk
+  int32_t *gmark;             // batch: last round in which each graph had a changed row
   RoundStats *rs;       // [row_cap + 2], slot = round - row_base
   Ctrl *ctrl;
   int32_t max_rounds;
@@ -113,7 +116,8 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds, seed_bits;
+  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds, seed_bits,
+      gmark;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -130,12 +134,15 @@ struct PieceList {
 // chunk's column indices are stored column-major (arc k of lane l at
 // off[c] + 32 k + l, -1 past a piece's end), so a warp reading step k of a
 // chunk loads 128 contiguous bytes.
+constexpr int32_t kSellPiece = 256;  // longest piece of the sliced-ELL copy
+
 struct SellList {
   int32_t Lmax = 0;
   DevBuf items;  // ulonglong2 make_item per lane slot, nchunks * 32
   DevBuf col;    // int32
   DevBuf off;    // int64 per chunk
   DevBuf len;    // int32 per chunk (its longest piece)
+  DevBuf seg;    // int32 per chunk: its graph, for a packed batch (else empty)
   int64_t nchunks = 0;
   int64_t slots = 0;  // total col entries
 };
@@ -152,11 +159,16 @@ struct pg_graph {
   int32_t *out_col = nullptr;
   bool owns_in = true;
   bool owns_out = true;
+  bool owns_sell = true;  // false in a view (make_view)
+  // a packed batch: the graph of each node (device, borrowed) and how many
+  const int32_t *seg_of = nullptr;
+  int32_t nseg = 0;
   double mean_degree = 0.0;
   int64_t max_degree = 0;
   pg::PieceList pieces;
   pg::SellList sell;
   pg::Workspace ws;
+  pg::Workspace *ext_ws = nullptr;  // a view running on its server slot's workspace
   pg_stats last{};
   int hint_p = 0, hint_s = 0;  // sweeps of the last pass, first batch of the next
   std::mutex mu;
@@ -167,6 +179,10 @@ namespace pg {
 // Grow-only device buffer; contents are not preserved on growth.
 pg_status ensure(DevBuf &b, size_t bytes);
 void release(DevBuf &b);
+// Frees every buffer, event and pinned block of a workspace.
+void release_workspace(Workspace &w);
+// Device bytes a workspace holds.
+int64_t workspace_held(const Workspace &w);
 pg_status cuda_status(cudaError_t e);
 int sm_count();
 // Dense piece list of g for piece length L (cached in g).
@@ -186,5 +202,24 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
                                 int32_t ncols, int32_t s_bits, int32_t max_rounds,
                                 WindowSink sink, void *sink_ctx, int32_t *rounds,
                                 const pg_options *opt, void *stream, pg_stats *st_out);
+// Seeds of several requests merged on one graph: seed i owns bit and count
+// column i, and a node may carry several seeds; windows go to the sink.
+pg_status propagate_columns(pg_graph *g, const int32_t *seeds, int32_t nseeds, int32_t max_rounds,
+                            WindowSink sink, void *sink_ctx, int32_t *rounds,
+                            const pg_options *opt, void *stream, pg_stats *st_out);
+// A handle sharing master's device CSR, out-CSR and sliced-ELL copy (built
+// first if missing) with its own workspace, piece list and CUDA graphs, so
+// that several propagations on one graph can run at once on different
+// streams. The master must outlive the view.
+pg_status make_view(pg_graph *master, cudaStream_t st, pg_graph **out);
+// One timed run of a tuning candidate: its time and a hash of its counts.
+typedef std::function<pg_status(const pg_options &, double *ms, uint64_t *hash)> TuneRun;
+// Coordinate descent over the schedule options (see tune.cu).
+pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, pg_options *inout,
+                       pg_tune_report *rep);
+uint64_t fnv1a(uint64_t h, const void *data, size_t bytes);
+// Device bytes a propagation of s seeds on g will hold in its workspace
+// (window_rows as pg_options.window_rows).
+int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows);
 
 }  // namespace pg

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pg {
@@ -241,6 +243,31 @@ __global__ void k_sell_hist(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
   }
 }
 
+// Packed batch: bucket (graph, Lmax - len), so that each graph's pieces are
+// contiguous (longest first) and can be padded to whole chunks.
+__global__ void k_sell_hist_seg(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
+                                const int32_t *seg_of, unsigned long long *hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 it = pieces[i];
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    const int32_t v = (int32_t)(it.y >> 32);
+    atomicAdd(&hist[(int64_t)seg_of[v] * (Lmax + 1) + (Lmax - len)], 1ULL);
+  }
+}
+
+__global__ void k_sell_scatter_seg(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
+                                   const int32_t *seg_of, unsigned long long *cursor,
+                                   ulonglong2 *sorted) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 it = pieces[i];
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    const int32_t v = (int32_t)(it.y >> 32);
+    sorted[atomicAdd(&cursor[(int64_t)seg_of[v] * (Lmax + 1) + (Lmax - len)], 1ULL)] = it;
+  }
+}
+
 __global__ void k_sell_scatter(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
                                unsigned long long *cursor, ulonglong2 *sorted) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
@@ -294,28 +321,83 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
     return rc;
   }
   const int64_t np = tmp.count;
-  const int64_t nchunks = (np + 31) / 32;
+  int64_t nchunks = (np + 31) / 32;
   unsigned long long *hist = nullptr;
   int64_t *coff_tmp = nullptr;
-  rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * (Lmax + 2), st));
-  if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
-  if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
-  if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
-  if (rc == PG_OK) {
-    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (Lmax + 2), st);
-    // padding slots: zero-length items of row 0 (never active)
-    cudaMemsetAsync(sl.items.p, 0, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1), st);
-    k_sell_hist<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist);
-    rc = exclusive_scan_i64((int64_t *)hist, Lmax + 2, st);
-  }
-  if (rc == PG_OK) {
-    k_sell_scatter<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist,
-                                                    (ulonglong2 *)sl.items.p);
-    k_sell_chunks<<<grid_for(nchunks), kBlock, 0, st>>>((const ulonglong2 *)sl.items.p, np,
-                                                        nchunks, (int32_t *)sl.len.p,
-                                                        (int64_t *)sl.off.p);
-    cudaMemsetAsync((int64_t *)sl.off.p + nchunks, 0, sizeof(int64_t), st);
-    rc = cuda_status(cudaGetLastError());
+  if (g->seg_of && g->nseg > 0) {
+    // a packed batch: each graph's pieces sorted by length and padded to
+    // whole chunks, so that a chunk belongs to one graph
+    const int64_t nb = (int64_t)g->nseg * (Lmax + 1);
+    std::vector<unsigned long long> h((size_t)nb);
+    rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * nb, st));
+    if (rc == PG_OK) {
+      cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nb, st);
+      k_sell_hist_seg<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax,
+                                                       g->seg_of, hist);
+      rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(h.data(), hist, sizeof(unsigned long long) * nb,
+                                       cudaMemcpyDeviceToHost, st));
+    if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    std::vector<int32_t> chunk_seg;
+    unsigned long long base = 0;
+    for (int32_t k = 0; rc == PG_OK && k < g->nseg; ++k) {
+      unsigned long long run = base;
+      for (int32_t b = 0; b <= Lmax; ++b) {
+        const unsigned long long c = h[(size_t)k * (Lmax + 1) + b];
+        h[(size_t)k * (Lmax + 1) + b] = run;
+        run += c;
+      }
+      const unsigned long long padded = (run - base + 31) / 32 * 32;
+      chunk_seg.insert(chunk_seg.end(), (size_t)(padded / 32), k);
+      base += padded;
+    }
+    nchunks = (int64_t)(base / 32);
+    if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
+    if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
+    if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
+    if (rc == PG_OK) rc = ensure(sl.seg, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
+    if (rc == PG_OK && nchunks > 0)
+      rc = cuda_status(cudaMemcpyAsync(sl.seg.p, chunk_seg.data(), sizeof(int32_t) * nchunks,
+                                       cudaMemcpyHostToDevice, st));
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(hist, h.data(), sizeof(unsigned long long) * nb,
+                                       cudaMemcpyHostToDevice, st));
+    if (rc == PG_OK) {
+      cudaMemsetAsync(sl.items.p, 0, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1), st);
+      k_sell_scatter_seg<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax,
+                                                          g->seg_of, hist,
+                                                          (ulonglong2 *)sl.items.p);
+      k_sell_chunks<<<grid_for(nchunks), kBlock, 0, st>>>((const ulonglong2 *)sl.items.p, np,
+                                                          nchunks, (int32_t *)sl.len.p,
+                                                          (int64_t *)sl.off.p);
+      cudaMemsetAsync((int64_t *)sl.off.p + nchunks, 0, sizeof(int64_t), st);
+      rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));  // h outlives the copy
+  } else {
+    release(sl.seg);
+    rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * (Lmax + 2), st));
+    if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
+    if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
+    if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
+    if (rc == PG_OK) {
+      cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (Lmax + 2), st);
+      // padding slots: zero-length items of row 0 (never active)
+      cudaMemsetAsync(sl.items.p, 0, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1), st);
+      k_sell_hist<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist);
+      rc = exclusive_scan_i64((int64_t *)hist, Lmax + 2, st);
+    }
+    if (rc == PG_OK) {
+      k_sell_scatter<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist,
+                                                      (ulonglong2 *)sl.items.p);
+      k_sell_chunks<<<grid_for(nchunks), kBlock, 0, st>>>((const ulonglong2 *)sl.items.p, np,
+                                                          nchunks, (int32_t *)sl.len.p,
+                                                          (int64_t *)sl.off.p);
+      cudaMemsetAsync((int64_t *)sl.off.p + nchunks, 0, sizeof(int64_t), st);
+      rc = cuda_status(cudaGetLastError());
+    }
   }
   if (rc == PG_OK) rc = exclusive_scan_i64((int64_t *)sl.off.p, nchunks + 1, st);
   int64_t slots = 0;
@@ -342,6 +424,57 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
     sl.Lmax = 0;
   }
   return rc;
+}
+
+void release_workspace(Workspace &w) {
+  for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0, &w.F1,
+                    &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gmark})
+    release(*b);
+  if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
+  w.ctrl_h = nullptr;
+  for (auto &e : w.ev)
+    if (e) cudaEventDestroy(e);
+  w.ev[0] = w.ev[1] = nullptr;
+  for (auto &e : w.tev)
+    if (e) cudaEventDestroy(e);
+  w.tev.clear();
+}
+
+int64_t workspace_held(const Workspace &w) {
+  int64_t b = 0;
+  for (const DevBuf *x : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0,
+                          &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits,
+                          &w.gmark})
+    b += (int64_t)x->bytes;
+  return b;
+}
+
+pg_status make_view(pg_graph *master, cudaStream_t st, pg_graph **out) {
+  if (!master || !out) return PG_EINVAL;
+  pg_graph *v = new pg_graph();
+  {
+    std::lock_guard<std::mutex> lk(master->mu);
+    pg_status rc = ensure_sell(master, kSellPiece, st);
+    if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    if (rc) {
+      delete v;
+      return rc;
+    }
+    v->n = master->n;
+    v->m = master->m;
+    v->directed = master->directed;
+    v->device = master->device;
+    v->row_ptr = master->row_ptr;
+    v->col = master->col;
+    v->out_ptr = master->out_ptr;
+    v->out_col = master->out_col;
+    v->mean_degree = master->mean_degree;
+    v->max_degree = master->max_degree;
+    v->sell = master->sell;
+  }
+  v->owns_in = v->owns_out = v->owns_sell = false;
+  *out = v;
+  return PG_OK;
 }
 
 }  // namespace pg
@@ -387,16 +520,10 @@ void pg_graph_free(pg_graph *g) {
     std::lock_guard<std::mutex> lk(g->mu);
     free_graph_arrays(g);
     release(g->pieces.list);
-    for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len}) release(*b);
-    Workspace &w = g->ws;
-    for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0, &w.F1, &w.E, &w.A,
-                      &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits})
-      release(*b);
-    if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
-    for (auto &e : w.ev)
-      if (e) cudaEventDestroy(e);
-    for (auto &e : w.tev)
-      if (e) cudaEventDestroy(e);
+    if (g->owns_sell)
+      for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len, &g->sell.seg})
+        release(*b);
+    release_workspace(g->ws);
   }
   delete g;
 }

@@ -250,7 +250,11 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
 
 // Dense round over the sliced-ELL copy: a warp per chunk of 32 pieces, lane
 // l owns piece l; step k reads arc k of all 32 pieces in one coalesced load,
-// and the U deltas of a lane's U steps are gathered together.
+// and the U deltas of a lane's U steps are gathered together. The next
+// chunk's descriptor is loaded while the current one is processed, and the
+// first U column loads of a piece are issued before its saturation bit is
+// known (only the gathers wait for it), so a short piece costs one column
+// latency and one gather latency.
 template <int CW>
 __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const uint64_t *Dprev,
                                            const uint32_t *Cprev, int32_t *F, uint32_t *Ccur,
@@ -262,19 +266,50 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
                                            unsigned long long &my_gath,
                                            unsigned long long &my_items) {
   constexpr int U = CW <= 2 ? PG_DENSE_UNROLL_NARROW : PG_DENSE_UNROLL_WIDE;
+  constexpr bool kPrefetch = CW <= 2;  // measured: helps latency-bound narrow rows only
   const size_t Wp = (size_t)p.Wp;
   const int nch = p.Wp / CW;
-  for (int64_t c = warp; c < p.sell_chunks; c += nwarps) {
-    const ulonglong2 it = p.sell_items[c * 32 + lane];
+  int64_t c = warp;
+  ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
+  int clen_next = 0;
+  int64_t off_next = 0;
+  if (kPrefetch && c < p.sell_chunks) {
+    it_next = p.sell_items[c * 32 + lane];
+    clen_next = __ldg(p.sell_len + c);
+    off_next = __ldg(p.sell_off + c);
+  }
+  for (; c < p.sell_chunks; c += nwarps) {
+    if (!kPrefetch) {
+      it_next = p.sell_items[c * 32 + lane];
+      clen_next = __ldg(p.sell_len + c);
+      off_next = __ldg(p.sell_off + c);
+    }
+    const ulonglong2 it = it_next;
+    const int clen = clen_next;
+    const int32_t *cc = p.sell_col + off_next + lane;
+    const int64_t cn = c + nwarps;
+    if (kPrefetch && cn < p.sell_chunks) {
+      it_next = p.sell_items[cn * 32 + lane];
+      clen_next = __ldg(p.sell_len + cn);
+      off_next = __ldg(p.sell_off + cn);
+    }
+    // a packed batch: a graph without a change in round t-1 has none in t
+    if (p.sell_seg && __ldg(p.gmark + __ldg(p.sell_seg + c)) != ctrl->t - 1) continue;
     const int32_t v = (int32_t)(it.y >> 32);
     const bool whole = (it.y & 0x80000000ULL) != 0ULL;
     const int len = (int)(it.y & 0x7FFFFFFFULL);
-    bool act = len > 0 && !test_bit(p.Sat, v);
-    const int clen = __ldg(p.sell_len + c);
-    const int32_t *cc = p.sell_col + __ldg(p.sell_off + c) + lane;
-    if (act) {
-      ++my_items;
-      my_scan += (unsigned long long)len;
+    // first batch of column indices: for narrow rows issued before the
+    // saturation test (latency matters more than the wasted reads there)
+    int32_t u0[U];
+    bool act;
+    if constexpr (kPrefetch) {
+#pragma unroll
+      for (int q = 0; q < U; ++q) u0[q] = q < len ? __ldg(cc + 32LL * q) : -1;
+      act = len > 0 && !test_bit(p.Sat, v);
+    } else {
+      act = len > 0 && !test_bit(p.Sat, v);
+#pragma unroll
+      for (int q = 0; q < U; ++q) u0[q] = act && q < len ? __ldg(cc + 32LL * q) : -1;
     }
     bool row_changed = false, any_delta = false;
     for (int ch = 0; ch < nch; ++ch) {
@@ -284,8 +319,14 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       if (act && whole) load_words<CW>(own, p.X + (size_t)v * Wp + ch * CW);
       for (int k0 = 0; k0 < clen; k0 += U) {
         int32_t u[U];
+        if (k0 == 0) {
 #pragma unroll
-        for (int q = 0; q < U; ++q) u[q] = (act && k0 + q < len) ? __ldg(cc + 32LL * (k0 + q)) : -1;
+          for (int q = 0; q < U; ++q) u[q] = act ? u0[q] : -1;
+        } else {
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+            u[q] = (act && k0 + q < len) ? __ldg(cc + 32LL * (k0 + q)) : -1;
+        }
         if (p.test_changed) {
 #pragma unroll
           for (int q = 0; q < U; ++q)
@@ -301,6 +342,10 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
 #pragma unroll
       for (int k = 0; k < CW; ++k) any_delta |= acc[k] != 0ULL;
       if (act) row_changed |= finish_piece<CW>(p, v, ch, whole, own, acc);
+    }
+    if (act) {
+      ++my_items;
+      my_scan += (unsigned long long)len;
     }
     act = act && any_delta;  // no changed in-neighbour: not active in round t
     if (act) {
@@ -382,6 +427,9 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
     const int64_t nitems = (int64_t)ctrl->nA;
     const int nch = p.Wp / CW;
     const size_t Wp = (size_t)p.Wp;
+    constexpr bool kPrefetch = CW <= 2;  // next item loaded during this one
+    ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
+    if (kPrefetch && warp * GPW + gw < nitems) it_next = p.A[warp * GPW + gw];
     for (int64_t base = warp * GPW; base < nitems; base += nwarps * GPW) {
       const int64_t item = base + gw;
       bool act = false, whole = true;
@@ -389,7 +437,8 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
       int64_t b = 0;
       int len = 0;
       if (item < nitems) {
-        const ulonglong2 it = p.A[item];
+        const ulonglong2 it = kPrefetch ? it_next : p.A[item];
+        if (kPrefetch && item + nwarps * GPW < nitems) it_next = p.A[item + nwarps * GPW];
         b = (int64_t)it.x;
         v = (int32_t)(it.y >> 32);
         whole = (it.y & 0x80000000ULL) != 0ULL;
@@ -454,5 +503,7 @@ PullFn pull_fn_cw1(int G);
 PullFn pull_fn_cw2(int G);
 PullFn pull_fn_cw4(int G);
 PullFn pull_fn_cw8(int G);
+// Wide rows (more than 8 words): a warp per row piece, for Wp words per row.
+PullFn pull_fn_wide(int Wp);
 
 }  // namespace pg

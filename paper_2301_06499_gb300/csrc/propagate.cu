@@ -14,7 +14,7 @@ namespace pg {
 constexpr int32_t kStatusWindow = 100;  // device asks the host to move the counts window
 constexpr int kSmemCountMax = 12288;    // per-seed counters kept in shared memory up to this s
 constexpr int kExpandArcs = 8;          // out-arcs per expansion piece (LE)
-constexpr int kSellPiece = 256;         // longest piece of the dense rounds' sliced-ELL copy
+constexpr int kWidePiece = 256;         // in-arcs per piece of the wide-row pull
 
 // ------------------------------------------------------------- k_zero
 // Zeroes both signature buffers, the bitmaps, the pass's counts window and
@@ -74,11 +74,16 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
 // One block. Round 0 of the pass: seed i gets bit i (Sig(x_i)[i] = 1) as a
 // change of round 0 (X = 0, Y = the bit), so the post kernel of round 0
 // counts the pairs (x_i, x_i), records the seeds' deltas and expands them
-// like any other frontier.
+// like any other frontier. A node may carry several seeds' bits (requests
+// merged on one graph); it enters the frontier once.
 __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
                                                const int32_t *seed_bit, int sp) {
   __shared__ unsigned long long tot;
-  if (threadIdx.x == 0) tot = 0ULL;
+  __shared__ unsigned int nf;
+  if (threadIdx.x == 0) {
+    tot = 0ULL;
+    nf = 0u;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   // whole warps iterate so that the warp-level appends see every lane
@@ -86,21 +91,24 @@ __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
     const int i = base + lane;
     unsigned long long od = 0;
     int32_t x = 0;
-    const bool ok = i < sp;
-    if (ok) {
+    bool first = false;
+    if (i < sp) {
       x = seeds[i];
       const int bit = seed_bit ? seed_bit[i] : i;  // a batch: the seed's index in its graph
-      p.Y[(size_t)x * p.Wp + (bit >> 6)] = 1ULL << (bit & 63);
-      set_bit(p.C0, x);
-      p.F0[i] = x;
-      od = (unsigned long long)(p.out_ptr[x + 1] - p.out_ptr[x]);
-      atomicAdd(&tot, od);
+      atomicOr(reinterpret_cast<unsigned long long *>(p.Y + (size_t)x * p.Wp + (bit >> 6)),
+               1ULL << (bit & 63));
+      first = !set_bit(p.C0, x);
+      if (first) {
+        p.F0[atomicAdd(&nf, 1u)] = x;
+        od = (unsigned long long)(p.out_ptr[x + 1] - p.out_ptr[x]);
+        atomicAdd(&tot, od);
+      }
     }
-    const unsigned long long ne = ok ? (od + p.LE - 1) / p.LE : 0ULL;
+    const unsigned long long ne = first ? (od + p.LE - 1) / p.LE : 0ULL;
     warp_append_pieces(p.E, &p.ctrl->nE, x, ne, lane);
   }
   __syncthreads();
-  if (threadIdx.x == 0) p.ctrl->fpack = ((unsigned long long)sp << kFsumBits) | tot;
+  if (threadIdx.x == 0) p.ctrl->fpack = ((unsigned long long)nf << kFsumBits) | tot;
 }
 
 __device__ __forceinline__ bool row_full(const uint64_t *row, int Wp, int s) {
@@ -191,7 +199,30 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     const int gid0 = __shfl_sync(kFullMask, gid, 0);
     const bool one_graph = !p.node_graph || __all_sync(kFullMask, !valid || gid == gid0);
     const int c0w = __shfl_sync(kFullMask, c0v, 0);
-    const int sw = __shfl_sync(kFullMask, sv, 0);
+    if (p.gmark && valid && (lane == 0 || !one_graph)) p.gmark[gid] = t;  // graph still changing
+    if (!one_graph) {
+      // rows of several graphs in this warp: count each graph's lanes apart
+      // (the rows are not yet synced, so X ^ Y is still the delta)
+      unsigned todo = __ballot_sync(kFullMask, valid);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int gl = __shfl_sync(kFullMask, gid, leader);
+        const int cg = __shfl_sync(kFullMask, c0v, leader);
+        const bool mine = valid && gid == gl;
+        todo &= ~__ballot_sync(kFullMask, mine);
+        for (int w = 0; w < Wp; ++w) {
+          const uint64_t d =
+              mine ? (xr[w] ^ __ldg(reinterpret_cast<const unsigned long long *>(yr) + w)) : 0ULL;
+          if (__any_sync(kFullMask, d != 0ULL)) {
+            const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+            const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+            const int c0 = cg + w * 64 + lane;
+            if (n0) atomicAdd(&crow[c0], n0);
+            if (n1) atomicAdd(&crow[c0 + 32], n1);
+          }
+        }
+      }
+    }
     bool full = valid;
     for (int w = 0; w < Wp; ++w) {
       uint64_t o = 0, nw = 0;
@@ -205,31 +236,24 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
         dr[w] = d;
       }
       full = full && ((nw | ~valid_mask(w, sv)) == ~0ULL);
-      if (one_graph) {
-        if (__any_sync(kFullMask, d != 0ULL)) {
-          const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
-          const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
-          const int c0 = w * 64 + lane;
-          if (n0) {
-            if (SMEM)
-              atomicAdd(&scnt[c0], n0);
-            else
-              atomicAdd(&crow[c0w + c0], n0);
-          }
-          if (n1) {
-            if (SMEM)
-              atomicAdd(&scnt[c0 + 32], n1);
-            else
-              atomicAdd(&crow[c0w + c0 + 32], n1);
-          }
+      if (one_graph && __any_sync(kFullMask, d != 0ULL)) {
+        const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+        const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+        const int c0 = w * 64 + lane;
+        if (n0) {
+          if (SMEM)
+            atomicAdd(&scnt[c0], n0);
+          else
+            atomicAdd(&crow[c0w + c0], n0);
         }
-      } else {
-        // rows of several graphs in this warp: count bit by bit
-        for (uint64_t r = d; r; r &= r - 1ULL)
-          atomicAdd(&crow[c0v + w * 64 + __ffsll((long long)r) - 1], 1u);
+        if (n1) {
+          if (SMEM)
+            atomicAdd(&scnt[c0 + 32], n1);
+          else
+            atomicAdd(&crow[c0w + c0 + 32], n1);
+        }
       }
     }
-    (void)sw;
     if (full) set_bit(p.Sat, v);
   }
   // the deltas of round t-1 were read by the pull of round t: clear them
@@ -378,6 +402,7 @@ __global__ void k_window_shift(Params p, int64_t count_words, int32_t rs_slots) 
 // ---------------------------------------------------------------- host side
 struct Plan {
   int CW = 1, G = 4, UNR = 8, L = 32, Wp = 1;
+  bool wide = false;  // pull_wide: a warp per row piece
   PullFn pull = nullptr;
   int grid_pull = 1, grid_post = 1;
   size_t post_smem = 0;
@@ -414,7 +439,26 @@ static int auto_group(double mean_degree, int unr) {
 static pg_status make_plan(const pg_graph *g, int sp, const pg_options &o, bool s_mode, Plan &pl) {
   const int W = s_mode ? 1 : (sp + 63) / 64;
   pl.CW = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
+  if (o.words_per_thread != 0) {
+    const int c = o.words_per_thread;
+    if (c < 0 || c > 8 || (c & (c - 1))) return PG_EINVAL;
+    pl.CW = std::min(pl.CW, c);
+  }
   pl.Wp = (W + pl.CW - 1) / pl.CW * pl.CW;
+  if (o.wide_rows < 0 || o.wide_rows > 2) return PG_EINVAL;
+  if (W > 8 && o.wide_rows != 2) {
+    // a warp per row piece, lanes over the row's words (pull_wide.cu)
+    pl.CW = 8;
+    pl.Wp = (W + 7) / 8 * 8;
+    pl.UNR = 8;
+    pl.G = 32;
+    pl.L = kWidePiece;
+    pl.pull = pull_fn_wide(pl.Wp);
+    pl.smem_counts = sp <= kSmemCountMax;
+    pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)sp : 0;
+    pl.wide = true;
+    return PG_OK;
+  }
   pl.UNR = pl.CW <= 2 ? 8 : (pl.CW == 4 ? 4 : 2);
   int G = o.group_lanes > 0 ? o.group_lanes : auto_group(g->mean_degree, pl.UNR);
   if (G > 32 || (G & (G - 1))) return PG_EINVAL;
@@ -619,7 +663,7 @@ struct BatchSeg {
 static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bool eb,
                           int hint, PassOut &po, const BatchSeg *bs = nullptr) {
   pg_graph *g = cl.g;
-  Workspace &w = g->ws;
+  Workspace &w = g->ext_ws ? *g->ext_ws : g->ws;
   cudaStream_t st = cl.st;
   Plan pl;
   const int s_bits = bs ? bs->s_bits : sp;
@@ -632,7 +676,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   rc = ensure_pieces(g, pl.L, st);
   if (rc) return rc;
-  if (cl.o.direction != PG_DIR_SPARSE && (rc = ensure_sell(g, kSellPiece, st))) return rc;
+  if (cl.o.direction != PG_DIR_SPARSE && !pl.wide && (rc = ensure_sell(g, kSellPiece, st)))
+    return rc;
   const int64_t n = g->n;
   const int64_t nbm = (n + 31) / 32;
   const int32_t row_cap = cl.row_cap;
@@ -649,7 +694,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       (rc = ensure(w.counts, sizeof(uint32_t) * (size_t)row_cap * ncols)) ||
       (rc = ensure(w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2))) ||
       (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)) ||
-      (bs && (rc = ensure(w.seed_bits, sizeof(int32_t) * sp))))
+      (bs && (rc = ensure(w.seed_bits, sizeof(int32_t) * sp))) ||
+      (g->nseg > 0 && (rc = ensure(w.gmark, sizeof(int32_t) * (size_t)g->nseg))))
     return rc;
   if (!w.ctrl_h) {
     if (cudaMallocHost((void **)&w.ctrl_h, 2 * sizeof(Ctrl)) != cudaSuccess) {
@@ -688,7 +734,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.sell_col = (const int32_t *)g->sell.col.p;
   p.sell_off = (const int64_t *)g->sell.off.p;
   p.sell_len = (const int32_t *)g->sell.len.p;
-  p.sell_chunks = cl.o.direction != PG_DIR_SPARSE ? g->sell.nchunks : 0;
+  p.sell_chunks = cl.o.direction != PG_DIR_SPARSE && !pl.wide ? g->sell.nchunks : 0;
   p.L = pl.L;
   p.LE = kExpandArcs;
   p.counts = (uint32_t *)w.counts.p;
@@ -696,6 +742,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.node_graph = bs ? bs->node_graph : nullptr;
   p.graph_s = bs ? bs->graph_s : nullptr;
   p.graph_col0 = bs ? bs->graph_col0 : nullptr;
+  // a packed batch: dense rounds skip the chunks of graphs that did not
+  // change in the previous round (their rows cannot change any more)
+  const bool seg = bs && g->nseg > 0;
+  p.gmark = seg ? (int32_t *)w.gmark.p : nullptr;
+  p.sell_seg = seg && !pl.wide && g->sell.seg.p ? (const int32_t *)g->sell.seg.p : nullptr;
   p.rs = (RoundStats *)w.rs.p;
   p.ctrl = (Ctrl *)w.ctrl.p;
   p.max_rounds = cl.max_rounds;
@@ -738,6 +789,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   rc = cuda_status(cudaMemcpyAsync(w.seeds.p, seeds_h, sizeof(int32_t) * sp,
                                    cudaMemcpyHostToDevice, st));
+  if (rc == PG_OK && p.gmark)
+    rc = cuda_status(cudaMemsetAsync(p.gmark, 0xFF, sizeof(int32_t) * (size_t)g->nseg, st));
   if (rc == PG_OK && bs)
     rc = cuda_status(cudaMemcpyAsync(w.seed_bits.p, bs->seed_bit, sizeof(int32_t) * sp,
                                      cudaMemcpyHostToDevice, st));
@@ -1010,23 +1063,28 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   return status == PG_ERANGE ? PG_ERANGE : PG_OK;
 }
 
-// Runs one packed batch (see batch.cu): all seeds of all graphs in one pass;
-// each copied counts window goes to the caller's sink.
-pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
-                                int32_t nseeds, const int32_t *node_graph_d,
-                                const int32_t *graph_s_d, const int32_t *graph_col0_d,
-                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
-                                WindowSink sink, void *sink_ctx, int32_t *rounds,
-                                const pg_options *opt, void *stream, pg_stats *st_out) {
-  if (!g || !seeds || !seed_bit || nseeds < 1 || ncols < 1 || s_bits < 1 || max_rounds < 0 ||
-      !sink)
+// One PROPAGATE-P pass whose counts windows go to a sink: the seeds of a
+// packed batch (bs set) or of several requests merged on one graph (seed i
+// owns bit and column i; a node may carry several bits).
+static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseeds,
+                                const BatchSeg *bs, int32_t max_rounds, WindowSink sink,
+                                void *sink_ctx, int32_t *rounds, const pg_options *opt,
+                                void *stream, pg_stats *st_out) {
+  const int32_t ncols = bs ? bs->ncols : nseeds;
+  if (!g || !seeds || nseeds < 1 || ncols < 1 || max_rounds < 0 || !sink || !rounds)
     return PG_EINVAL;
+  for (int32_t i = 0; i < nseeds; ++i)
+    if (seeds[i] < 0 || seeds[i] >= g->n) return PG_EINVAL;
   std::lock_guard<std::mutex> lk(g->mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != g->device) return PG_EINVAL;
   Call cl;
   cl.g = g;
   cl.st = (cudaStream_t)stream;
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
+  if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
   cl.s_total = ncols;
   cl.max_rounds = max_rounds;
   cl.counts_h = nullptr;
@@ -1035,9 +1093,8 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
   int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ncols));
   if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
   cl.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
-  BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits};
   PassOut po;
-  pg_status rc = run_pass(cl, seeds, nseeds, 0, false, g->hint_p, po, &bs);
+  pg_status rc = run_pass(cl, seeds, nseeds, 0, false, g->hint_p, po, bs);
   if (rc) {
     cudaGetLastError();
     return rc;
@@ -1055,14 +1112,64 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
     st.rows_gathered += r.gathered;
     st.items += r.items;
     st.changed_rows += r.changed;
+    st.frontier_arcs += r.fsum;
   }
   st.sweeps = po.rounds + 1;
   st.passes = 1;
   st.launches = po.launches;
   st.dense_rounds = po.dense_rounds;
+  st.ms_pull = po.ms_pull;
+  st.ms_post = po.ms_post;
+  st.ms_init = po.ms_init;
+  st.pull_launches = po.pull_launches;
+  st.post_launches = po.post_launches;
+  {
+    Plan pl;
+    if (make_plan(g, bs ? bs->s_bits : nseeds, cl.o, false, pl) == PG_OK) {
+      st.words_per_row = pl.Wp;
+      st.group_lanes = pl.G;
+    }
+  }
+  st.test_changed = cl.o.test_changed == 1 ||
+                    (cl.o.test_changed == 0 && g->n * (int64_t)st.words_per_row * 8 > (64LL << 20));
   g->last = st;
   if (st_out) *st_out = st;
   return po.status == PG_ERANGE ? PG_ERANGE : PG_OK;
+}
+
+pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
+                                int32_t nseeds, const int32_t *node_graph_d,
+                                const int32_t *graph_s_d, const int32_t *graph_col0_d,
+                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
+                                WindowSink sink, void *sink_ctx, int32_t *rounds,
+                                const pg_options *opt, void *stream, pg_stats *st_out) {
+  if (!seed_bit || !node_graph_d || !graph_s_d || !graph_col0_d || s_bits < 1) return PG_EINVAL;
+  BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits};
+  return propagate_sink(g, seeds, nseeds, &bs, max_rounds, sink, sink_ctx, rounds, opt, stream,
+                        st_out);
+}
+
+int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows) {
+  // the buffers run_pass ensures, sized for the widest plan of s seeds
+  const int64_t n = g->n, m = g->m;
+  const int W = (s + 63) / 64;
+  const int CW = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
+  const int64_t Wp = (W + CW - 1) / CW * CW;
+  const int64_t nbm = (n + 31) / 32;
+  const int64_t pieces = n + m / 2 + 1;  // pieces hold at least 2 arcs
+  const int64_t cap_rows =
+      window_rows > 0 ? window_rows : std::max<int64_t>(64, (256LL << 20) / (4LL * s));
+  const int64_t row_cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
+  return 4 * n * Wp * 8 + 5 * nbm * 4 + 2 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
+         pieces * 16 + row_cap * s * 4 + (row_cap + 2) * (int64_t)sizeof(RoundStats) +
+         (int64_t)s * 8 + 4096;
+}
+
+pg_status propagate_columns(pg_graph *g, const int32_t *seeds, int32_t nseeds, int32_t max_rounds,
+                            WindowSink sink, void *sink_ctx, int32_t *rounds,
+                            const pg_options *opt, void *stream, pg_stats *st_out) {
+  return propagate_sink(g, seeds, nseeds, nullptr, max_rounds, sink, sink_ctx, rounds, opt,
+                        stream, st_out);
 }
 
 }  // namespace pg
@@ -1082,6 +1189,8 @@ void pg_default_options(pg_options *o) {
   o->use_graphs = 1;
   o->timing = 0;
   o->window_rows = 0;
+  o->words_per_thread = 0;
+  o->wide_rows = 0;
 }
 
 pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,

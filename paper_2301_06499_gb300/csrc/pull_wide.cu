@@ -1,0 +1,151 @@
+// Pull kernel for wide signatures (many seeds per node): a warp per row
+// piece, its 32 lanes spread over the row's words.
+//
+// Same round as k_pull (Alg. 1 inner loop on the deltas of round t-1): for
+// each in-neighbour u of the piece, Sig_next(v) |= D_{t-1}(u). With W words
+// per node, lane l holds words l, l + 32, l + 64, ... of the row, so the
+// warp reads each gathered neighbour row as one contiguous 8·W-byte segment
+// (256 bytes per 32 words) instead of W/8 separate 64-byte pieces; column
+// indices are loaded 32 at a time (one per lane), their changed bits tested
+// in parallel, and the surviving neighbours broadcast by shuffle. Dense rounds
+// walk the row-major piece list of every unsaturated row, sparse rounds the
+// pieces the post kernel claimed. Activity, statistics, frontier appends and
+// the finish of split rows follow k_pull.
+#include "kernels.cuh"
+
+namespace pg {
+
+// NW words per lane held in registers (rows of up to 32·NW words); NW = 0
+// sweeps a longer row in passes of 32 words, re-reading the piece's columns
+// (from L1) in each pass.
+template <int NW>
+__global__ void __launch_bounds__(kBlock) k_pull_wide(Params p) {
+  constexpr int R = NW > 0 ? NW : 1;  // words per lane per pass
+  Ctrl *ctrl = p.ctrl;
+  if (*(volatile int32_t *)&ctrl->done) return;
+  const int t = ctrl->t;
+  const bool dense = ctrl->mode == kModeDense;
+  const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
+  const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
+  int32_t *F = (t & 1) ? p.F1 : p.F0;
+  uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
+  uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
+  uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
+
+  const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * kBlock;
+  for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
+
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid >> 5;
+  const int64_t nwarps = nthreads >> 5;
+  const int Wp = p.Wp;
+  const int passes = NW > 0 ? 1 : (Wp + 31) / 32;
+  const ulonglong2 *list = dense ? p.Pall : p.A;
+  const int64_t nitems = dense ? p.nPall : (int64_t)ctrl->nA;
+  unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
+
+  for (int64_t item = warp; item < nitems; item += nwarps) {
+    const ulonglong2 it = list[item];
+    const int64_t b = (int64_t)it.x;
+    const int32_t v = (int32_t)(it.y >> 32);
+    const bool whole = (it.y & 0x80000000ULL) != 0ULL;
+    const int len = (int)(it.y & 0x7FFFFFFFULL);
+    if (len == 0) continue;
+    if (dense && test_bit(p.Sat, v)) continue;  // warp-uniform
+    // a packed batch: a graph without a change in round t-1 has none in t
+    if (dense && p.gmark && __ldg(p.gmark + __ldg(p.node_graph + v)) != t - 1) continue;
+    const uint64_t *xr = p.X + (size_t)v * Wp;
+    uint64_t *yr = p.Y + (size_t)v * Wp;
+    bool any_delta = false, row_changed = false;
+    for (int pass = 0; pass < passes; ++pass) {
+      const int w0 = pass * 32 * R + lane;  // lane's first word of this pass
+      uint64_t acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = 0ULL;
+      for (int a0 = 0; a0 < len; a0 += 32) {
+        int32_t u = a0 + lane < len ? __ldg(p.col + b + a0 + lane) : -1;
+        if (u >= 0 && p.test_changed && !test_bit(Cprev, u)) u = -1;
+        unsigned m = __ballot_sync(kFullMask, u >= 0);
+        if (pass == 0 && lane == 0) my_gath += (unsigned long long)__popc(m);
+        while (m) {  // four neighbours at a time: their loads are independent
+          int32_t uu[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int src = m ? __ffs(m) - 1 : 0;
+            uu[q] = m ? __shfl_sync(kFullMask, u, src) : -1;
+            m &= m ? m - 1 : 0u;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (uu[q] >= 0) {
+              const uint64_t *dr = Dprev + (size_t)uu[q] * Wp;
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                const int w = w0 + 32 * r;
+                if (w < Wp) acc[r] |= __ldg(reinterpret_cast<const unsigned long long *>(dr) + w);
+              }
+            }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int w = w0 + 32 * r;
+        if (w >= Wp) continue;
+        any_delta |= acc[r] != 0ULL;
+        if (whole) {
+          const uint64_t own = __ldg(reinterpret_cast<const unsigned long long *>(xr) + w);
+          const uint64_t nw = own | acc[r];
+          if (nw != own) {
+            yr[w] = nw;
+            row_changed = true;
+          }
+        } else if (acc[r]) {
+          const unsigned long long old =
+              atomicOr(reinterpret_cast<unsigned long long *>(yr + w), (unsigned long long)acc[r]);
+          row_changed |= (old | acc[r]) != old;
+        }
+      }
+    }
+    any_delta = __any_sync(kFullMask, any_delta);
+    row_changed = __any_sync(kFullMask, row_changed);
+    bool app = false;
+    if (lane == 0) {
+      ++my_items;
+      my_scan += (unsigned long long)len;
+      if (dense && any_delta) {  // active in round t (sparse rounds count at the claim)
+        unsigned long long deg = 0;
+        if (whole)
+          deg = (unsigned long long)len;
+        else if (!set_bit(Kcur, v))
+          deg = (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        my_mact += deg;
+        my_work += deg * (unsigned long long)seeds_of(p, v);
+      }
+      if (row_changed && (dense ? any_delta : true)) {
+        if (whole) {
+          atomicOr(Ccur + (v >> 5), 1u << (v & 31));
+          app = true;
+        } else {
+          app = !set_bit(Ccur, v);
+        }
+      }
+    }
+    frontier_append(p, ctrl, F, v, app, lane);
+  }
+  RoundStats *r = p.rs + (t - ctrl->row_base);
+  const unsigned long long vals[5] = {my_mact, my_work, my_scan, my_gath, my_items};
+  unsigned long long *const dsts[5] = {&r->m_active, &r->work, &r->scanned, &r->gathered,
+                                       &r->items};
+  block_add<5>(vals, dsts);
+}
+
+PullFn pull_fn_wide(int Wp) {
+  if (Wp <= 32) return &k_pull_wide<1>;
+  if (Wp <= 64) return &k_pull_wide<2>;
+  if (Wp <= 96) return &k_pull_wide<3>;
+  if (Wp <= 128) return &k_pull_wide<4>;
+  return &k_pull_wide<0>;
+}
+
+}  // namespace pg

@@ -135,3 +135,26 @@ def test_batch_rejects_bad_input():
         k = b.add_inputs(g, np.array([0, 5], np.int32))
         with pytest.raises(pg.PropagateError):
             b.result(k)  # no run yet
+
+
+@pytest.mark.parametrize("direction", [pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+def test_batch_forced_direction(direction):
+    """Every round dense (sliced-ELL chunks of finished graphs skipped) or
+    every round sparse; a long path among short graphs of the same width."""
+    items = list(_mix()[:12])
+    extra = [(I.path(400, directed=True), np.array([0, 7, 399], np.int32)),
+             (I.grid(60, 60, 0.05, 71), I.seeds(3600, 64, 72))]
+    with pg.Batch() as b:
+        for it in items:
+            b.add_inputs(it.graph, it.seeds)
+        for g, sd in extra:
+            b.add_inputs(g, sd)
+        b.run(opts=pg.options(direction=direction))
+        for k, it in enumerate(items):
+            want, _ = _plain(it)
+            got = b.result(k)
+            assert got.rounds == want.rounds and np.array_equal(got.counts, want.counts)
+        for j, (g, sd) in enumerate(extra):
+            want = oracle.run(g, sd)
+            got = b.result(len(items) + j)
+            assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])

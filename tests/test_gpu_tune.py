@@ -1,0 +1,113 @@
+"""Autotuner (pg_autotune, pg_batch_tune) and the schedule knobs it turns:
+every words-per-thread / lanes / threshold / changed-test choice gives
+bit-identical counts (checked against the oracle), and the tuner returns
+options whose counts equal the defaults'."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2301_06499_gb300 as pg
+from paper_2301_06499_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def _case(s):
+    g = I.rmat(13, 12, 41, directed=True)
+    seeds = I.seeds(g.n, s, 42)
+    return g, seeds, oracle.run(g, seeds)
+
+
+@pytest.mark.parametrize("s,wpt", [(256, 1), (256, 2), (256, 4), (512, 2), (512, 4),
+                                   (512, 8), (700, 4), (128, 1)])
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+def test_words_per_thread_schedules_identical(s, wpt, direction):
+    g, seeds, want = _case(s)
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_p(G, seeds, opts=pg.options(words_per_thread=wpt, direction=direction))
+    assert res.rounds == want["rounds"]
+    assert np.array_equal(res.counts, want["counts"])
+    assert np.array_equal(res.m_active, want["m_active"])
+
+
+def test_words_per_thread_rejects_bad_values():
+    g, seeds, _ = _case(256)
+    G = pg.Graph.from_inputs(g)
+    for bad in (3, 16, -1):
+        with pytest.raises(pg.PropagateError):
+            pg.propagate_p(G, seeds, opts=pg.options(words_per_thread=bad))
+
+
+def test_autotune_keeps_counts():
+    g, seeds, want = _case(256)
+    G = pg.Graph.from_inputs(g)
+    o, rep = pg.autotune(G, seeds, max_trials=12)
+    assert 1 <= rep["trials"] <= 12
+    assert rep["best_ms"] <= rep["default_ms"] + 1e-9
+    res = pg.propagate_p(G, seeds, opts=o)
+    assert np.array_equal(res.counts, want["counts"])
+    d = pg.options_dict(o)
+    assert d["words_per_thread"] in (0, 1, 2, 4)
+    assert d["group_lanes"] in (0, 1, 2, 4, 8, 16, 32)
+
+
+def test_batch_tune_then_run():
+    items = I.mix(16, 500, 20_000, 8)
+    with pg.Batch() as b:
+        for it in items:
+            b.add_inputs(it.graph, it.seeds)
+        rep = b.tune(max_trials=6)
+        assert rep["trials"] >= 1
+        b.run()  # tuned options
+        groups = b.group_options()
+        assert sum(ng for ng, _ in groups) == len(items)
+        for k, it in enumerate(items):
+            want = oracle.run(it.graph, it.seeds)
+            got = b.result(k)
+            assert got.rounds == want["rounds"]
+            assert np.array_equal(got.counts, want["counts"])
+
+
+# ------------------------------------------------------------ wide rows
+@functools.lru_cache(maxsize=None)
+def _wide_case(kind, s):
+    if kind == "rmat":  # hubs: rows longer than one 256-arc piece
+        g = I.rmat(14, 16, 51, directed=True)
+    else:
+        g = I.er(12_000, 10, 52)
+    seeds = I.seeds(g.n, s, 53)
+    return g, seeds, oracle.run(g, seeds)
+
+
+@pytest.mark.parametrize("kind,s", [("rmat", 520), ("rmat", 1024), ("er", 2047), ("rmat", 2100),
+                                    ("er", 4100), ("rmat", 6000), ("er", 8200)])
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+def test_wide_rows_identical(kind, s, direction):
+    """Every words-per-lane class of the wide kernel (1-4 words in registers,
+    and the generic passes above 128 words), split rows, both round kinds."""
+    g, seeds, want = _wide_case(kind, s)
+    G = pg.Graph.from_inputs(g)
+    for wide in (0, 2):
+        res = pg.propagate_p(G, seeds, opts=pg.options(direction=direction, wide_rows=wide))
+        assert res.rounds == want["rounds"], wide
+        assert np.array_equal(res.counts, want["counts"]), wide
+        assert np.array_equal(res.m_active, want["m_active"]), wide
+
+
+def test_wide_rows_in_batch_and_server():
+    g, seeds, want = _wide_case("er", 2047)
+    g2, seeds2, want2 = _wide_case("rmat", 2100)
+    with pg.Batch() as b:
+        b.add_inputs(g, seeds)
+        b.add_inputs(g2, seeds2)
+        b.run()
+        assert np.array_equal(b.result(0).counts, want["counts"])
+        assert np.array_equal(b.result(1).counts, want2["counts"])
+    with pg.Server(slots=2) as srv:
+        a = srv.submit(srv.add_inputs(g), seeds)
+        c = srv.submit(srv.add_inputs(g2), seeds2)
+        assert np.array_equal(srv.result(a)[0].counts, want["counts"])
+        assert np.array_equal(srv.result(c)[0].counts, want2["counts"])
