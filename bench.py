@@ -745,8 +745,10 @@ def run_reference(args):
 
 def profile_run(args):
     """Builds the workload and calls PROPAGATE-P or -S twice with plain
-    launches (no CUDA graph), the program profiled by ncu: its pull launches
-    are the first call's, then the second call's (one per round)."""
+    launches and per-launch events (no CUDA graph): the program profiled by
+    ncu. The second call runs like a timed bench call (the first call's
+    round count is its hint); prints each call's pull launches, so that a
+    capture can skip the first call."""
     import torch
     torch.cuda.set_device(0)
     import paper_2301_06499_gb300 as pg
@@ -756,9 +758,13 @@ def profile_run(args):
     seeds = I.seeds(g.n, s, seed_stream(args.workload, 0))
     G = pg.Graph.from_inputs(g)
     fn = pg.propagate_p if args.profile_run == "p" else pg.propagate_s
+    calls = []
     for _ in range(2):
-        res = fn(G, seeds, opts=pg.options(use_graphs=0))
-    print(json.dumps({"workload": args.workload, "rounds": res.rounds, **G.last_stats()}))
+        res = fn(G, seeds, opts=pg.options(use_graphs=0, timing=1))
+        st = G.last_stats()
+        calls.append({"pull_launches": st["pull_launches"], "post_launches": st["post_launches"],
+                      "rounds": res.rounds, "ms_pull": st["ms_pull"]})
+    print(json.dumps({"workload": args.workload, "calls": calls}))
 
 
 def main():

@@ -120,6 +120,14 @@ typedef struct {
                                the words (one contiguous read per gathered
                                neighbour); 2 = lanes over 8-word chunks as
                                for narrower rows (words_per_thread applies) */
+  int32_t passes_together;  /* PROPAGATE-S: passes run as one propagation over
+                               that many copies of the graph side by side
+                               (passes never exchange bits), as far as a
+                               quarter of the free device memory holds the
+                               copies; 1 = one pass at a time; 0 = automatic:
+                               as many as keep the copies under 2^24 arcs
+                               (small graphs, where one pass cannot fill the
+                               GPU) */
 } pg_options;
 
 #define PG_DIR_AUTO 0

@@ -33,6 +33,7 @@ struct pg_batch {
     pg_graph *g = nullptr;
     pg::DevBuf node_graph, graph_s, graph_col0;
     std::vector<int32_t> seeds, seed_bit, col0;
+    std::vector<int64_t> graph_m;  // arcs of each member
     int32_t ncols = 0, s_bits = 0, max_rounds = 0;
     bool tuned = false;
     pg_options opt{};  // chosen by pg_batch_tune
@@ -105,6 +106,7 @@ pg_status build_groups(pg_batch *b, cudaStream_t st) {
       }
       graph_s.push_back(s);
       graph_col0.push_back(ncols);
+      gr.graph_m.push_back(it.m);
       ncols += s;
       s_bits = std::max(s_bits, s);
       maxr = std::max<int32_t>(maxr, (int32_t)std::min<int64_t>(it.n - 1, 0x3FFFFFFF));
@@ -248,8 +250,8 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
     const pg_options *o = opt ? opt : (gr.tuned ? &gr.opt : nullptr);
     rc = propagate_batch_group(gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
                                (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
-                               (const int32_t *)gr.graph_col0.p, gr.ncols, gr.s_bits,
-                               gr.max_rounds, &take_window, &ctx, &T, o, stream, &st1);
+                               (const int32_t *)gr.graph_col0.p, gr.graph_m.data(), gr.ncols,
+                               gr.s_bits, gr.max_rounds, &take_window, &ctx, &T, o, stream, &st1);
     if (rc) {
       for (auto &it : b->items) {
         it.counts.clear();
@@ -289,8 +291,8 @@ pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report,
       pg_status e = propagate_batch_group(
           gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
           (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
-          (const int32_t *)gr.graph_col0.p, gr.ncols, gr.s_bits, gr.max_rounds, &hash_window, &hc,
-          &T, &o, stream, nullptr);
+          (const int32_t *)gr.graph_col0.p, gr.graph_m.data(), gr.ncols, gr.s_bits,
+          gr.max_rounds, &hash_window, &hc, &T, &o, stream, nullptr);
       const auto t1 = std::chrono::steady_clock::now();
       if (e) return e;
       *ms = std::chrono::duration<double, std::milli>(t1 - t0).count();

@@ -21,14 +21,16 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kFsumBits = 37;
 constexpr unsigned long long kFsumMask = (1ULL << kFsumBits) - 1ULL;
 
-enum : int32_t { kModeDense = 0, kModeSparse = 1 };
+// kModeMixed (packed batches): each graph of the union picks its own kind
+// of round from its own frontier (see Params::gfsum).
+enum : int32_t { kModeDense = 0, kModeSparse = 1, kModeMixed = 2 };
 
 // Device-side control block of one propagation (one pass).
 struct Ctrl {
   int32_t t;            // round being executed
   int32_t done;         // 1 once the fixpoint (or an error) is reached
   int32_t status;       // pg_status of the device side
-  int32_t mode;         // kModeDense / kModeSparse for round t
+  int32_t mode;         // kModeDense / kModeSparse / kModeMixed for round t
   unsigned long long fpack;  // frontier F_t: (count << kFsumBits) | out-arc sum
   unsigned long long nA;     // pieces in the sparse work list of round t
   unsigned long long nA_next;
@@ -87,7 +89,11 @@ struct Params {
   const int32_t *graph_s;     // batch: seeds of each graph
   const int32_t *graph_col0;  // batch: first count column of each graph
   const int32_t *sell_seg;    // batch: graph of each sliced-ELL chunk
-  int32_t *gmark;             // batch: last round in which each graph had a changed row
+  // batch: out-arc sum of each graph's frontier, [2][graphs] by round parity,
+  // and the sum above which that graph's next round is a full sweep
+  unsigned long long *gfsum;
+  const unsigned long long *gthr;
+  int32_t nseg;               // batch: graphs in the union
   RoundStats *rs;       // [row_cap + 2], slot = round - row_base
   Ctrl *ctrl;
   int32_t max_rounds;
@@ -117,7 +123,7 @@ struct DevBuf {
 
 struct Workspace {
   DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds, seed_bits,
-      gmark;
+      gfsum, gthr;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -163,6 +169,11 @@ struct pg_graph {
   // a packed batch: the graph of each node (device, borrowed) and how many
   const int32_t *seg_of = nullptr;
   int32_t nseg = 0;
+  // PROPAGATE-S passes run together: rep_K copies of this graph side by side
+  // (make_replicas), the copy of each node, and per-call pass tables
+  pg_graph *rep = nullptr;
+  int32_t rep_K = 0;
+  pg::DevBuf rep_graph_of, rep_graph_s, rep_graph_col0;
   double mean_degree = 0.0;
   int64_t max_degree = 0;
   pg::PieceList pieces;
@@ -196,12 +207,14 @@ void drop_graph_cache(pg_graph *g);
 // Receives each copied-out counts window of a batch run.
 typedef void (*WindowSink)(void *ctx, int32_t row_base, int32_t rows, const uint32_t *data,
                            int32_t ncols);
+// graph_m: host, arcs of each graph (each picks its own kind of round).
 pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
                                 int32_t nseeds, const int32_t *node_graph_d,
                                 const int32_t *graph_s_d, const int32_t *graph_col0_d,
-                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
-                                WindowSink sink, void *sink_ctx, int32_t *rounds,
-                                const pg_options *opt, void *stream, pg_stats *st_out);
+                                const int64_t *graph_m, int32_t ncols, int32_t s_bits,
+                                int32_t max_rounds, WindowSink sink, void *sink_ctx,
+                                int32_t *rounds, const pg_options *opt, void *stream,
+                                pg_stats *st_out);
 // Seeds of several requests merged on one graph: seed i owns bit and count
 // column i, and a node may carry several seeds; windows go to the sink.
 pg_status propagate_columns(pg_graph *g, const int32_t *seeds, int32_t nseeds, int32_t max_rounds,
@@ -218,6 +231,10 @@ typedef std::function<pg_status(const pg_options &, double *ms, uint64_t *hash)>
 pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, pg_options *inout,
                        pg_tune_report *rep);
 uint64_t fnv1a(uint64_t h, const void *data, size_t bytes);
+// K copies of g side by side, cached in g (see pg_graph::rep); PG_EINVAL if
+// they would not fit the index ranges.
+pg_status make_replicas(pg_graph *g, int K, cudaStream_t st);
+void drop_replicas(pg_graph *g);
 // Device bytes a propagation of s seeds on g will hold in its workspace
 // (window_rows as pg_options.window_rows).
 int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows);

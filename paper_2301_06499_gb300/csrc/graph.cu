@@ -159,17 +159,45 @@ __global__ void k_count_out(const int32_t *col, int64_t m, unsigned long long *c
     atomicAdd(&cnt[col[j]], 1ULL);
 }
 
-__global__ void __launch_bounds__(kBlock) k_scatter_out(const int64_t *rp, const int32_t *col,
-                                                        int64_t n, unsigned long long *cursor,
+// Transpose scatter over row pieces of at most kScatterPiece arcs, a thread
+// per piece. Rows are sorted, so at step k the lanes of a warp often hold the
+// same source (a hub): lanes with equal sources take their slots with one
+// fetch-and-add by the lowest of them, which keeps hub cursors uncontended.
+constexpr int kScatterPiece = 32;
+
+__global__ void __launch_bounds__(kBlock) k_scatter_out(const ulonglong2 *pieces, int64_t np,
+                                                        const int32_t *col,
+                                                        unsigned long long *cursor,
                                                         int32_t *out_col) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-  for (int64_t v = warp; v < n; v += nwarps)
-    for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
-      unsigned long long pos = atomicAdd(&cursor[col[j]], 1ULL);
-      out_col[pos] = (int32_t)v;
+  const int64_t nth = (int64_t)gridDim.x * kBlock;
+  // whole warps iterate, so that the lane matching sees every lane
+  for (int64_t base = ((int64_t)blockIdx.x * kBlock + threadIdx.x) & ~31LL; base < np;
+       base += nth) {
+    const int64_t i = base + lane;
+    int64_t first = 0;
+    int32_t v = 0;
+    int len = 0;
+    if (i < np) {
+      const ulonglong2 it = pieces[i];
+      first = (int64_t)it.x;
+      v = (int32_t)(it.y >> 32);
+      len = (int)(it.y & 0x7FFFFFFFULL);
     }
+    int most = len;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(kFullMask, most, off));
+    for (int k = 0; k < most; ++k) {
+      const int32_t u = k < len ? __ldg(col + first + k) : -1;
+      const unsigned peers = __match_any_sync(kFullMask, u);
+      const int leader = __ffs(peers) - 1;
+      unsigned long long pos = 0;
+      if (u >= 0 && lane == leader)
+        pos = atomicAdd(&cursor[u], (unsigned long long)__popc(peers));
+      pos = __shfl_sync(kFullMask, pos, leader);
+      if (u >= 0) out_col[pos + __popc(peers & ((1u << lane) - 1u))] = v;
+    }
+  }
 }
 
 __global__ void k_max_degree(const int64_t *rp, int64_t n, unsigned long long *mx) {
@@ -428,7 +456,7 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
 
 void release_workspace(Workspace &w) {
   for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0, &w.F1,
-                    &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gmark})
+                    &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum, &w.gthr})
     release(*b);
   if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
   w.ctrl_h = nullptr;
@@ -444,9 +472,90 @@ int64_t workspace_held(const Workspace &w) {
   int64_t b = 0;
   for (const DevBuf *x : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.F0,
                           &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits,
-                          &w.gmark})
+                          &w.gfsum, &w.gthr})
     b += (int64_t)x->bytes;
   return b;
+}
+
+// K copies of a CSR side by side: copy k's rows are k*n.., its arcs k*m..,
+// its column indices shifted by k*n.
+__global__ void k_replicate(const int64_t *rp, const int32_t *col, int64_t n, int64_t m, int K,
+                            int64_t *rp_out, int32_t *col_out) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = gtid; i < (int64_t)K * n; i += nth) {
+    const int64_t k = i / n;
+    rp_out[i] = k * m + rp[i - k * n];
+  }
+  if (gtid == 0) rp_out[(int64_t)K * n] = (int64_t)K * m;
+  for (int64_t j = gtid; j < (int64_t)K * m; j += nth) {
+    const int64_t k = j / m;
+    col_out[j] = (int32_t)(col[j - k * m] + k * n);
+  }
+}
+
+__global__ void k_fill_graph_of(int32_t *node_graph, int64_t n, int K) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)K * n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    node_graph[i] = (int32_t)(i / n);
+}
+
+pg_status make_replicas(pg_graph *g, int K, cudaStream_t st) {
+  if (g->rep && g->rep_K == K) return PG_OK;
+  drop_replicas(g);
+  const int64_t n = g->n, m = g->m, Kn = (int64_t)K * n, Km = (int64_t)K * m;
+  if (K < 2 || Kn >= 0x7FFFFFFFLL || Km >= (1LL << kFsumBits)) return PG_EINVAL;
+  pg_graph *r = new pg_graph();
+  r->n = Kn;
+  r->m = Km;
+  r->directed = g->directed;
+  r->device = g->device;
+  r->mean_degree = g->mean_degree;
+  r->max_degree = g->max_degree;
+  pg_status rc = cuda_status(cudaMalloc((void **)&r->row_ptr, sizeof(int64_t) * (Kn + 1)));
+  if (!rc) rc = cuda_status(cudaMalloc((void **)&r->col, sizeof(int32_t) * std::max<int64_t>(Km, 1)));
+  if (!rc) {
+    k_replicate<<<grid_for(std::max(Kn, Km)), kBlock, 0, st>>>(g->row_ptr, g->col, n, m, K,
+                                                               r->row_ptr, r->col);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (!rc && g->out_ptr == g->row_ptr) {
+    r->out_ptr = r->row_ptr;
+    r->out_col = r->col;
+    r->owns_out = false;
+  } else if (!rc) {
+    rc = cuda_status(cudaMalloc((void **)&r->out_ptr, sizeof(int64_t) * (Kn + 1)));
+    if (!rc)
+      rc = cuda_status(cudaMalloc((void **)&r->out_col, sizeof(int32_t) * std::max<int64_t>(Km, 1)));
+    if (!rc) {
+      k_replicate<<<grid_for(std::max(Kn, Km)), kBlock, 0, st>>>(g->out_ptr, g->out_col, n, m, K,
+                                                                 r->out_ptr, r->out_col);
+      rc = cuda_status(cudaGetLastError());
+    }
+  }
+  if (!rc) rc = ensure(g->rep_graph_of, sizeof(int32_t) * (size_t)Kn);
+  if (!rc) {
+    k_fill_graph_of<<<grid_for(Kn), kBlock, 0, st>>>((int32_t *)g->rep_graph_of.p, n, K);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc) {
+    pg_graph_free(r);
+    release(g->rep_graph_of);
+    return rc;
+  }
+  r->seg_of = (const int32_t *)g->rep_graph_of.p;
+  r->nseg = K;
+  g->rep = r;
+  g->rep_K = K;
+  return PG_OK;
+}
+
+void drop_replicas(pg_graph *g) {
+  if (g->rep) pg_graph_free(g->rep);
+  g->rep = nullptr;
+  g->rep_K = 0;
+  for (DevBuf *b : {&g->rep_graph_of, &g->rep_graph_s, &g->rep_graph_col0}) release(*b);
 }
 
 pg_status make_view(pg_graph *master, cudaStream_t st, pg_graph **out) {
@@ -523,6 +632,7 @@ void pg_graph_free(pg_graph *g) {
     if (g->owns_sell)
       for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len, &g->sell.seg})
         release(*b);
+    drop_replicas(g);
     release_workspace(g->ws);
   }
   delete g;
@@ -609,8 +719,14 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
       if (rc == PG_OK) rc = exclusive_scan_i64(g->out_ptr, n + 1, st);
       if (rc == PG_OK) {
         cudaMemcpyAsync(cursor, g->out_ptr, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st);
-        k_scatter_out<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, n, cursor, g->out_col);
-        rc = cuda_status(cudaGetLastError());
+        // row pieces of at most kScatterPiece arcs (scratch; the graph's
+        // cached piece list is built later for the pull's own piece length)
+        rc = ensure_pieces(g, kScatterPiece, st);
+        if (rc == PG_OK) {
+          k_scatter_out<<<grid_for(g->pieces.count), kBlock, 0, st>>>(
+              (const ulonglong2 *)g->pieces.list.p, g->pieces.count, g->col, cursor, g->out_col);
+          rc = cuda_status(cudaGetLastError());
+        }
       }
       if (cursor) cudaFreeAsync(cursor, st);
       if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
@@ -619,6 +735,7 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
   if (rc != PG_OK) {
     cudaGetLastError();
     free_graph_arrays(g);
+    release(g->pieces.list);
     delete g;
     return rc;
   }

@@ -197,6 +197,16 @@ __device__ __forceinline__ void frontier_append(const Params &p, Ctrl *ctrl, int
   if (lane == 0)
     basep = atomicAdd(&ctrl->fpack, ((unsigned long long)__popc(mask) << kFsumBits) + odt);
   basep = __shfl_sync(kFullMask, basep, 0);
+  if (p.gfsum) {  // a packed batch: each graph's own frontier out-arcs
+    unsigned long long *gf = p.gfsum + (size_t)(ctrl->t & 1) * (size_t)p.nseg;
+    const int gid = app ? __ldg(p.node_graph + v) : -1;
+    const int g0 = __shfl_sync(kFullMask, gid, __ffs(mask) - 1);
+    if (__all_sync(kFullMask, !app || gid == g0)) {
+      if (lane == 0 && odt) atomicAdd(gf + g0, odt);
+    } else if (app && od) {
+      atomicAdd(gf + gid, od);
+    }
+  }
   if (app) {
     const int rank = __popc(mask & ((1u << lane) - 1u));
     F[(int64_t)(basep >> kFsumBits) + rank] = v;
@@ -293,8 +303,11 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       clen_next = __ldg(p.sell_len + cn);
       off_next = __ldg(p.sell_off + cn);
     }
-    // a packed batch: a graph without a change in round t-1 has none in t
-    if (p.sell_seg && __ldg(p.gmark + __ldg(p.sell_seg + c)) != ctrl->t - 1) continue;
+    // a packed batch: only the graphs whose own frontier chose a full sweep
+    if (p.gfsum) {
+      const int gs = __ldg(p.sell_seg + c);
+      if (p.gfsum[(size_t)((ctrl->t - 1) & 1) * (size_t)p.nseg + gs] <= __ldg(p.gthr + gs)) continue;
+    }
     const int32_t v = (int32_t)(it.y >> 32);
     const bool whole = (it.y & 0x80000000ULL) != 0ULL;
     const int len = (int)(it.y & 0x7FFFFFFFULL);
@@ -402,7 +415,7 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
   const int t = ctrl->t;
-  const bool dense = ctrl->mode == kModeDense;
+  const int mode = ctrl->mode;
   const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
   const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
   int32_t *F = (t & 1) ? p.F1 : p.F0;
@@ -418,10 +431,12 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
   unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
-  if (dense) {
+  // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
+  // of the graphs that chose a full sweep and take the others' work list
+  if (mode != kModeSparse)
     pull_dense<CW>(p, ctrl, Dprev, Cprev, F, Ccur, Kcur, lane, warp, nwarps, my_mact, my_work,
                    my_scan, my_gath, my_items);
-  } else {
+  if (mode != kModeDense) {
     const int gl = lane & (G - 1);
     const int gw = lane / G;
     const int64_t nitems = (int64_t)ctrl->nA;

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
         p.F0[atomicAdd(&nf, 1u)] = x;
         od = (unsigned long long)(p.out_ptr[x + 1] - p.out_ptr[x]);
         atomicAdd(&tot, od);
+        if (p.gfsum && od) atomicAdd(p.gfsum + p.node_graph[x], od);  // round 0's parity
       }
     }
     const unsigned long long ne = first ? (od + p.LE - 1) / p.LE : 0ULL;
@@ -177,8 +178,9 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
   const int Wp = p.Wp, s = p.s;
   uint32_t *crow = p.counts + (size_t)row * (size_t)p.ncols;
 
+  uint32_t *cdst = SMEM ? scnt : crow;  // per-seed counters of this block / of the round
   if (SMEM) {
-    for (int i = threadIdx.x; i < s; i += kBlock) scnt[i] = 0u;
+    for (int i = threadIdx.x; i < p.ncols; i += kBlock) scnt[i] = 0u;
     __syncthreads();
   }
   // A. count, record deltas, sync, saturation
@@ -199,7 +201,6 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
     const int gid0 = __shfl_sync(kFullMask, gid, 0);
     const bool one_graph = !p.node_graph || __all_sync(kFullMask, !valid || gid == gid0);
     const int c0w = __shfl_sync(kFullMask, c0v, 0);
-    if (p.gmark && valid && (lane == 0 || !one_graph)) p.gmark[gid] = t;  // graph still changing
     if (!one_graph) {
       // rows of several graphs in this warp: count each graph's lanes apart
       // (the rows are not yet synced, so X ^ Y is still the delta)
@@ -217,8 +218,8 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
             const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
             const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
             const int c0 = cg + w * 64 + lane;
-            if (n0) atomicAdd(&crow[c0], n0);
-            if (n1) atomicAdd(&crow[c0 + 32], n1);
+            if (n0) atomicAdd(&cdst[c0], n0);
+            if (n1) atomicAdd(&cdst[c0 + 32], n1);
           }
         }
       }
@@ -239,19 +240,9 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
       if (one_graph && __any_sync(kFullMask, d != 0ULL)) {
         const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
         const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
-        const int c0 = w * 64 + lane;
-        if (n0) {
-          if (SMEM)
-            atomicAdd(&scnt[c0], n0);
-          else
-            atomicAdd(&crow[c0w + c0], n0);
-        }
-        if (n1) {
-          if (SMEM)
-            atomicAdd(&scnt[c0 + 32], n1);
-          else
-            atomicAdd(&crow[c0w + c0 + 32], n1);
-        }
+        const int c0 = c0w + w * 64 + lane;
+        if (n0) atomicAdd(&cdst[c0], n0);
+        if (n1) atomicAdd(&cdst[c0 + 32], n1);
       }
     }
     if (full) set_bit(p.Sat, v);
@@ -263,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
   }
   if (SMEM) {
     __syncthreads();
-    for (int i = threadIdx.x; i < s; i += kBlock) {
+    for (int i = threadIdx.x; i < p.ncols; i += kBlock) {
       const uint32_t c = scnt[i];
       if (c) atomicAdd(&crow[i], c);
     }
@@ -272,9 +263,17 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
 
   // B. next direction and sparse work list
   const bool next_dense =
-      p.direction == PG_DIR_DENSE ||
-      (p.direction == PG_DIR_AUTO && (double)fsum > (double)p.dense_threshold * (double)p.m);
+      !p.gfsum && (p.direction == PG_DIR_DENSE ||
+                   (p.direction == PG_DIR_AUTO &&
+                    (double)fsum > (double)p.dense_threshold * (double)p.m));
   const bool expand = !next_dense && nF > 0 && t + 1 <= p.max_rounds + 1;
+  // a packed batch decides per graph: a graph whose frontier out-arcs exceed
+  // its own threshold is swept whole in round t+1 and not expanded here
+  const unsigned long long *gf_cur = p.gfsum ? p.gfsum + (size_t)(t & 1) * (size_t)p.nseg : nullptr;
+  if (p.gfsum) {
+    unsigned long long *gf_next = p.gfsum + (size_t)((t + 1) & 1) * (size_t)p.nseg;
+    for (int64_t i = gtid; i < p.nseg; i += nth) gf_next[i] = 0ULL;
+  }
   unsigned long long my_mact = 0, my_work = 0;
   if (expand) {
     // one thread per expansion piece of LE out-arcs, UNR arcs at a time
@@ -286,9 +285,12 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
         const unsigned long long it = p.E[i];
         const int32_t u = (int32_t)(it >> 32);
         const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
-        const int64_t o1 = __ldg(p.out_ptr + u + 1);
-        ob = __ldg(p.out_ptr + u) + k * p.LE;
-        oe = min(o1, ob + (int64_t)p.LE);
+        const int gu = gf_cur ? __ldg(p.node_graph + u) : 0;
+        if (!gf_cur || gf_cur[gu] <= __ldg(p.gthr + gu)) {
+          const int64_t o1 = __ldg(p.out_ptr + u + 1);
+          ob = __ldg(p.out_ptr + u) + k * p.LE;
+          oe = min(o1, ob + (int64_t)p.LE);
+        }
       }
       for (int h = 0; h < p.LE; h += UNR) {
         int32_t x[UNR];
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_post(Params p) {
       ctrl->done = 1;
     } else {
       ctrl->t = t + 1;
-      ctrl->mode = next_dense ? kModeDense : kModeSparse;
+      ctrl->mode = p.gfsum ? kModeMixed : next_dense ? kModeDense : kModeSparse;
       if (next_dense) ctrl->dense_rounds += 1;
       ctrl->nA = *(volatile unsigned long long *)&ctrl->nA_next;
       ctrl->nA_next = 0ULL;
@@ -656,6 +658,7 @@ struct BatchSeg {
   const int32_t *seed_bit;    // host, each seed's index within its graph
   int32_t ncols;              // count columns (sum of the graphs' seeds)
   int32_t s_bits;             // most seeds of one graph (bits per node)
+  const int64_t *graph_m;     // host, arcs of each graph (per-graph round kinds)
 };
 
 // One pass: sp seeds of the call, columns [col0, col0+sp); or, with bs, all
@@ -670,9 +673,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   const int ncols = bs ? bs->ncols : sp;
   pg_status rc = make_plan(g, s_bits, cl.o, eb, pl);
   if (rc) return rc;
-  if (bs) {
-    pl.smem_counts = false;  // a batch's columns exceed one block's counters
-    pl.post_smem = 0;
+  if (bs) {  // a batch's columns: in shared memory when they fit
+    pl.smem_counts = ncols <= kSmemCountMax;
+    pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)ncols : 0;
   }
   rc = ensure_pieces(g, pl.L, st);
   if (rc) return rc;
@@ -695,7 +698,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       (rc = ensure(w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2))) ||
       (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)) ||
       (bs && (rc = ensure(w.seed_bits, sizeof(int32_t) * sp))) ||
-      (g->nseg > 0 && (rc = ensure(w.gmark, sizeof(int32_t) * (size_t)g->nseg))))
+      (bs && g->nseg > 0 &&
+       ((rc = ensure(w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg)) ||
+        (rc = ensure(w.gthr, sizeof(unsigned long long) * (size_t)g->nseg)))))
     return rc;
   if (!w.ctrl_h) {
     if (cudaMallocHost((void **)&w.ctrl_h, 2 * sizeof(Ctrl)) != cudaSuccess) {
@@ -742,11 +747,13 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.node_graph = bs ? bs->node_graph : nullptr;
   p.graph_s = bs ? bs->graph_s : nullptr;
   p.graph_col0 = bs ? bs->graph_col0 : nullptr;
-  // a packed batch: dense rounds skip the chunks of graphs that did not
-  // change in the previous round (their rows cannot change any more)
-  const bool seg = bs && g->nseg > 0;
-  p.gmark = seg ? (int32_t *)w.gmark.p : nullptr;
-  p.sell_seg = seg && !pl.wide && g->sell.seg.p ? (const int32_t *)g->sell.seg.p : nullptr;
+  // a packed batch: each graph picks its own kind of round (the sliced-ELL
+  // chunks are per graph; finished graphs have no frontier and cost nothing)
+  const bool seg = bs && g->nseg > 0 && bs->graph_m;
+  p.gfsum = seg ? (unsigned long long *)w.gfsum.p : nullptr;
+  p.gthr = seg ? (const unsigned long long *)w.gthr.p : nullptr;
+  p.nseg = seg ? g->nseg : 0;
+  p.sell_seg = seg && !pl.wide ? (const int32_t *)g->sell.seg.p : nullptr;
   p.rs = (RoundStats *)w.rs.p;
   p.ctrl = (Ctrl *)w.ctrl.p;
   p.max_rounds = cl.max_rounds;
@@ -789,8 +796,19 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   rc = cuda_status(cudaMemcpyAsync(w.seeds.p, seeds_h, sizeof(int32_t) * sp,
                                    cudaMemcpyHostToDevice, st));
-  if (rc == PG_OK && p.gmark)
-    rc = cuda_status(cudaMemsetAsync(p.gmark, 0xFF, sizeof(int32_t) * (size_t)g->nseg, st));
+  if (rc == PG_OK && p.gfsum) {
+    std::vector<unsigned long long> thr((size_t)g->nseg);
+    const double f = p.dense_threshold;
+    for (int32_t k = 0; k < g->nseg; ++k)
+      thr[k] = cl.o.direction == PG_DIR_DENSE    ? 0ULL
+               : cl.o.direction == PG_DIR_SPARSE ? ~0ULL
+                                                 : (unsigned long long)(f * (double)bs->graph_m[k]);
+    rc = cuda_status(cudaMemsetAsync(p.gfsum, 0, 2 * sizeof(unsigned long long) * g->nseg, st));
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(w.gthr.p, thr.data(), sizeof(unsigned long long) * g->nseg,
+                                       cudaMemcpyHostToDevice, st));
+    if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));  // thr outlives the copy
+  }
   if (rc == PG_OK && bs)
     rc = cuda_status(cudaMemcpyAsync(w.seed_bits.p, bs->seed_bit, sizeof(int32_t) * sp,
                                      cudaMemcpyHostToDevice, st));
@@ -967,6 +985,34 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   return PG_OK;
 }
 
+// How many PROPAGATE-S passes run together (over replicas of the graph).
+// Automatic: only while the copies together stay small (kReplicaArcs arcs):
+// one pass of a larger graph already fills the GPU, and there the copies'
+// per-graph bookkeeping costs more than the launches it saves (measured on
+// a 65 M-arc R-MAT). Always as far as a quarter of the free device memory
+// holds the copies and their workspace and node ids stay below 2^31.
+constexpr int64_t kReplicaArcs = 1LL << 24;
+
+static int passes_together(const pg_graph *g, int npasses, const pg_options &o) {
+  if (npasses < 2 || o.passes_together == 1) return 1;
+  int K = o.passes_together > 1
+              ? std::min(o.passes_together, npasses)
+              : (int)std::min<int64_t>(npasses, kReplicaArcs / std::max<int64_t>(g->m, 1));
+  if (K < 2) return 1;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int64_t csr = (g->n + 1) * 8 + g->m * 4;
+  // in/out CSR, sliced-ELL and piece lists, and a one-word workspace
+  const int64_t per_copy = csr * (g->directed ? 2 : 1) + g->m * 5 + g->n * 64;
+  while (K > 1 && ((int64_t)K * per_copy > (int64_t)(fr / 4) || (int64_t)K * g->n >= 0x7FFFFFFFLL ||
+                   (int64_t)K * g->m >= (1LL << kFsumBits)))
+    --K;
+  return K;
+}
+
 static pg_status check_seeds(const pg_graph *g, const int32_t *seeds, int32_t s) {
   if (!seeds || s < 1 || s > g->n) return PG_EINVAL;
   std::vector<int32_t> v(seeds, seeds + s);
@@ -1008,7 +1054,85 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   int32_t T = 0, status = PG_OK;
   int passes = 0;
   int &hint = s_mode ? g->hint_s : g->hint_p;
-  for (int b = 0; b < s; b += planes) {
+  const int npasses = (s + planes - 1) / planes;
+  const int K = s_mode ? passes_together(g, npasses, cl.o) : 1;
+  if (K > 1) {
+    // PROPAGATE-S passes K at a time, as one propagation over K copies of the
+    // graph: pass k's planes live in copy k (its seeds shifted by k*n), its
+    // counts in columns k*planes.. of the group; copies never exchange bits
+    if ((rc = make_replicas(g, K, cl.st))) return rc;
+    pg_graph *r = g->rep;
+    if ((rc = ensure(g->rep_graph_s, sizeof(int32_t) * K)) ||
+        (rc = ensure(g->rep_graph_col0, sizeof(int32_t) * K)))
+      return rc;
+    for (int b0 = 0; b0 < s; b0 += K * planes) {
+      const int ns = std::min(K * planes, s - b0);
+      std::vector<int32_t> rs(ns), bit(ns), gs(K, 1), gc(K, 0);
+      std::vector<int64_t> gm(K, g->m);
+      for (int i = 0; i < ns; ++i) {
+        const int k = i / planes;
+        rs[i] = seeds[b0 + i] + (int32_t)((int64_t)k * g->n);
+        bit[i] = i - k * planes;
+        gs[k] = std::min(planes, ns - k * planes);
+        gc[k] = k * planes;
+      }
+      if ((rc = cuda_status(cudaMemcpyAsync(g->rep_graph_s.p, gs.data(), sizeof(int32_t) * K,
+                                            cudaMemcpyHostToDevice, cl.st))) ||
+          (rc = cuda_status(cudaMemcpyAsync(g->rep_graph_col0.p, gc.data(), sizeof(int32_t) * K,
+                                            cudaMemcpyHostToDevice, cl.st))))
+        return rc;
+      Call cr;
+      cr.g = r;
+      cr.st = cl.st;
+      cr.o = cl.o;
+      cr.s_total = s;
+      cr.max_rounds = cl.max_rounds;
+      cr.counts_h = cl.counts_h;
+      int64_t rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ns));
+      if (cl.o.window_rows > 0) rows = cl.o.window_rows;
+      cr.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)out->max_rounds + 1, rows));
+      BatchSeg bs{(const int32_t *)g->rep_graph_of.p, (const int32_t *)g->rep_graph_s.p,
+                  (const int32_t *)g->rep_graph_col0.p, bit.data(), ns, planes, gm.data()};
+      PassOut po;
+      rc = run_pass(cr, rs.data(), ns, b0, true, r->hint_s, po, &bs);
+      if (rc == PG_OK && po.status == PG_OK) r->hint_s = std::min(po.rounds + 1, 64);
+      if (rc) {
+        cudaGetLastError();
+        return rc;
+      }
+      passes += (ns + planes - 1) / planes;
+      if (cl.rs_h.size() < cr.rs_h.size()) cl.rs_h.resize(cr.rs_h.size(), RoundStats{});
+      for (size_t t = 0; t < cr.rs_h.size(); ++t) {
+        RoundStats &d = cl.rs_h[t];
+        const RoundStats &x = cr.rs_h[t];
+        d.work += x.work;
+        d.m_active += x.m_active;
+        d.scanned += x.scanned;
+        d.gathered += x.gathered;
+        d.items += x.items;
+        d.changed += x.changed;
+        d.fsum += x.fsum;
+      }
+      // rows that only some groups reached: the others' columns are zero there
+      if (po.rounds < T) {
+        for (int32_t t = po.rounds + 1; t <= std::min(T, out->max_rounds); ++t)
+          std::memset(out->counts + (size_t)t * s + b0, 0, sizeof(uint32_t) * ns);
+      } else if (po.rounds > T && b0 > 0) {
+        for (int32_t t = T + 1; t <= std::min(po.rounds, out->max_rounds); ++t)
+          std::memset(out->counts + (size_t)t * s, 0, sizeof(uint32_t) * b0);
+      }
+      T = std::max(T, po.rounds);
+      if (po.status == PG_ERANGE) status = PG_ERANGE;
+      st.dense_rounds += po.dense_rounds;
+      st.launches += po.launches;
+      st.ms_pull += po.ms_pull;
+      st.ms_post += po.ms_post;
+      st.ms_init += po.ms_init;
+      st.pull_launches += po.pull_launches;
+      st.post_launches += po.post_launches;
+    }
+  }
+  for (int b = 0; K <= 1 && b < s; b += planes) {
     const int sp = std::min(planes, s - b);
     PassOut po;
     rc = run_pass(cl, seeds + b, sp, b, s_mode, hint, po);
@@ -1140,11 +1264,12 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
 pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t *seed_bit,
                                 int32_t nseeds, const int32_t *node_graph_d,
                                 const int32_t *graph_s_d, const int32_t *graph_col0_d,
-                                int32_t ncols, int32_t s_bits, int32_t max_rounds,
-                                WindowSink sink, void *sink_ctx, int32_t *rounds,
-                                const pg_options *opt, void *stream, pg_stats *st_out) {
+                                const int64_t *graph_m, int32_t ncols, int32_t s_bits,
+                                int32_t max_rounds, WindowSink sink, void *sink_ctx,
+                                int32_t *rounds, const pg_options *opt, void *stream,
+                                pg_stats *st_out) {
   if (!seed_bit || !node_graph_d || !graph_s_d || !graph_col0_d || s_bits < 1) return PG_EINVAL;
-  BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits};
+  BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits, graph_m};
   return propagate_sink(g, seeds, nseeds, &bs, max_rounds, sink, sink_ctx, rounds, opt, stream,
                         st_out);
 }
@@ -1191,6 +1316,7 @@ void pg_default_options(pg_options *o) {
   o->window_rows = 0;
   o->words_per_thread = 0;
   o->wide_rows = 0;
+  o->passes_together = 0;
 }
 
 pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,

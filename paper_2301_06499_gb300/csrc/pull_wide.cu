@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_wide(Params p) {
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
   const int t = ctrl->t;
-  const bool dense = ctrl->mode == kModeDense;
+  const int mode = ctrl->mode;
   const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
   const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
   int32_t *F = (t & 1) ? p.F1 : p.F0;
@@ -41,20 +41,25 @@ __global__ void __launch_bounds__(kBlock) k_pull_wide(Params p) {
   const int64_t nwarps = nthreads >> 5;
   const int Wp = p.Wp;
   const int passes = NW > 0 ? 1 : (Wp + 31) / 32;
-  const ulonglong2 *list = dense ? p.Pall : p.A;
-  const int64_t nitems = dense ? p.nPall : (int64_t)ctrl->nA;
   unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
+  // dense: every row's pieces; sparse: the claimed pieces; mixed (a packed
+  // batch): the pieces of graphs that chose a full sweep, then the claimed ones
+  const int64_t ndense = mode != kModeSparse ? p.nPall : 0;
+  const int64_t nitems = ndense + (mode != kModeDense ? (int64_t)ctrl->nA : 0);
 
   for (int64_t item = warp; item < nitems; item += nwarps) {
-    const ulonglong2 it = list[item];
+    const bool dense = item < ndense;
+    const ulonglong2 it = dense ? p.Pall[item] : p.A[item - ndense];
     const int64_t b = (int64_t)it.x;
     const int32_t v = (int32_t)(it.y >> 32);
     const bool whole = (it.y & 0x80000000ULL) != 0ULL;
     const int len = (int)(it.y & 0x7FFFFFFFULL);
     if (len == 0) continue;
     if (dense && test_bit(p.Sat, v)) continue;  // warp-uniform
-    // a packed batch: a graph without a change in round t-1 has none in t
-    if (dense && p.gmark && __ldg(p.gmark + __ldg(p.node_graph + v)) != t - 1) continue;
+    if (dense && p.gfsum) {  // a packed batch: only graphs in a full sweep
+      const int gs = __ldg(p.node_graph + v);
+      if (p.gfsum[(size_t)((t - 1) & 1) * (size_t)p.nseg + gs] <= __ldg(p.gthr + gs)) continue;
+    }
     const uint64_t *xr = p.X + (size_t)v * Wp;
     uint64_t *yr = p.Y + (size_t)v * Wp;
     bool any_delta = false, row_changed = false;

@@ -2,9 +2,10 @@
 
   python -m paper_2301_06499_gb300.ncu_summary launches <launches.csv>
       per kernel: launches, total device time, share (markdown table)
-  python -m paper_2301_06499_gb300.ncu_summary traffic <metrics.csv> <workload> <kernel_hash>
-      per kernel: mean DRAM bytes (read + write) per launch (JSON, the form
-      bench.py reads from profiles/pull_traffic.json)
+  python -m paper_2301_06499_gb300.ncu_summary traffic <metrics.csv> <workload> <kernel_hash> [skip]
+      per kernel: mean DRAM bytes (read + write) per launch, over its launches
+      after the first `skip` of that kernel (JSON, the form bench.py reads
+      from profiles/pull_traffic.json)
 """
 from __future__ import annotations
 
@@ -52,15 +53,20 @@ def launches(path):
             for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1])}
 
 
-def traffic(path):
+def traffic(path, skip: int = 0):
     per = collections.defaultdict(lambda: collections.defaultdict(float))
     for r in _rows(path):
         m = r.get("Metric Name")
         if m not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             continue
         b = float(r["Metric Value"].replace(",", "")) * _UNIT_B.get(r["Metric Unit"], 1.0)
-        per[short_name(r["Kernel Name"])][r["ID"]] += b
-    return {k: sum(v.values()) / len(v) for k, v in per.items()}
+        per[short_name(r["Kernel Name"])][int(r["ID"])] += b
+    out = {}
+    for k, v in per.items():
+        ids = sorted(v)[skip:]
+        if ids:
+            out[k] = sum(v[i] for i in ids) / len(ids)
+    return out
 
 
 def main(argv):
@@ -72,7 +78,7 @@ def main(argv):
             print(f"| `{k}` | {v['launches']} | {v['total_ms']:.3f} | {v['share']:.3f} |")
         return 0
     if len(argv) >= 4 and argv[0] == "traffic":
-        res = traffic(argv[1])
+        res = traffic(argv[1], int(argv[4]) if len(argv) > 4 else 0)
         print(json.dumps({"workload": argv[2], "kernel_hash": argv[3],
                           "bytes_per_launch": res}, indent=1))
         return 0

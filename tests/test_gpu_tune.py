@@ -111,3 +111,30 @@ def test_wide_rows_in_batch_and_server():
         c = srv.submit(srv.add_inputs(g2), seeds2)
         assert np.array_equal(srv.result(a)[0].counts, want["counts"])
         assert np.array_equal(srv.result(c)[0].counts, want2["counts"])
+
+
+# ------------------------------------------------ PROPAGATE-S passes together
+def _oracle_s_mactive(g, seeds, planes, rounds):
+    _, _, dmat = oracle.seed_histograms(g, seeds, with_distances=True)
+    total = np.zeros(rounds + 2, dtype=np.uint64)
+    for b in range(0, len(seeds), planes):
+        sub = np.ascontiguousarray(dmat[:, b:b + planes])
+        part = oracle.m_active(g, sub, int(sub.max()) + 1)
+        total[:part.size] += part
+    return total
+
+
+@pytest.mark.parametrize("planes", [64, 17, 1])
+@pytest.mark.parametrize("together", [1, 2, 3, 0])
+def test_s_passes_together_identical(planes, together):
+    g = I.rmat(12, 10, 81, directed=True)
+    seeds = I.seeds(g.n, 150, 82)
+    want = oracle.run(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_s(G, seeds, opts=pg.options(planes_per_pass=planes,
+                                                   passes_together=together))
+    assert res.rounds == want["rounds"]
+    assert np.array_equal(res.counts, want["counts"])
+    assert np.array_equal(res.m_active, _oracle_s_mactive(g, seeds, planes, want["rounds"]))
+    st = G.last_stats()
+    assert st["passes"] == -(-150 // planes)
