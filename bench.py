@@ -51,6 +51,10 @@ WORKLOADS = {
     "rmat23_undirected_s512": (dict(kind="rmat", scale=23, ef=16, seed=2, directed=False), 512,
                                "undirected R-MAT scale 23, edge factor 16, s=512 (profiling "
                                "stand-in for scale 26)"),
+    # the serving workload's widest requests: eps = 0.05 on n = 1e6 gives
+    # s = ceil(ln n / eps^2) rounded to 64 = 5568 seeds (87 words per node)
+    "er1e6_s5568": (dict(kind="er", n=1_000_000, d=16, seed=6), 5568,
+                    "undirected ER n=1e6 avg degree 16, s=5568 (wide signatures)"),
 }
 # Batched workload: 512 graphs, n log-uniform in [1e3, 1e6], ER / R-MAT / grid
 # with RNG seed 4, s per graph from eps in {0.1, 0.2} (see inputs.mix).
@@ -68,7 +72,7 @@ SERVE_WORKLOADS = {
                         variants=4),
 }
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
-            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2}
+            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2, "er1e6_s5568": 7}
 
 
 def make_graph(spec):
@@ -183,8 +187,10 @@ def pull_bytes(st: dict) -> float:
 def kernel_name(st: dict) -> str:
     """Name of the pull kernel instantiation a call used (words per gather,
     lanes per group), as ncu prints it."""
-    wp = st["words_per_row"]
-    cw = 1 if wp <= 1 else 2 if wp <= 2 else 4 if wp <= 4 else 8
+    wp, cw = st["words_per_row"], st["words_per_gather"]
+    if cw == 0:  # the wide-row kernel: words per lane held in registers
+        nw = 1 if wp <= 32 else 2 if wp <= 64 else 3 if wp <= 96 else 4 if wp <= 128 else 0
+        return f"k_pull_wide<{nw}>"
     return f"k_pull<{cw}, {st['group_lanes']}>"
 
 
@@ -207,21 +213,43 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sptr = __import__("ctypes").c_void_p(stream.cuda_stream)
     G = pg.Graph.from_inputs(g, stream=sptr)
-    opts_time = pg.options(timing=1)
-    opts_run = pg.options(use_graphs=0 if args.plain_launches else 1)
+    # schedule options: the library's autotuner picks them for this graph and
+    # these seeds (untimed; counts are checked identical across candidates)
+    tuned = None
+    o_p, o_s = pg.options(), pg.options()
+    if args.tune:
+        t0 = time.perf_counter()
+        o_p, rep_p = pg.autotune(G, seeds, max_trials=args.tune_trials, stream=sptr)
+        o_s, rep_s = pg.autotune(G, seeds, max_trials=args.tune_trials, stream=sptr,
+                                 algorithm="s")
+        keys = ("direction", "dense_threshold", "group_lanes", "test_changed",
+                "words_per_thread", "wide_rows", "passes_together")
+        tuned = {"tune_s": time.perf_counter() - t0,
+                 "p": {k: pg.options_dict(o_p)[k] for k in keys} | {"trials": rep_p["trials"]},
+                 "s": {k: pg.options_dict(o_s)[k] for k in keys} | {"trials": rep_s["trials"]}}
+
+    def with_(o, **kw):
+        o2 = pg.options(**{k: getattr(o, k) for k, _ in o._fields_})
+        for k, v in kw.items():
+            setattr(o2, k, v)
+        return o2
+
+    opts_time_p, opts_time_s = with_(o_p, timing=1), with_(o_s, timing=1)
+    plain = 0 if args.plain_launches else 1
+    opts_run_p, opts_run_s = with_(o_p, use_graphs=plain), with_(o_s, use_graphs=plain)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
-    def step(opts):
-        rp = pg.propagate_p(G, seeds, opts=opts, stream=sptr)
+    def step():
+        rp = pg.propagate_p(G, seeds, opts=opts_time_p, stream=sptr)
         stp = G.last_stats()
-        rs = pg.propagate_s(G, seeds, opts=opts, stream=sptr)
+        rs = pg.propagate_s(G, seeds, opts=opts_time_s, stream=sptr)
         sts = G.last_stats()
         pg.metrics(rp, g.n)
         return rp, rs, stp, sts
 
     # warm-up (also fixes the per-step work)
     for _ in range(args.warmup):
-        rp, rs, stp, sts = step(opts_time)
+        rp, rs, stp, sts = step()
     assert np.array_equal(rp.counts, rs.counts), "PROPAGATE-P and -S disagree"
     work_p = rp.seed_edge_traversals
     work_step = 2 * work_p
@@ -236,10 +264,10 @@ def run_ours(args):
             flush.fill_(1)  # L2 flush, outside the timed events
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            rp = pg.propagate_p(G, seeds, opts=opts_time, stream=sptr)
+            rp = pg.propagate_p(G, seeds, opts=opts_time_p, stream=sptr)
             stp = G.last_stats()
             e1.record(stream)
-            rs = pg.propagate_s(G, seeds, opts=opts_time, stream=sptr)
+            rs = pg.propagate_s(G, seeds, opts=opts_time_s, stream=sptr)
             sts = G.last_stats()
             pg.metrics(rp, g.n)
             e2.record(stream)
@@ -274,8 +302,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = pg.Graph.from_csr(rp_pinned, col_pinned, g.n, directed=g.directed, stream=sptr)
-        r1 = pg.propagate_p(G2, seeds, opts=opts_run, stream=sptr)
-        r2 = pg.propagate_s(G2, seeds, opts=opts_run, stream=sptr)
+        r1 = pg.propagate_p(G2, seeds, opts=opts_run_p, stream=sptr)
+        r2 = pg.propagate_s(G2, seeds, opts=opts_run_s, stream=sptr)
         pg.metrics(r1, g.n)
         G2.close()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -317,7 +345,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m, "s": s,
                    "rounds": rp.rounds, "seed_edge_traversals_per_step": work_step,
                    "l2": "flushed between steps (512 MB write); inputs also exceed L2",
-                   "parallelism": f"replicas x{world} (independent seed samples)"},
+                   "parallelism": f"replicas x{world} (independent seed samples)",
+                   "options": tuned or "library defaults (--tune 0)"},
         "parts": {"propagate_p_ms": statistics.mean(p_ms), "propagate_s_ms": statistics.mean(s_ms),
                   "propagate_p_seed_edges_per_s": work_p / (statistics.mean(p_ms) / 1e3),
                   "propagate_s_seed_edges_per_s": work_p / (statistics.mean(s_ms) / 1e3)},
@@ -744,11 +773,11 @@ def run_reference(args):
 
 
 def profile_run(args):
-    """Builds the workload and calls PROPAGATE-P or -S twice with plain
-    launches and per-launch events (no CUDA graph): the program profiled by
-    ncu. The second call runs like a timed bench call (the first call's
-    round count is its hint); prints each call's pull launches, so that a
-    capture can skip the first call."""
+    """Builds the workload, tunes it like the bench, and calls PROPAGATE-P or
+    -S twice with plain launches and per-launch events (no CUDA graph): the
+    program profiled by ncu. The second call runs like a timed bench call
+    (the first call's round count is its hint) inside the NVTX range
+    "bench_call", which captures select; prints each call's launches."""
     import torch
     torch.cuda.set_device(0)
     import paper_2301_06499_gb300 as pg
@@ -758,13 +787,21 @@ def profile_run(args):
     seeds = I.seeds(g.n, s, seed_stream(args.workload, 0))
     G = pg.Graph.from_inputs(g)
     fn = pg.propagate_p if args.profile_run == "p" else pg.propagate_s
+    o = pg.options()
+    if args.tune:  # the schedule the bench times
+        o, _ = pg.autotune(G, seeds, max_trials=args.tune_trials, algorithm=args.profile_run)
+    o.use_graphs, o.timing = 0, 1
     calls = []
-    for _ in range(2):
-        res = fn(G, seeds, opts=pg.options(use_graphs=0, timing=1))
+    for k in range(2):
+        if k == 1:  # the call a capture selects: ncu --nvtx --nvtx-include "bench_call/"
+            torch.cuda.nvtx.range_push("bench_call")
+        res = fn(G, seeds, opts=o)
+        if k == 1:
+            torch.cuda.nvtx.range_pop()
         st = G.last_stats()
         calls.append({"pull_launches": st["pull_launches"], "post_launches": st["post_launches"],
                       "rounds": res.rounds, "ms_pull": st["ms_pull"]})
-    print(json.dumps({"workload": args.workload, "calls": calls}))
+    print(json.dumps({"workload": args.workload, "options": pg.options_dict(o), "calls": calls}))
 
 
 def main():
@@ -777,7 +814,7 @@ def main():
                     sorted(SERVE_WORKLOADS), default="rmat22_directed_s256")
     ap.add_argument("--slots", type=int, default=4, help="server slots (serving workload)")
     ap.add_argument("--tune", type=int, default=1,
-                    help="batched workload: 1 = autotune each width class before timing")
+                    help="1 = let the autotuner pick the schedule options before timing")
     ap.add_argument("--tune-trials", type=int, default=16)
     ap.add_argument("--cpu-seeds", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -57,6 +57,13 @@ typedef struct pg_graph pg_graph;
 #define PG_DEVICE_PTRS 1u /* row_ptr and col are device pointers */
 #define PG_BORROW 2u      /* with PG_DEVICE_PTRS: use the caller's arrays in
                              place; they must outlive the graph */
+#define PG_REVERSE 4u     /* pull along the other direction: the counts are
+                             then balls grown backward, the nodes that reach
+                             each seed (the direction Algorithm 1 literally
+                             iterates, Sig(u) |= Sig(v) for u -> v); the
+                             library pulls over the out-edge transpose it
+                             builds. Directed graphs only (undirected graphs
+                             are their own transpose). */
 
 /*
  * Per-round, per-seed counts. Caller-owned host buffers.
@@ -166,7 +173,9 @@ typedef struct {
   int32_t pull_launches;
   int32_t post_launches;
   int32_t test_changed;      /* 1 if changed bits were tested before gathers */
-  int32_t reserved;
+  int32_t words_per_gather;  /* signature words one lane gathers per arc (the
+                                pull instantiation k_pull<words, lanes>); 0 =
+                                the wide-row kernel (a warp per piece) */
   uint64_t seed_edge_traversals; /* sum over rounds and active rows of
                                s x in-degree (the benchmark's work measure;
                                s of the row's own graph in a batch) */
@@ -188,7 +197,7 @@ void pg_default_options(pg_options *opt);
  *  col      int32[m], each in [0, n), strictly increasing within a row
  *  directed 1: general digraph (the library builds the out-edge transpose);
  *           0: the caller asserts the CSR is symmetric (in = out)
- *  flags    PG_DEVICE_PTRS / PG_BORROW; host arrays are copied
+ *  flags    PG_DEVICE_PTRS / PG_BORROW / PG_REVERSE; host arrays are copied
  *  stream   cudaStream_t for the copies and validation kernels
  * Errors: PG_EINVAL for n < 1, n >= 2^31, m < 0, or a malformed CSR (checked
  * on the device); PG_ENOMEM; PG_ECUDA.
@@ -250,7 +259,8 @@ pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
  * signature words a lane gathers per arc (words_per_thread) and the
  * frontier density at which a round becomes a full sweep (dense_threshold),
  * plus whether changed bits are tested before delta gathers. pg_autotune
- * times PROPAGATE-P on g with these seeds under candidate values, one
+ * times PROPAGATE-P (algorithm PG_ALG_P) or PROPAGATE-S (PG_ALG_S) on g
+ * with these seeds under candidate values, one
  * parameter at a time starting from *inout (coordinate descent; a candidate
  * replaces the current value when it is at least 2% faster), and writes the
  * fastest options back to *inout. Every candidate's counts are compared
@@ -265,8 +275,11 @@ typedef struct {
   double best_ms;       /* best time of the returned options */
 } pg_tune_report;
 
-pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t max_trials,
-                      pg_options *inout, pg_tune_report *report, void *stream);
+#define PG_ALG_P 0 /* PROPAGATE-P (Algorithm 1) */
+#define PG_ALG_S 1 /* PROPAGATE-S (Algorithm 2): also tunes passes_together */
+pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t algorithm,
+                      int32_t max_trials, pg_options *inout, pg_tune_report *report,
+                      void *stream);
 
 /*
  * Allocation-free PROPAGATE-P. The paper has no counterpart: this entry

@@ -27,7 +27,8 @@ import numpy as np
 from . import _abi
 from ._abi import (PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE, PropagateError)
 
-__all__ = ["Graph", "Result", "Batch", "Server", "autotune", "options_dict", "propagate_p", "propagate_s", "metrics", "options",
+__all__ = ["Graph", "Result", "Batch", "Server", "autotune", "options_dict", "progressive",
+           "propagate_p", "propagate_s", "metrics", "options",
            "PropagateError", "PG_DIR_AUTO", "PG_DIR_DENSE", "PG_DIR_SPARSE", "library_path"]
 
 
@@ -72,9 +73,11 @@ class Graph:
 
     @classmethod
     def from_csr(cls, row_ptr, col, n: int | None = None, directed: bool = True,
-                 stream=None) -> "Graph":
+                 stream=None, reverse: bool = False) -> "Graph":
         """row_ptr int64[n+1] and col int32[m] as numpy arrays (copied from the
-        host) or CUDA torch tensors (used in place)."""
+        host) or CUDA torch tensors (used in place). reverse=True counts balls
+        grown backward (nodes reaching each seed; PG_REVERSE)."""
+        rev = _abi.PG_REVERSE if reverse else 0
         L = _abi.lib()
         h = ctypes.c_void_p()
         st = stream if stream is not None else _current_stream()
@@ -85,7 +88,7 @@ class Graph:
             cl = col.to(torch.int32).contiguous()
             n = rp.numel() - 1 if n is None else n
             m = cl.numel()
-            flags = _abi.PG_DEVICE_PTRS | _abi.PG_BORROW
+            flags = _abi.PG_DEVICE_PTRS | _abi.PG_BORROW | rev
             rc = L.pg_graph_from_csr(rp.data_ptr(), cl.data_ptr() if m else None, n, m,
                                      int(directed), flags, st, ctypes.byref(h))
             keep = (rp, cl)
@@ -95,14 +98,15 @@ class Graph:
             n = rp.size - 1 if n is None else n
             m = cl.size
             rc = L.pg_graph_from_csr(rp.ctypes.data, cl.ctypes.data if m else None, n, m,
-                                     int(directed), 0, st, ctypes.byref(h))
+                                     int(directed), rev, st, ctypes.byref(h))
         _abi.check(rc, "pg_graph_from_csr")
         return cls(h, int(n), int(m), keep)
 
     @classmethod
-    def from_inputs(cls, g, stream=None) -> "Graph":
+    def from_inputs(cls, g, stream=None, reverse: bool = False) -> "Graph":
         """From a generated graph (``inputs.Graph``) held in host memory."""
-        return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream)
+        return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream,
+                            reverse=reverse)
 
     def rounds_bound(self) -> int:
         r = ctypes.c_int32()
@@ -189,16 +193,19 @@ def propagate_s(g: Graph, seeds, max_rounds: int | None = None, opts=None,
     return _run(_abi.lib().pg_propagate_s, "pg_propagate_s", g, seeds, max_rounds, opts, stream)
 
 
-def autotune(g: "Graph", seeds, max_trials: int = 24, opts=None, stream=None):
-    """pg_autotune: fastest schedule options for PROPAGATE-P on g with these
-    seeds (counts checked identical across candidates). Returns
-    (options, report dict)."""
+def autotune(g: "Graph", seeds, max_trials: int = 24, opts=None, stream=None,
+             algorithm: str = "p"):
+    """pg_autotune: fastest schedule options for PROPAGATE-P (algorithm "p")
+    or PROPAGATE-S ("s") on g with these seeds (counts checked identical
+    across candidates). Returns (options, report dict)."""
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     st = stream if stream is not None else _current_stream()
     o = opts if opts is not None else options()
+    alg = {"p": _abi.PG_ALG_P, "s": _abi.PG_ALG_S}[algorithm]
     rep = _abi.TuneReport()
-    _abi.check(_abi.lib().pg_autotune(g._h, seeds.ctypes.data, int(seeds.size), int(max_trials),
-                                      ctypes.byref(o), ctypes.byref(rep), st), "pg_autotune")
+    _abi.check(_abi.lib().pg_autotune(g._h, seeds.ctypes.data, int(seeds.size), alg,
+                                      int(max_trials), ctypes.byref(o), ctypes.byref(rep), st),
+               "pg_autotune")
     return o, {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
 
 
@@ -427,6 +434,47 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def progressive(g: "Graph", eps: float, rng_seed: int = 0, block: int = 256,
+                stable_tol: float | None = None, opts=None, stream=None):
+    """Progressive sampling: PROPAGATE-P over seed blocks drawn uniformly
+    without replacement, until the sample reaches ceil(ln n / eps^2) seeds
+    (the order of Thm. 3's sample size, constant 1) or, with stable_tol set,
+    until average distance and effective diameter (interpolated) both move by
+    less than stable_tol (relative) over two consecutive blocks. Seeds never
+    interact, so the counts equal one call with all the drawn seeds.
+
+    Returns (Result over all drawn seeds, seeds, history of metrics)."""
+    n = g.n
+    target = min(n, int(np.ceil(np.log(max(n, 2)) / (eps * eps))))
+    order = np.random.default_rng(rng_seed).permutation(n).astype(np.int32)
+    cols, drawn, hist, T = [], 0, [], 0
+    calm = 0
+    while drawn < target:
+        sd = order[drawn:min(drawn + block, target)]
+        r = propagate_p(g, sd, opts=opts, stream=stream)
+        cols.append(r.counts)
+        drawn += sd.size
+        T = max(T, r.rounds)
+        counts = np.zeros((T + 1, drawn), dtype=np.uint32)
+        c0 = 0
+        for c in cols:
+            counts[:c.shape[0], c0:c0 + c.shape[1]] = c
+            c0 += c.shape[1]
+        res = Result(rounds=T, counts=counts, m_active=np.zeros(T + 2, dtype=np.uint64),
+                     s=drawn, n=n)
+        m = metrics(res, n)
+        if hist and stable_tol is not None:
+            prev = hist[-1]
+            d1 = abs(m["avg_distance"] - prev["avg_distance"]) / max(prev["avg_distance"], 1e-300)
+            d2 = (abs(m["eff_diameter_interp"] - prev["eff_diameter_interp"]) /
+                  max(prev["eff_diameter_interp"], 1e-300))
+            calm = calm + 1 if max(d1, d2) < stable_tol else 0
+        hist.append(dict(m, seeds=drawn))
+        if calm >= 2:
+            break
+    return res, order[:drawn].copy(), hist
 
 
 def metrics(res: Result, n: int | None = None, tau=(9, 10)) -> dict:

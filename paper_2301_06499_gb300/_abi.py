@@ -17,7 +17,9 @@ PG_NOALLOC_SCRATCH_BYTES = 32 << 20
 PG_NOALLOC_MAX_SEEDS = 1024
 PG_DEVICE_PTRS = 1
 PG_BORROW = 2
+PG_REVERSE = 4
 PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
+PG_ALG_P, PG_ALG_S = 0, 1
 
 
 class Options(ctypes.Structure):
@@ -53,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("ms_pull", ctypes.c_double), ("ms_post", ctypes.c_double),
                 ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
                 ("post_launches", ctypes.c_int32), ("test_changed", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
+                ("words_per_gather", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
 
 
 class TuneReport(ctypes.Structure):
@@ -114,7 +116,7 @@ SIGNATURES = {
     "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "pg_propagate_p_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _i32,
                                               ctypes.POINTER(_i32), _vp]),
-    "pg_autotune": (ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.POINTER(Options),
+    "pg_autotune": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, ctypes.POINTER(Options),
                                    ctypes.POINTER(TuneReport), _vp]),
     "pg_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "pg_batch_free": (None, [_vp]),

@@ -302,7 +302,7 @@ pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report,
     pg_options o;
     pg_default_options(&o);
     pg_tune_report r{};
-    if ((rc = tune_options(run, gr.s_bits, max_trials, &o, &r))) return rc;
+    if ((rc = tune_options(run, gr.s_bits, max_trials, &o, &r, false))) return rc;
     gr.opt = o;
     gr.tuned = true;
     sum.trials += r.trials;

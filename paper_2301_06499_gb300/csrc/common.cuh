@@ -229,7 +229,7 @@ pg_status make_view(pg_graph *master, cudaStream_t st, pg_graph **out);
 typedef std::function<pg_status(const pg_options &, double *ms, uint64_t *hash)> TuneRun;
 // Coordinate descent over the schedule options (see tune.cu).
 pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, pg_options *inout,
-                       pg_tune_report *rep);
+                       pg_tune_report *rep, bool s_mode);
 uint64_t fnv1a(uint64_t h, const void *data, size_t bytes);
 // K copies of g side by side, cached in g (see pg_graph::rep); PG_EINVAL if
 // they would not fit the index ranges.

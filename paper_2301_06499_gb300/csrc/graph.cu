@@ -732,6 +732,25 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
       if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
     }
   }
+  if (rc == PG_OK && (flags & PG_REVERSE) && directed) {
+    // pull over the transpose: rows become out-lists, the out-side in-lists
+    std::swap(g->row_ptr, g->out_ptr);
+    std::swap(g->col, g->out_col);
+    std::swap(g->owns_in, g->owns_out);
+    release(g->pieces.list);  // built over the other side for the transpose
+    g->pieces.L = 0;
+    unsigned long long *mx2 = nullptr;
+    rc = cuda_status(cudaMallocAsync((void **)&mx2, sizeof(unsigned long long), st));
+    unsigned long long mxo = 0;
+    if (rc == PG_OK) {
+      cudaMemsetAsync(mx2, 0, sizeof(unsigned long long), st);
+      k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, mx2);
+      rc = cuda_status(cudaMemcpyAsync(&mxo, mx2, sizeof(mxo), cudaMemcpyDeviceToHost, st));
+      cudaFreeAsync(mx2, st);
+      if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    }
+    g->max_degree = (int64_t)mxo;
+  }
   if (rc != PG_OK) {
     cudaGetLastError();
     free_graph_arrays(g);

@@ -247,12 +247,18 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
 }
 
 // Tuning knobs (compile-time): minimum resident blocks per SM for the pull
-// kernel (caps registers) and arcs per lane per step of the dense sweep.
+// kernel (caps registers; the kernels are latency-bound, so occupancy pays:
+// 4 blocks of 256 threads = 64 registers, measured 10% faster than 3 for
+// 4-word rows on R-MAT 22; 8-word rows keep 3, they spill at 64) and arcs
+// per lane per step of the dense sweep.
 #ifndef PG_PULL_MIN_BLOCKS
-#define PG_PULL_MIN_BLOCKS 3
+#define PG_PULL_MIN_BLOCKS 4
+#endif
+#ifndef PG_PULL_MIN_BLOCKS_WIDE
+#define PG_PULL_MIN_BLOCKS_WIDE 3
 #endif
 #ifndef PG_DENSE_UNROLL_NARROW
-#define PG_DENSE_UNROLL_NARROW 8
+#define PG_DENSE_UNROLL_NARROW 4
 #endif
 #ifndef PG_DENSE_UNROLL_WIDE
 #define PG_DENSE_UNROLL_WIDE 4
@@ -260,33 +266,44 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
 
 // Dense round over the sliced-ELL copy: a warp per chunk of 32 pieces, lane
 // l owns piece l; step k reads arc k of all 32 pieces in one coalesced load,
-// and the U deltas of a lane's U steps are gathered together. The next
-// chunk's descriptor is loaded while the current one is processed, and the
-// first U column loads of a piece are issued before its saturation bit is
-// known (only the gathers wait for it), so a short piece costs one column
-// latency and one gather latency.
+// and the U deltas of a lane's U steps are gathered together. The sweep is
+// software-pipelined so that column loads never wait behind gathers:
+//  - within a chunk (rows of up to 4 words), the next U column indices are
+//    loaded before the current U deltas are gathered;
+//  - for narrow rows (1-2 words), the next chunk's descriptor is loaded when
+//    a chunk starts and its first U column indices when the chunk ends
+//    (before the frontier append), ahead of the saturation test: there the
+//    latency matters more than the reads wasted on saturated rows.
 template <int CW>
 __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const uint64_t *Dprev,
                                            const uint32_t *Cprev, int32_t *F, uint32_t *Ccur,
                                            uint32_t *Kcur, int lane,
                                            int64_t warp, int64_t nwarps,
-                                           unsigned long long &my_mact,
+                                           uint32_t &my_mact,
                                            unsigned long long &my_work,
-                                           unsigned long long &my_scan,
-                                           unsigned long long &my_gath,
-                                           unsigned long long &my_items) {
+                                           uint32_t &my_scan,
+                                           uint32_t &my_gath,
+                                           uint32_t &my_items) {
   constexpr int U = CW <= 2 ? PG_DENSE_UNROLL_NARROW : PG_DENSE_UNROLL_WIDE;
-  constexpr bool kPrefetch = CW <= 2;  // measured: helps latency-bound narrow rows only
+  constexpr bool kPrefetch = CW <= 2;
+  constexpr bool kPipe = CW <= 4;  // at 8 words the registers are not there
   const size_t Wp = (size_t)p.Wp;
   const int nch = p.Wp / CW;
   int64_t c = warp;
   ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
   int clen_next = 0;
   int64_t off_next = 0;
+  int32_t u0[U];  // first column batch of the chunk about to start
+  auto first_batch = [&](int len_of, int64_t off) {
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      u0[q] = q < len_of ? __ldg(p.sell_col + off + lane + 32LL * q) : -1;
+  };
   if (kPrefetch && c < p.sell_chunks) {
     it_next = p.sell_items[c * 32 + lane];
     clen_next = __ldg(p.sell_len + c);
     off_next = __ldg(p.sell_off + c);
+    first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
   }
   for (; c < p.sell_chunks; c += nwarps) {
     if (!kPrefetch) {
@@ -298,7 +315,8 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
     const int clen = clen_next;
     const int32_t *cc = p.sell_col + off_next + lane;
     const int64_t cn = c + nwarps;
-    if (kPrefetch && cn < p.sell_chunks) {
+    const bool has_next = kPrefetch && cn < p.sell_chunks;
+    if (has_next) {
       it_next = p.sell_items[cn * 32 + lane];
       clen_next = __ldg(p.sell_len + cn);
       off_next = __ldg(p.sell_off + cn);
@@ -306,21 +324,16 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
     // a packed batch: only the graphs whose own frontier chose a full sweep
     if (p.gfsum) {
       const int gs = __ldg(p.sell_seg + c);
-      if (p.gfsum[(size_t)((ctrl->t - 1) & 1) * (size_t)p.nseg + gs] <= __ldg(p.gthr + gs)) continue;
+      if (p.gfsum[(size_t)((ctrl->t - 1) & 1) * (size_t)p.nseg + gs] <= __ldg(p.gthr + gs)) {
+        if (has_next) first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
+        continue;
+      }
     }
     const int32_t v = (int32_t)(it.y >> 32);
     const bool whole = (it.y & 0x80000000ULL) != 0ULL;
     const int len = (int)(it.y & 0x7FFFFFFFULL);
-    // first batch of column indices: for narrow rows issued before the
-    // saturation test (latency matters more than the wasted reads there)
-    int32_t u0[U];
-    bool act;
-    if constexpr (kPrefetch) {
-#pragma unroll
-      for (int q = 0; q < U; ++q) u0[q] = q < len ? __ldg(cc + 32LL * q) : -1;
-      act = len > 0 && !test_bit(p.Sat, v);
-    } else {
-      act = len > 0 && !test_bit(p.Sat, v);
+    bool act = len > 0 && !test_bit(p.Sat, v);
+    if (!kPrefetch) {
 #pragma unroll
       for (int q = 0; q < U; ++q) u0[q] = act && q < len ? __ldg(cc + 32LL * q) : -1;
     }
@@ -330,15 +343,22 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
 #pragma unroll
       for (int k = 0; k < CW; ++k) own[k] = acc[k] = 0;
       if (act && whole) load_words<CW>(own, p.X + (size_t)v * Wp + ch * CW);
-      for (int k0 = 0; k0 < clen; k0 += U) {
-        int32_t u[U];
-        if (k0 == 0) {
+      int32_t u[U];
 #pragma unroll
-          for (int q = 0; q < U; ++q) u[q] = act ? u0[q] : -1;
-        } else {
+      for (int q = 0; q < U; ++q)
+        u[q] = !act ? -1 : ch == 0 ? u0[q] : (q < len ? __ldg(cc + 32LL * q) : -1);
+      for (int k0 = 0; k0 < clen; k0 += U) {
+        const bool more = kPipe && k0 + U < clen;  // warp-uniform
+        int32_t un[U];
+        if (!kPipe && k0 > 0) {
 #pragma unroll
           for (int q = 0; q < U; ++q)
             u[q] = (act && k0 + q < len) ? __ldg(cc + 32LL * (k0 + q)) : -1;
+        }
+        if (more) {
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+            un[q] = (act && k0 + U + q < len) ? __ldg(cc + 32LL * (k0 + U + q)) : -1;
         }
         if (p.test_changed) {
 #pragma unroll
@@ -351,24 +371,29 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
             or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
             if (ch == 0) ++my_gath;
           }
+        if (more) {
+#pragma unroll
+          for (int q = 0; q < U; ++q) u[q] = un[q];
+        }
       }
 #pragma unroll
       for (int k = 0; k < CW; ++k) any_delta |= acc[k] != 0ULL;
       if (act) row_changed |= finish_piece<CW>(p, v, ch, whole, own, acc);
     }
+    if (has_next) first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
     if (act) {
       ++my_items;
-      my_scan += (unsigned long long)len;
+      my_scan += (uint32_t)len;
     }
     act = act && any_delta;  // no changed in-neighbour: not active in round t
     if (act) {
-      unsigned long long deg = 0;
+      uint32_t deg = 0;
       if (whole)
-        deg = (unsigned long long)len;
+        deg = (uint32_t)len;
       else if (!set_bit(Kcur, v))
-        deg = (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        deg = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
       my_mact += deg;
-      my_work += deg * (unsigned long long)seeds_of(p, v);
+      my_work += (unsigned long long)deg * (unsigned long long)seeds_of(p, v);
     }
     bool app = false;
     if (act && row_changed) {
@@ -409,7 +434,8 @@ struct PullUnroll {
 // L2) is tested before its delta is gathered, so unchanged neighbours cost no
 // signature-sized read: worth it when the deltas are far larger than L2.
 template <int CW, int G>
-__global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
+__global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL_MIN_BLOCKS_WIDE)
+    k_pull(Params p) {
   constexpr int UNR = PullUnroll<CW>::value;
   constexpr int GPW = 32 / G;
   Ctrl *ctrl = p.ctrl;
@@ -430,7 +456,10 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
-  unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
+  // per-thread work counters: a thread sees at most tens of thousands of
+  // arcs per launch, so 32 bits hold all but the seed-weighted work
+  uint32_t my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0;
+  unsigned long long my_work = 0;
   // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
   // of the graphs that chose a full sweep and take the others' work list
   if (mode != kModeSparse)
@@ -462,7 +491,7 @@ __global__ void __launch_bounds__(kBlock, PG_PULL_MIN_BLOCKS) k_pull(Params p) {
       }
       if (gl == 0 && act) {
         ++my_items;
-        my_scan += (unsigned long long)len;
+        my_scan += (uint32_t)len;
       }
       int32_t u[UNR];
 #pragma unroll

@@ -31,7 +31,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t bytes) {
 }
 
 pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, pg_options *inout,
-                       pg_tune_report *rep) {
+                       pg_tune_report *rep, bool s_mode) {
   pg_tune_report r{};
   pg_options cur = *inout;
   double best = 0.0;
@@ -54,7 +54,7 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
   pg_status rc = measure(cur, &best);
   if (rc) return rc;
   r.default_ms = best;
-  const int W = (s_bits + 63) / 64;
+  const int W = s_mode ? 1 : (s_bits + 63) / 64;  // PROPAGATE-S: one word per node
   const int cw_class = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
   std::vector<int> wpt;
   for (int c : {0, 1, 2, 4, 8})
@@ -105,6 +105,14 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
     o.test_changed = tc;
     if ((rc = try_value(o))) return rc;
   }
+  if (s_mode && s_bits > 64) {  // PROPAGATE-S: passes one at a time or together
+    for (int k : {1, 2, 4, 0}) {
+      if (k == cur.passes_together) continue;
+      pg_options o = cur;
+      o.passes_together = k;
+      if ((rc = try_value(o))) return rc;
+    }
+  }
   r.best_ms = best;
   *inout = cur;
   if (rep) *rep = r;
@@ -115,9 +123,16 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
 
 using namespace pg;
 
-extern "C" pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t max_trials,
-                                 pg_options *inout, pg_tune_report *report, void *stream) {
-  if (!g || !seeds || s < 1 || !inout || max_trials < 1) return PG_EINVAL;
+extern "C" pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t algorithm,
+                                 int32_t max_trials, pg_options *inout, pg_tune_report *report,
+                                 void *stream) {
+  if (!g || !seeds || s < 1 || !inout || max_trials < 1 || algorithm < 0 || algorithm > 1)
+    return PG_EINVAL;
+  const bool s_mode = algorithm == PG_ALG_S;
+  auto call = [&](pg_counts *c, const pg_options *o) {
+    return s_mode ? pg_propagate_s(g, seeds, s, c, o, stream)
+                  : pg_propagate_p(g, seeds, s, c, o, stream);
+  };
   int32_t cap = 0;
   pg_status rc = pg_query_rounds_bound(g, &cap);
   if (rc) return rc;
@@ -128,7 +143,7 @@ extern "C" pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, i
   for (;;) {
     counts.assign((size_t)(rows + 1) * s, 0u);
     c = pg_counts{s, rows, 0, 0, counts.data(), nullptr};
-    rc = pg_propagate_p(g, seeds, s, &c, inout, stream);
+    rc = call(&c, inout);
     if (rc == PG_ERANGE && rows < cap) {
       rows = cap;
       continue;
@@ -140,7 +155,7 @@ extern "C" pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, i
   TuneRun run = [&](const pg_options &o, double *ms, uint64_t *hash) -> pg_status {
     pg_counts cc{s, rows, 0, 0, counts.data(), nullptr};
     const auto t0 = std::chrono::steady_clock::now();
-    pg_status e = pg_propagate_p(g, seeds, s, &cc, &o, stream);
+    pg_status e = call(&cc, &o);
     const auto t1 = std::chrono::steady_clock::now();
     if (e) return e;
     *ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -148,5 +163,5 @@ extern "C" pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, i
     *hash = fnv1a(h, counts.data(), sizeof(uint32_t) * (size_t)(cc.rounds + 1) * s);
     return PG_OK;
   };
-  return tune_options(run, s, max_trials, inout, report);
+  return tune_options(run, s, max_trials, inout, report, s_mode);
 }

@@ -274,3 +274,33 @@ def test_repeated_calls_different_widths_reuse_graph():
     for s in (64, 512, 3, 256, 64):
         seeds = I.seeds(g.n, s, s)
         _assert_same(pg.propagate_p(G, seeds), _oracle_p(g, seeds))
+
+
+# ------------------------------------------- the paper's literal direction
+def _transpose(g):
+    """Host transpose of a CSR over in-edges (the in-CSR of the reversed
+    graph), with sorted rows."""
+    n = g.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.row_ptr))
+    src = np.asarray(g.col, dtype=np.int64)
+    order = np.lexsort((rows, src))
+    col_t = rows[order].astype(np.int32)
+    rp_t = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp_t, src + 1, 1)
+    return I.Graph(n=n, row_ptr=np.cumsum(rp_t), col=col_t, directed=True, name=g.name + "_T",
+                   meta={})
+
+
+@pytest.mark.parametrize("fn", ["p", "s"])
+def test_reverse_flag_counts_backward_balls(fn):
+    """PG_REVERSE: counts of nodes that reach each seed, i.e. the forward
+    balls of the reversed graph (the oracle on the explicit transpose)."""
+    g = I.rmat(12, 8, 91, directed=True)
+    seeds = I.seeds(g.n, 100, 92)
+    want = oracle.run(_transpose(g), seeds)
+    G = pg.Graph.from_inputs(g, reverse=True)
+    res = (pg.propagate_p if fn == "p" else pg.propagate_s)(G, seeds)
+    assert res.rounds == want["rounds"]
+    assert np.array_equal(res.counts, want["counts"])
+    fwd = oracle.run(g, seeds)
+    assert not np.array_equal(fwd["counts"][:2], want["counts"][:2])  # the direction matters

@@ -54,6 +54,16 @@ def test_autotune_keeps_counts():
     assert d["group_lanes"] in (0, 1, 2, 4, 8, 16, 32)
 
 
+def test_autotune_propagate_s_keeps_counts():
+    g, seeds, want = _case(256)
+    G = pg.Graph.from_inputs(g)
+    o, rep = pg.autotune(G, seeds, max_trials=10, algorithm="s")
+    assert 1 <= rep["trials"] <= 10
+    res = pg.propagate_s(G, seeds, opts=o)
+    assert np.array_equal(res.counts, want["counts"])
+    assert pg.options_dict(o)["passes_together"] in (0, 1, 2, 4)
+
+
 def test_batch_tune_then_run():
     items = I.mix(16, 500, 20_000, 8)
     with pg.Batch() as b:
@@ -138,3 +148,26 @@ def test_s_passes_together_identical(planes, together):
     assert np.array_equal(res.m_active, _oracle_s_mactive(g, seeds, planes, want["rounds"]))
     st = G.last_stats()
     assert st["passes"] == -(-150 // planes)
+
+
+# ------------------------------------------------------ progressive sampling
+def test_progressive_sampling():
+    """Blocks of seeds until the Thm. 3 sample size: the counts equal the
+    oracle's for the drawn seeds, and the estimates approach the exact
+    all-pairs values (s = n) within eps."""
+    g = I.er(3000, 8, 101)
+    eps = 0.1
+    G = pg.Graph.from_inputs(g)
+    res, seeds, hist = pg.progressive(G, eps, rng_seed=5, block=200)
+    assert res.s == len(seeds) == min(g.n, int(np.ceil(np.log(g.n) / eps ** 2)))
+    assert len(set(seeds.tolist())) == len(seeds)
+    want = oracle.run(g, seeds)
+    assert np.array_equal(res.counts, want["counts"])
+    exact = oracle.run(g, np.arange(g.n, dtype=np.int32))["metrics"]
+    est = pg.metrics(res, g.n)
+    assert abs(est["avg_distance"] - exact["avg_distance"]) <= eps * exact["avg_distance"]
+    assert hist[-1]["seeds"] == res.s and len(hist) == -(-res.s // 200)
+    # stability rule: stops earlier, still a prefix of the same draw
+    res2, seeds2, hist2 = pg.progressive(G, eps, rng_seed=5, block=200, stable_tol=0.05)
+    assert res2.s <= res.s and np.array_equal(seeds2, seeds[:res2.s])
+    assert np.array_equal(res2.counts[:, :], oracle.run(g, seeds2)["counts"])
