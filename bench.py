@@ -260,6 +260,9 @@ def run_ours(args):
     per_kernel = {}  # pull kernel name -> [ms, launches, bytes]
     p_ms, s_ms = [], []
     with Clocks(torch.cuda.current_device()) as clk:
+        # NVTX range of the timed steps: a launch-list capture selects it with
+        # ncu --nvtx --nvtx-include bench_timed/
+        torch.cuda.nvtx.range_push("bench_timed")
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush, outside the timed events
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -282,6 +285,7 @@ def run_ours(args):
                 k[2] += pull_bytes(st)
                 post_ms += st["ms_post"]
                 launches += st["launches"]
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -709,11 +713,15 @@ def run_serve(args):
 
 
 def kernel_hash() -> str:
+    """Hash of the sources that define the pull kernels (their device code
+    and the parameter block): a stored DRAM-traffic figure applies only to
+    the kernels it was captured from."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2301_06499_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
+        if name in ("kernels.cuh", "common.cuh") or (name.startswith("pull_") and
+                                                       name.endswith(".cu")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:12]
 

@@ -127,28 +127,42 @@ pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st) {
 // ------------------------------------------------------------ validation
 // err bits: 1 row_ptr[0] != 0, 2 non-monotone / past m, 4 col out of range,
 // 8 row not strictly increasing, 16 row_ptr[n] != m.
-__global__ void __launch_bounds__(kBlock) k_validate(const int64_t *rp, const int32_t *col,
-                                                     int64_t n, int64_t m, int *err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-  if (warp == 0 && lane == 0) {
+// CSR validation in two flat passes (all coalesced): rows, one thread each,
+// check their bounds and mark their first arc in a bitmap of m bits; arcs,
+// one thread each, check their column and, unless a row starts there, that
+// they follow the previous arc in increasing order.
+__global__ void k_validate_rows(const int64_t *rp, int64_t n, int64_t m, uint32_t *starts,
+                                int *err) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  if (gtid == 0) {
     if (rp[0] != 0) atomicOr(err, 1);
     if (rp[n] != m) atomicOr(err, 16);
   }
-  for (int64_t v = warp; v < n; v += nwarps) {
+  for (int64_t v = gtid; v < n; v += nth) {
     const int64_t b = rp[v], e = rp[v + 1];
-    if (b > e || b < 0 || e > m) {
-      if (lane == 0) atomicOr(err, 2);
-      continue;
-    }
+    if (b > e || b < 0 || e > m)
+      atomicOr(err, 2);
+    else if (b < e)
+      atomicOr(starts + (b >> 5), 1u << (b & 31));
+  }
+}
+
+__global__ void k_validate_arcs(const int32_t *col, int64_t n, int64_t m, const uint32_t *starts,
+                                int *err) {
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  // whole warps iterate, so that the warp-wide OR sees every lane
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < m;
+       base += nth) {
+    const int64_t j = base + (threadIdx.x & 31);
     int bad = 0;
-    for (int64_t j = b + lane; j < e; j += 32) {
-      int32_t c = col[j];
+    if (j < m) {
+      const int32_t c = col[j];
       if (c < 0 || c >= n) bad |= 4;
-      if (j > b && col[j - 1] >= c) bad |= 8;
+      if (j > 0 && !((starts[j >> 5] >> (j & 31)) & 1u) && col[j - 1] >= c) bad |= 8;
     }
-    if (bad) atomicOr(err, bad);
+    bad = __reduce_or_sync(kFullMask, (unsigned)bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
   }
 }
 
@@ -687,9 +701,19 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
   if (rc == PG_OK) {
     cudaMemsetAsync(err, 0, sizeof(int), st);
     cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
-    k_validate<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, n, m, err);
-    k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, mx);
-    rc = cuda_status(cudaGetLastError());
+    uint32_t *starts = nullptr;
+    const int64_t swords = (m + 31) / 32 + 1;
+    rc = cuda_status(cudaMallocAsync((void **)&starts, sizeof(uint32_t) * swords, st));
+    if (rc == PG_OK) {
+      cudaMemsetAsync(starts, 0, sizeof(uint32_t) * swords, st);
+      k_validate_rows<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, m, starts, err);
+      k_validate_arcs<<<grid_for(m), kBlock, 0, st>>>(g->col, n, m, starts, err);
+      cudaFreeAsync(starts, st);
+    }
+    if (rc == PG_OK) {
+      k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, mx);
+      rc = cuda_status(cudaGetLastError());
+    }
   }
   int err_h = 0;
   unsigned long long mx_h = 0;

@@ -149,8 +149,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 //     pieces, adding its in-degree to m_active[t+1].
 //  C. last block: fixpoint test (Alg. 1: do ... while Count > 0), hand-over
 //     to round t+1, and, inside a while-graph, the loop condition.
+// Four resident blocks per SM (64 registers, no spills): like the pull, the
+// kernel is latency-bound, and at the default 80 registers only three fit.
 template <bool SMEM>
-__global__ void __launch_bounds__(kBlock) k_post(Params p) {
+__global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
   extern __shared__ uint32_t scnt[];
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) {

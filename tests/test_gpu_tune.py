@@ -171,3 +171,21 @@ def test_progressive_sampling():
     res2, seeds2, hist2 = pg.progressive(G, eps, rng_seed=5, block=200, stable_tol=0.05)
     assert res2.s <= res.s and np.array_equal(seeds2, seeds[:res2.s])
     assert np.array_equal(res2.counts[:, :], oracle.run(g, seeds2)["counts"])
+
+
+def test_exact_mode_wide_rows():
+    """s = n on 3,000 nodes (47 words per node): PROPAGATE-P through the wide
+    kernel, PROPAGATE-S as 47 passes run together over replicas; metrics
+    from all pairs."""
+    g = I.er(3000, 6, 111)
+    seeds = np.arange(g.n, dtype=np.int32)
+    want = oracle.run(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_p(G, seeds)
+    assert G.last_stats()["words_per_gather"] == 0  # the wide-row kernel
+    assert res.rounds == want["rounds"] and np.array_equal(res.counts, want["counts"])
+    assert np.array_equal(res.m_active, want["m_active"])
+    res_s = pg.propagate_s(G, seeds)
+    assert np.array_equal(res_s.counts, want["counts"])
+    m = pg.metrics(res, g.n)
+    assert m["R_last"] == want["metrics"]["R_last"]
