@@ -250,9 +250,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     if (full) set_bit(p.Sat, v);
   }
   // the deltas of round t-1 were read by the pull of round t: clear them
-  for (int64_t i = gtid; i < nFprev * Wp; i += nth) {
-    const int64_t r = i / Wp;
-    Dprev[(size_t)Fprev[r] * Wp + (i - r * Wp)] = 0ULL;
+  for (int64_t r = gtid; r < nFprev; r += nth) {  // a thread per row, no division
+    uint64_t *dr = Dprev + (size_t)Fprev[r] * Wp;
+    for (int w = 0; w < Wp; ++w) dr[w] = 0ULL;
   }
   if (SMEM) {
     __syncthreads();
@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
                                p.node_graph ? p.graph_s[p.node_graph[x[q]]] : s));
         bool claim[UNR];
 #pragma unroll
-        for (int q = 0; q < UNR; ++q) claim[q] = cand[q] && !set_bit(Knext, x[q]);
+        for (int q = 0; q < UNR; ++q)  // a bit already seen set needs no atomic
+          claim[q] = cand[q] && !test_bit_live(Knext, x[q]) && !set_bit(Knext, x[q]);
 #pragma unroll
         for (int q = 0; q < UNR; ++q) {
           unsigned long long np = 0;
