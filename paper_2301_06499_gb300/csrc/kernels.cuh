@@ -249,13 +249,14 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
 // Tuning knobs (compile-time): minimum resident blocks per SM for the pull
 // kernel (caps registers; the kernels are latency-bound, so occupancy pays:
 // 4 blocks of 256 threads = 64 registers, measured 10% faster than 3 for
-// 4-word rows on R-MAT 22; 8-word rows keep 3, they spill at 64) and arcs
-// per lane per step of the dense sweep.
+// 4-word rows on R-MAT 22, and 2.6% faster for 8-word rows on the scale-26
+// R-MAT although those spill ~150 bytes at 64 registers) and arcs per lane
+// per step of the dense sweep.
 #ifndef PG_PULL_MIN_BLOCKS
 #define PG_PULL_MIN_BLOCKS 4
 #endif
 #ifndef PG_PULL_MIN_BLOCKS_WIDE
-#define PG_PULL_MIN_BLOCKS_WIDE 3
+#define PG_PULL_MIN_BLOCKS_WIDE 4
 #endif
 #ifndef PG_DENSE_UNROLL_NARROW
 #define PG_DENSE_UNROLL_NARROW 4
