@@ -702,7 +702,7 @@ def run_serve(args):
         "roofline": None,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": served_s * 1e3},
-        "gpu_launches": None,
+        "gpu_launches": int(st1["gpu_launches"] - st0["gpu_launches"]),
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

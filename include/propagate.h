@@ -460,6 +460,7 @@ typedef struct {
   int64_t budget_bytes;           /* the admission budget */
   int32_t graphs, queued, running, reserved;
   uint64_t seed_edge_traversals;  /* summed over propagations */
+  int64_t gpu_launches;           /* kernels the propagations launched */
 } pg_server_stats;
 
 /* Fills *cfg with the defaults. */

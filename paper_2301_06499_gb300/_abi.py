@@ -90,7 +90,8 @@ class ServerStats(ctypes.Structure):
                 ("inflight_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64), ("graphs", ctypes.c_int32),
                 ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
+                ("reserved", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64),
+                ("gpu_launches", ctypes.c_int64)]
 
 
 PG_REQ_QUEUED, PG_REQ_RUNNING, PG_REQ_DONE, PG_REQ_FAILED, PG_REQ_CANCELLED = 0, 1, 2, 3, 4

@@ -301,7 +301,10 @@ void worker(pg_server *srv, int k) {
       }
       srv->st.running -= (int32_t)job.reqs.size();
       srv->st.propagations += 1;
-      if (rc == PG_OK) srv->st.seed_edge_traversals += pst.seed_edge_traversals;
+      if (rc == PG_OK) {
+        srv->st.seed_edge_traversals += pst.seed_edge_traversals;
+        srv->st.gpu_launches += pst.launches;
+      }
       srv->st.inflight_bytes = slots_total(srv);
     }
     srv->done_cv.notify_all();

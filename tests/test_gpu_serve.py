@@ -65,6 +65,7 @@ def test_burst_same_alone_and_in_mix():
         st = srv.stats()
     assert st["completed"] == 60 and st["failed"] == 0
     assert st["propagations"] <= 60
+    assert st["gpu_launches"] >= 3 * st["propagations"]  # set-up kernels + rounds
     assert max(i["merged"] for i in infos) >= 1
     assert st["peak_bytes"] <= st["budget_bytes"]
 
