@@ -55,6 +55,9 @@ WORKLOADS = {
     # s = ceil(ln n / eps^2) rounded to 64 = 5568 seeds (87 words per node)
     "er1e6_s5568": (dict(kind="er", n=1_000_000, d=16, seed=6), 5568,
                     "undirected ER n=1e6 avg degree 16, s=5568 (wide signatures)"),
+    # exact mode: every node a seed (all-pairs distances), 1563 words per node
+    "exact_er1e5": (dict(kind="er", n=100_000, d=8, seed=8), 100_000,
+                    "undirected ER n=1e5 avg degree 8, s=n (exact all-pairs)"),
 }
 # Batched workload: 512 graphs, n log-uniform in [1e3, 1e6], ER / R-MAT / grid
 # with RNG seed 4, s per graph from eps in {0.1, 0.2} (see inputs.mix).
@@ -72,7 +75,8 @@ SERVE_WORKLOADS = {
                         variants=4),
 }
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
-            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2, "er1e6_s5568": 7}
+            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2, "er1e6_s5568": 7,
+            "exact_er1e5": 9}
 
 
 def make_graph(spec):

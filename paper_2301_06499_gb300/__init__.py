@@ -165,7 +165,10 @@ def _run(fn, what, g: Graph, seeds, max_rounds, opts, stream) -> Result:
     st = stream if stream is not None else _current_stream()
     o = opts if opts is not None else options()
     bound = g.rounds_bound()
-    cap = min(bound, 65535) if max_rounds is None else int(max_rounds)
+    # first try: room for up to 65535 rounds but at most ~1 GB of counters
+    # (many seeds); a run with more rounds reports it and is repeated
+    cap = (min(bound, 65535, max(1024, (1 << 30) // (4 * max(s, 1))))
+           if max_rounds is None else int(max_rounds))
     while True:
         counts = np.zeros((cap + 1, s), dtype=np.uint32)
         mact = np.zeros(cap + 2, dtype=np.uint64)

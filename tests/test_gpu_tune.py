@@ -189,3 +189,23 @@ def test_exact_mode_wide_rows():
     assert np.array_equal(res_s.counts, want["counts"])
     m = pg.metrics(res, g.n)
     assert m["R_last"] == want["metrics"]["R_last"]
+
+
+def test_exact_mode_313_words():
+    """s = n on 20,000 nodes: 313 words per node, so the wide-row kernel
+    sweeps each row in several 32-words-per-lane passes; P, S and the
+    all-pairs metrics match the oracle."""
+    g = I.er(20_000, 8, 121)
+    seeds = np.arange(g.n, dtype=np.int32)
+    want = oracle.run(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_SPARSE):
+        res = pg.propagate_p(G, seeds, opts=pg.options(direction=direction))
+        assert G.last_stats()["words_per_gather"] == 0
+        assert res.rounds == want["rounds"] and np.array_equal(res.counts, want["counts"])
+        assert np.array_equal(res.m_active, want["m_active"])
+    res_s = pg.propagate_s(G, seeds)
+    assert np.array_equal(res_s.counts, want["counts"])
+    m = pg.metrics(res, g.n)
+    for k in ("R_last", "avg_distance"):
+        assert m[k] == pytest.approx(want["metrics"][k], rel=1e-12)
