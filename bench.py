@@ -58,6 +58,9 @@ WORKLOADS = {
     # exact mode: every node a seed (all-pairs distances), 1563 words per node
     "exact_er1e5": (dict(kind="er", n=100_000, d=8, seed=8), 100_000,
                     "undirected ER n=1e5 avg degree 8, s=n (exact all-pairs)"),
+    "exact_er3e4": (dict(kind="er", n=30_000, d=8, seed=8), 30_000,
+                    "undirected ER n=3e4 avg degree 8, s=n (exact all-pairs; profiling "
+                    "stand-in for n=1e5)"),
 }
 # Batched workload: 512 graphs, n log-uniform in [1e3, 1e6], ER / R-MAT / grid
 # with RNG seed 4, s per graph from eps in {0.1, 0.2} (see inputs.mix).
@@ -76,7 +79,7 @@ SERVE_WORKLOADS = {
 }
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
             "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2, "er1e6_s5568": 7,
-            "exact_er1e5": 9}
+            "exact_er1e5": 9, "exact_er3e4": 9}
 
 
 def make_graph(spec):

@@ -70,6 +70,7 @@ struct Params {
   uint32_t *C0, *C1;   // changed-in-round bitmaps, alternating by round parity
   uint32_t *K0, *K1;   // claim / active bitmaps, alternating
   uint32_t *Sat;       // saturated (all s bits set)
+  uint32_t *rowbits;   // wide rows: set bits of each row so far (else null)
   int64_t nbm;         // 32-bit words per bitmap
   int32_t *F0, *F1;    // rows changed in round t, by round parity
   unsigned long long *E;  // out-arc pieces of F rows: (row << 32) | piece of LE arcs
@@ -122,8 +123,8 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, F0, F1, E, A, counts, rs, ctrl, seeds, seed_bits,
-      gfsum, gthr;
+  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, F0, F1, E, A, counts, rs, ctrl, seeds,
+      seed_bits, gfsum, gthr;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events

@@ -13,6 +13,7 @@ namespace pg {
 
 constexpr int32_t kStatusWindow = 100;  // device asks the host to move the counts window
 constexpr int kSmemCountMax = 12288;    // per-seed counters kept in shared memory up to this s
+constexpr int kWidePostWords = 16;      // rows of this many words take k_post's tiled part A
 constexpr int kExpandArcs = 8;          // out-arcs per expansion piece (LE)
 constexpr int kWidePiece = 256;         // in-arcs per piece of the wide-row pull
 
@@ -48,6 +49,8 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     p.K1[i] = 0u;
     p.Sat[i] = 0u;
   }
+  if (p.rowbits)
+    for (int64_t i = gtid; i < p.n; i += nth) p.rowbits[i] = 0u;
   for (int64_t i = gtid; i < count_words; i += nth) p.counts[i] = 0u;
   unsigned long long *rsw = reinterpret_cast<unsigned long long *>(p.rs);
   for (int64_t i = gtid; i < rs_words; i += nth) rsw[i] = 0ULL;
@@ -151,7 +154,12 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 //     to round t+1, and, inside a while-graph, the loop condition.
 // Four resident blocks per SM (64 registers, no spills): like the pull, the
 // kernel is latency-bound, and at the default 80 registers only three fit.
-template <bool SMEM>
+//
+// WIDE (rows of 16 or more words, one graph): part A runs over tiles of 32
+// frontier rows (a lane each) x 32 words, so that the grid spreads over the
+// words of a row and not only over the rows; a row is saturated when its
+// running count of set bits (rowbits) reaches s, which exactly one tile sees.
+template <bool SMEM, bool WIDE>
 __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
   extern __shared__ uint32_t scnt[];
   Ctrl *ctrl = p.ctrl;
@@ -186,6 +194,53 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     __syncthreads();
   }
   // A. count, record deltas, sync, saturation
+  if constexpr (WIDE) {
+    const int nblk = (Wp + 31) >> 5;
+    const int64_t ntiles = ((nF + 31) >> 5) * (int64_t)nblk;
+    for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
+      const int64_t grp = tile / nblk;
+      const int w0 = (int)(tile - grp * nblk) * 32;
+      const int w1 = min(w0 + 32, Wp);
+      const int64_t i = grp * 32 + lane;
+      const bool valid = i < nF;
+      const int32_t v = valid ? F[i] : 0;
+      uint64_t *xr = p.X + (size_t)v * Wp;
+      const uint64_t *yr = p.Y + (size_t)v * Wp;
+      uint64_t *dr = Dcur + (size_t)v * Wp;
+      uint32_t gained = 0;
+      for (int w = w0; w < w1; w += 4) {  // rows are 64-byte aligned, Wp % 8 == 0
+        uint64_t o[4] = {0ULL, 0ULL, 0ULL, 0ULL}, nw[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+        if (valid) {
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(xr + w);
+          const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(xr + w + 2);
+          o[0] = a.x;
+          o[1] = a.y;
+          o[2] = b.x;
+          o[3] = b.y;
+          ld_nc_256(nw, yr + w);
+        }
+        uint64_t d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = o[k] ^ nw[k];
+        if ((d[0] | d[1] | d[2] | d[3]) != 0ULL) {  // the deltas were zero before
+          store_words<4>(xr + w, nw);
+          store_words<4>(dr + w, d);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          gained += (uint32_t)__popcll(d[k]);
+          if (__any_sync(kFullMask, d[k] != 0ULL)) {
+            const uint32_t n0 = __popc(transpose32((uint32_t)d[k], lane));
+            const uint32_t n1 = __popc(transpose32((uint32_t)(d[k] >> 32), lane));
+            const int c0 = (w + k) * 64 + lane;
+            if (n0) atomicAdd(&cdst[c0], n0);
+            if (n1) atomicAdd(&cdst[c0 + 32], n1);
+          }
+        }
+      }
+      if (gained && atomicAdd(p.rowbits + v, gained) + gained == (uint32_t)s) set_bit(p.Sat, v);
+    }
+  } else {
   for (int64_t base = warp * 32; base < nF; base += nwarps * 32) {
     const int64_t i = base + lane;
     const bool valid = i < nF;
@@ -249,10 +304,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     }
     if (full) set_bit(p.Sat, v);
   }
+  }
   // the deltas of round t-1 were read by the pull of round t: clear them
-  for (int64_t r = gtid; r < nFprev; r += nth) {  // a thread per row, no division
-    uint64_t *dr = Dprev + (size_t)Fprev[r] * Wp;
-    for (int w = 0; w < Wp; ++w) dr[w] = 0ULL;
+  if constexpr (WIDE) {  // a warp per row, 16 bytes a lane
+    const ulonglong2 z = make_ulonglong2(0ULL, 0ULL);
+    for (int64_t r = warp; r < nFprev; r += nwarps) {
+      ulonglong2 *dr = reinterpret_cast<ulonglong2 *>(Dprev + (size_t)Fprev[r] * Wp);
+      for (int k = lane; k < (Wp >> 1); k += 32) dr[k] = z;
+    }
+  } else {
+    for (int64_t r = gtid; r < nFprev; r += nth) {  // a thread per row, no division
+      uint64_t *dr = Dprev + (size_t)Fprev[r] * Wp;
+      for (int w = 0; w < Wp; ++w) dr[w] = 0ULL;
+    }
   }
   if (SMEM) {
     __syncthreads();
@@ -387,6 +451,8 @@ __global__ void k_window_shift(Params p, int64_t count_words, int32_t rs_slots) 
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   __shared__ RoundStats carry;
   if (threadIdx.x == 0 && blockIdx.x == 0) carry = p.rs[p.row_cap];
+  if (p.rowbits)
+    for (int64_t i = gtid; i < p.n; i += nth) p.rowbits[i] = 0u;
   for (int64_t i = gtid; i < count_words; i += nth) p.counts[i] = 0u;
   __syncthreads();
   if (blockIdx.x == 0) {
@@ -412,6 +478,7 @@ struct Plan {
   int grid_pull = 1, grid_post = 1;
   size_t post_smem = 0;
   bool smem_counts = true;
+  bool post_wide = false;  // k_post's tiled part A (rows of 16+ words, one graph)
 };
 
 static PullFn pick_pull(int CW, int G) {
@@ -477,15 +544,29 @@ static pg_status make_plan(const pg_graph *g, int sp, const pg_options &o, bool 
 }
 
 static const void *post_fn(const Plan &pl) {
-  return pl.smem_counts ? (const void *)&k_post<true> : (const void *)&k_post<false>;
+  if (pl.post_wide)
+    return pl.smem_counts ? (const void *)&k_post<true, true> : (const void *)&k_post<false, true>;
+  return pl.smem_counts ? (const void *)&k_post<true, false> : (const void *)&k_post<false, false>;
+}
+
+static void launch_post(const Plan &pl, const Params &p, cudaStream_t st) {
+  const size_t smem = pl.smem_counts ? pl.post_smem : 0;
+  if (pl.post_wide) {
+    if (pl.smem_counts)
+      k_post<true, true><<<pl.grid_post, kBlock, smem, st>>>(p);
+    else
+      k_post<false, true><<<pl.grid_post, kBlock, smem, st>>>(p);
+  } else {
+    if (pl.smem_counts)
+      k_post<true, false><<<pl.grid_post, kBlock, smem, st>>>(p);
+    else
+      k_post<false, false><<<pl.grid_post, kBlock, smem, st>>>(p);
+  }
 }
 
 static void launch_round(const Plan &pl, const Params &p, cudaStream_t st) {
   pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
-  if (pl.smem_counts)
-    k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
-  else
-    k_post<false><<<pl.grid_post, kBlock, 0, st>>>(p);
+  launch_post(pl, p, st);
 }
 
 struct PassOut {
@@ -564,6 +645,7 @@ struct GraphCache {
   int grid_pull = 0, grid_post = 0;
   size_t smem = 0;
   bool smem_counts = true;
+  bool post_wide = false;
   cudaStream_t cap = nullptr;
 };
 
@@ -586,6 +668,7 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   key.cond = c.p.cond;  // compare everything but the handle
   if (c.exec && c.pull == pl.pull && c.grid_pull == pl.grid_pull &&
       c.grid_post == pl.grid_post && c.smem == pl.post_smem && c.smem_counts == pl.smem_counts &&
+      c.post_wide == pl.post_wide &&
       std::memcmp(&c.p, &key, sizeof(Params)) == 0) {
     *out = c.exec;
     return PG_OK;
@@ -638,6 +721,7 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   c.grid_post = pl.grid_post;
   c.smem = pl.post_smem;
   c.smem_counts = pl.smem_counts;
+  c.post_wide = pl.post_wide;
   *out = c.exec;
   return PG_OK;
 }
@@ -694,6 +778,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     return rc;
   for (DevBuf *b : {&w.C0, &w.C1, &w.K0, &w.K1, &w.Sat})
     if ((rc = ensure(*b, sizeof(uint32_t) * nbm))) return rc;
+  pl.post_wide = !bs && pl.Wp >= kWidePostWords;
+  if (pl.post_wide && (rc = ensure(w.RB, sizeof(uint32_t) * n))) return rc;
   if ((rc = ensure(w.F0, sizeof(int32_t) * n)) || (rc = ensure(w.F1, sizeof(int32_t) * n)) ||
       (rc = ensure(w.E, sizeof(unsigned long long) * e_cap)) ||
       (rc = ensure(w.A, sizeof(ulonglong2) * std::max<int64_t>(g->pieces.count, 1))) ||
@@ -731,6 +817,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.K0 = (uint32_t *)w.K0.p;
   p.K1 = (uint32_t *)w.K1.p;
   p.Sat = (uint32_t *)w.Sat.p;
+  p.rowbits = pl.post_wide ? (uint32_t *)w.RB.p : nullptr;
   p.nbm = nbm;
   p.F0 = (int32_t *)w.F0.p;
   p.F1 = (int32_t *)w.F1.p;
@@ -773,7 +860,10 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
 
   const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
-  pl.grid_post = occupancy_grid(post_fn(pl), pl.post_smem, std::max<int64_t>(n, nbm));
+  // the wide part A has a warp per 32 rows x 32 words
+  const int64_t post_threads =
+      pl.post_wide ? (n + 31) / 32 * (int64_t)((pl.Wp + 31) / 32) * 32 : n;
+  pl.grid_post = occupancy_grid(post_fn(pl), pl.post_smem, std::max<int64_t>(post_threads, nbm));
   if (pl.post_smem > 48 * 1024)
     cudaFuncSetAttribute(post_fn(pl), cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pl.post_smem);
@@ -823,10 +913,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
                                                                                 rs_words);
   k_seed<<<1, 1024, 0, st>>>(p, (const int32_t *)w.seeds.p,
                              bs ? (const int32_t *)w.seed_bits.p : nullptr, sp);
-  if (pl.smem_counts)
-    k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
-  else
-    k_post<false><<<pl.grid_post, kBlock, 0, st>>>(p);
+  launch_post(pl, p, st);
   po.launches += 3;
   if (timing) {
     init_ev1 = ntev++;
@@ -877,10 +964,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
           cudaEventRecord(tev(a), st);
           pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
           cudaEventRecord(tev(b), st);
-          if (pl.smem_counts)
-            k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
-          else
-            k_post<false><<<pl.grid_post, kBlock, 0, st>>>(p);
+          launch_post(pl, p, st);
           cudaEventRecord(tev(c), st);
           pull_ev.push_back({a, b});
           post_ev.push_back({b, c});
@@ -914,10 +998,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
           cudaEventRecord(tev(a), st);
           pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
           cudaEventRecord(tev(b), st);
-          if (pl.smem_counts)
-            k_post<true><<<pl.grid_post, kBlock, pl.post_smem, st>>>(p);
-          else
-            k_post<false><<<pl.grid_post, kBlock, 0, st>>>(p);
+          launch_post(pl, p, st);
           cudaEventRecord(tev(c), st);
           pull_ev.push_back({a, b});
           post_ev.push_back({b, c});
@@ -1290,7 +1371,7 @@ int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_
   const int64_t cap_rows =
       window_rows > 0 ? window_rows : std::max<int64_t>(64, (256LL << 20) / (4LL * s));
   const int64_t row_cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
-  return 4 * n * Wp * 8 + 5 * nbm * 4 + 2 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
+  return 4 * n * Wp * 8 + 5 * nbm * 4 + 3 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
          pieces * 16 + row_cap * s * 4 + (row_cap + 2) * (int64_t)sizeof(RoundStats) +
          (int64_t)s * 8 + 4096;
 }

@@ -16,11 +16,13 @@
 namespace pg {
 
 // NW words per lane held in registers (rows of up to 32·NW words); NW = 0
-// sweeps a longer row in passes of 32 words, re-reading the piece's columns
-// (from L1) in each pass.
+// sweeps a longer row in passes of 128 words (4 per lane, so that 16 loads
+// of four neighbours are in flight), re-reading the piece's columns (from
+// L1) in each pass.
+// Five resident blocks per SM (48 registers, no spills).
 template <int NW>
-__global__ void __launch_bounds__(kBlock) k_pull_wide(Params p) {
-  constexpr int R = NW > 0 ? NW : 1;  // words per lane per pass
+__global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
+  constexpr int R = NW > 0 ? NW : 4;  // words per lane per pass
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
   const int t = ctrl->t;
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_wide(Params p) {
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
   const int Wp = p.Wp;
-  const int passes = NW > 0 ? 1 : (Wp + 31) / 32;
+  const int passes = NW > 0 ? 1 : (Wp + 32 * R - 1) / (32 * R);
   unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
   // dense: every row's pieces; sparse: the claimed pieces; mixed (a packed
   // batch): the pieces of graphs that chose a full sweep, then the claimed ones
