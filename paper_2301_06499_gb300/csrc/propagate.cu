@@ -156,9 +156,9 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 // kernel is latency-bound, and at the default 80 registers only three fit.
 //
 // WIDE (rows of 16 or more words, one graph): part A runs over tiles of 32
-// frontier rows (a lane each) x 32 words, so that the grid spreads over the
-// words of a row and not only over the rows; a row is saturated when its
-// running count of set bits (rowbits) reaches s, which exactly one tile sees.
+// frontier rows x 16 words, so that the grid spreads over the words of a row
+// and not only over the rows; a row is saturated when its running count of
+// set bits (rowbits) reaches s, which exactly one tile sees.
 template <bool SMEM, bool WIDE>
 __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
   extern __shared__ uint32_t scnt[];
@@ -195,50 +195,61 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
   }
   // A. count, record deltas, sync, saturation
   if constexpr (WIDE) {
-    const int nblk = (Wp + 31) >> 5;
+    // tiles of 32 frontier rows x 16 words: each half-warp moves 16
+    // consecutive words (128 bytes) of one row, so loads and stores are
+    // coalesced; the deltas go through shared memory to a lane-per-row
+    // layout for the per-seed bit transpose
+    __shared__ uint64_t tile_s[kBlock / 32][32][17];
+    uint64_t(*tl)[17] = tile_s[threadIdx.x >> 5];
+    const int half = lane >> 4, wl = lane & 15;
+    const int nblk = (Wp + 15) >> 4;
     const int64_t ntiles = ((nF + 31) >> 5) * (int64_t)nblk;
     for (int64_t tile = warp; tile < ntiles; tile += nwarps) {
       const int64_t grp = tile / nblk;
-      const int w0 = (int)(tile - grp * nblk) * 32;
-      const int w1 = min(w0 + 32, Wp);
+      const int w0 = (int)(tile - grp * nblk) * 16;
       const int64_t i = grp * 32 + lane;
-      const bool valid = i < nF;
-      const int32_t v = valid ? F[i] : 0;
-      uint64_t *xr = p.X + (size_t)v * Wp;
-      const uint64_t *yr = p.Y + (size_t)v * Wp;
-      uint64_t *dr = Dcur + (size_t)v * Wp;
-      uint32_t gained = 0;
-      for (int w = w0; w < w1; w += 4) {  // rows are 64-byte aligned, Wp % 8 == 0
-        uint64_t o[4] = {0ULL, 0ULL, 0ULL, 0ULL}, nw[4] = {0ULL, 0ULL, 0ULL, 0ULL};
-        if (valid) {
-          const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(xr + w);
-          const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(xr + w + 2);
-          o[0] = a.x;
-          o[1] = a.y;
-          o[2] = b.x;
-          o[3] = b.y;
-          ld_nc_256(nw, yr + w);
-        }
-        uint64_t d[4];
+      const int32_t vl = i < nF ? F[i] : -1;  // this lane's row in the transpose
+      const int w = w0 + wl;
+      const bool wok = w < Wp;
+      for (int r0 = 0; r0 < 32; r0 += 8) {  // 4 rows per half-warp: 8 loads in flight
+        int32_t v[4];
+        uint64_t x[4], y[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = o[k] ^ nw[k];
-        if ((d[0] | d[1] | d[2] | d[3]) != 0ULL) {  // the deltas were zero before
-          store_words<4>(xr + w, nw);
-          store_words<4>(dr + w, d);
+        for (int k = 0; k < 4; ++k) {
+          v[k] = __shfl_sync(kFullMask, vl, r0 + 2 * k + half);
+          x[k] = y[k] = 0ULL;
+          if (v[k] >= 0 && wok) {
+            const size_t o = (size_t)v[k] * Wp + w;
+            x[k] = p.X[o];
+            y[k] = __ldg(reinterpret_cast<const unsigned long long *>(p.Y) + o);
+          }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          gained += (uint32_t)__popcll(d[k]);
-          if (__any_sync(kFullMask, d[k] != 0ULL)) {
-            const uint32_t n0 = __popc(transpose32((uint32_t)d[k], lane));
-            const uint32_t n1 = __popc(transpose32((uint32_t)(d[k] >> 32), lane));
-            const int c0 = (w + k) * 64 + lane;
-            if (n0) atomicAdd(&cdst[c0], n0);
-            if (n1) atomicAdd(&cdst[c0 + 32], n1);
+          const uint64_t d = x[k] ^ y[k];
+          if (d) {  // the delta buffer of this round is zero elsewhere
+            const size_t o = (size_t)v[k] * Wp + w;
+            p.X[o] = y[k];
+            Dcur[o] = d;
           }
+          tl[r0 + 2 * k + half][wl] = d;
         }
       }
-      if (gained && atomicAdd(p.rowbits + v, gained) + gained == (uint32_t)s) set_bit(p.Sat, v);
+      __syncwarp();
+      uint32_t gained = 0;
+      for (int k = 0; k < 16; ++k) {
+        const uint64_t d = tl[lane][k];
+        gained += (uint32_t)__popcll(d);
+        if (__any_sync(kFullMask, d != 0ULL)) {
+          const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+          const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+          const int c0 = (w0 + k) * 64 + lane;
+          if (n0) atomicAdd(&cdst[c0], n0);
+          if (n1) atomicAdd(&cdst[c0 + 32], n1);
+        }
+      }
+      __syncwarp();
+      if (gained && atomicAdd(p.rowbits + vl, gained) + gained == (uint32_t)s) set_bit(p.Sat, vl);
     }
   } else {
   for (int64_t base = warp * 32; base < nF; base += nwarps * 32) {
@@ -451,8 +462,6 @@ __global__ void k_window_shift(Params p, int64_t count_words, int32_t rs_slots) 
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   __shared__ RoundStats carry;
   if (threadIdx.x == 0 && blockIdx.x == 0) carry = p.rs[p.row_cap];
-  if (p.rowbits)
-    for (int64_t i = gtid; i < p.n; i += nth) p.rowbits[i] = 0u;
   for (int64_t i = gtid; i < count_words; i += nth) p.counts[i] = 0u;
   __syncthreads();
   if (blockIdx.x == 0) {
@@ -547,6 +556,24 @@ static const void *post_fn(const Plan &pl) {
   if (pl.post_wide)
     return pl.smem_counts ? (const void *)&k_post<true, true> : (const void *)&k_post<false, true>;
   return pl.smem_counts ? (const void *)&k_post<true, false> : (const void *)&k_post<false, false>;
+}
+
+// Raises the dynamic shared memory limit of the shared-counter post kernels
+// to the largest count window (once per device, before any launch, so that
+// no thread changes it while another launches them).
+static void post_smem_optin() {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && (done >> dev) & 1ULL) return;
+  const int mx = (int)(sizeof(uint32_t) * kSmemCountMax);
+  cudaFuncSetAttribute((const void *)&k_post<true, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute((const void *)&k_post<true, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (dev < 64) done |= 1ULL << dev;
 }
 
 static void launch_post(const Plan &pl, const Params &p, cudaStream_t st) {
@@ -860,13 +887,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
 
   const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
-  // the wide part A has a warp per 32 rows x 32 words
+  // the wide part A has a warp per 32 rows x 16 words
   const int64_t post_threads =
-      pl.post_wide ? (n + 31) / 32 * (int64_t)((pl.Wp + 31) / 32) * 32 : n;
+      pl.post_wide ? (n + 31) / 32 * (int64_t)((pl.Wp + 15) / 16) * 32 : n;
+  post_smem_optin();
   pl.grid_post = occupancy_grid(post_fn(pl), pl.post_smem, std::max<int64_t>(post_threads, nbm));
-  if (pl.post_smem > 48 * 1024)
-    cudaFuncSetAttribute(post_fn(pl), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pl.post_smem);
 
   const bool timing = cl.o.timing != 0;
   const bool graphs = cl.o.use_graphs != 0 && !timing;
