@@ -230,7 +230,7 @@ def run_ours(args):
         o_s, rep_s = pg.autotune(G, seeds, max_trials=args.tune_trials, stream=sptr,
                                  algorithm="s")
         keys = ("direction", "dense_threshold", "group_lanes", "test_changed",
-                "words_per_thread", "wide_rows", "passes_together")
+                "words_per_thread", "wide_rows", "passes_together", "pass_words")
         tuned = {"tune_s": time.perf_counter() - t0,
                  "p": {k: pg.options_dict(o_p)[k] for k in keys} | {"trials": rep_p["trials"]},
                  "s": {k: pg.options_dict(o_s)[k] for k in keys} | {"trials": rep_s["trials"]}}

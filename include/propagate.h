@@ -135,6 +135,16 @@ typedef struct {
                                as many as keep the copies under 2^24 arcs
                                (small graphs, where one pass cannot fill the
                                GPU) */
+  int32_t pass_words;       /* PROPAGATE-S with 64 planes per pass: passes
+                               run side by side as the words of one
+                               signature over the same graph (word k = pass
+                               k's 64 one-bit planes; passes never exchange
+                               bits, and counts, rounds and m_active are each
+                               pass's own). 1 = one word per node; 2, 4 or
+                               8 = that many passes per propagation, as far
+                               as a quarter of the free device memory holds
+                               them; 0 = automatic: up to 8 when the graph is
+                               too large for copies (passes_together) */
 } pg_options;
 
 #define PG_DIR_AUTO 0

@@ -28,7 +28,8 @@ class Options(ctypes.Structure):
                 ("test_changed", ctypes.c_int32), ("planes_per_pass", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("window_rows", ctypes.c_int32), ("words_per_thread", ctypes.c_int32),
-                ("wide_rows", ctypes.c_int32), ("passes_together", ctypes.c_int32)]
+                ("wide_rows", ctypes.c_int32), ("passes_together", ctypes.c_int32),
+                ("pass_words", ctypes.c_int32)]
 
 
 class Counts(ctypes.Structure):

@@ -71,6 +71,10 @@ struct Params {
   uint32_t *K0, *K1;   // claim / active bitmaps, alternating
   uint32_t *Sat;       // saturated (all s bits set)
   uint32_t *rowbits;   // wide rows: set bits of each row so far (else null)
+  // PROPAGATE-S passes as the words of one signature: m_active per pass, with
+  // one claim bit per (word, row) for rows cut into pieces, by round parity
+  int32_t pass_words;
+  uint32_t *Kw0, *Kw1;  // [Wp][nbm] each (null unless pass_words)
   int64_t nbm;         // 32-bit words per bitmap
   int32_t *F0, *F1;    // rows changed in round t, by round parity
   unsigned long long *E;  // out-arc pieces of F rows: (row << 32) | piece of LE arcs
@@ -123,7 +127,7 @@ struct DevBuf {
 };
 
 struct Workspace {
-  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, F0, F1, E, A, counts, rs, ctrl, seeds,
+  DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, KW0, KW1, F0, F1, E, A, counts, rs, ctrl, seeds,
       seed_bits, gfsum, gthr;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};

@@ -469,7 +469,7 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
 }
 
 void release_workspace(Workspace &w) {
-  for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB, &w.F0,
+  for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB, &w.KW0, &w.KW1, &w.F0,
                     &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum,
                     &w.gthr})
     release(*b);
@@ -485,7 +485,7 @@ void release_workspace(Workspace &w) {
 
 int64_t workspace_held(const Workspace &w) {
   int64_t b = 0;
-  for (const DevBuf *x : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB,
+  for (const DevBuf *x : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB, &w.KW0, &w.KW1,
                           &w.F0, &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds,
                           &w.seed_bits, &w.gfsum, &w.gthr})
     b += (int64_t)x->bytes;

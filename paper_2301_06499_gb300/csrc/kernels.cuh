@@ -246,6 +246,36 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
   return changed;
 }
 
+// PROPAGATE-S with its passes as the words of one signature (p.pass_words):
+// word w of a row holds pass w's 64 one-bit planes. A row is active in pass
+// w in round t when an in-neighbour gained bits of that pass in round t-1
+// (its OR of deltas, acc, is nonzero in word w) and the row still lacks one
+// of the pass's bits (word w of X not full): the skip rule of Thm. 1 applied
+// to each pass on its own, as if the passes ran one after another. Adds the
+// active passes of one row piece to words (and their seeds to seeds); a row
+// cut into pieces is counted once per pass, by the piece whose claim bit
+// for that pass is set first.
+template <int CW>
+__device__ __forceinline__ void count_pass_words(const Params &p, int32_t v, int c, bool whole,
+                                                 const uint64_t (&own)[CW],
+                                                 const uint64_t (&acc)[CW], uint32_t *Kw,
+                                                 uint32_t &words, uint32_t &seeds) {
+#pragma unroll
+  for (int k = 0; k < CW; ++k) {
+    if (!acc[k]) continue;
+    const int w = c * CW + k;
+    if (!whole && set_bit(Kw + (size_t)w * (size_t)p.nbm, v)) continue;
+    const uint64_t vm = valid_mask(w, p.s);
+    const uint64_t x =
+        whole ? own[k]
+              : __ldg(reinterpret_cast<const unsigned long long *>(p.X) + (size_t)v * p.Wp + w);
+    if ((x | ~vm) != ~0ULL) {
+      ++words;
+      seeds += (uint32_t)__popcll(vm);
+    }
+  }
+}
+
 // Tuning knobs (compile-time): minimum resident blocks per SM for the pull
 // kernel (caps registers; the kernels are latency-bound, so occupancy pays:
 // 4 blocks of 256 threads = 64 registers, measured 10% faster than 3 for
@@ -275,10 +305,10 @@ __device__ __forceinline__ bool finish_piece(const Params &p, int32_t v, int c, 
 //    a chunk starts and its first U column indices when the chunk ends
 //    (before the frontier append), ahead of the saturation test: there the
 //    latency matters more than the reads wasted on saturated rows.
-template <int CW>
+template <int CW, bool PW>
 __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const uint64_t *Dprev,
                                            const uint32_t *Cprev, int32_t *F, uint32_t *Ccur,
-                                           uint32_t *Kcur, int lane,
+                                           uint32_t *Kcur, uint32_t *Kwcur, int lane,
                                            int64_t warp, int64_t nwarps,
                                            uint32_t &my_mact,
                                            unsigned long long &my_work,
@@ -339,6 +369,7 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       for (int q = 0; q < U; ++q) u0[q] = act && q < len ? __ldg(cc + 32LL * q) : -1;
     }
     bool row_changed = false, any_delta = false;
+    uint32_t pw_words = 0, pw_seeds = 0;
     for (int ch = 0; ch < nch; ++ch) {
       uint64_t own[CW], acc[CW];
 #pragma unroll
@@ -379,6 +410,8 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       }
 #pragma unroll
       for (int k = 0; k < CW; ++k) any_delta |= acc[k] != 0ULL;
+      if constexpr (PW)
+        if (act) count_pass_words<CW>(p, v, ch, whole, own, acc, Kwcur, pw_words, pw_seeds);
       if (act) row_changed |= finish_piece<CW>(p, v, ch, whole, own, acc);
     }
     if (has_next) first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
@@ -387,7 +420,14 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       my_scan += (uint32_t)len;
     }
     act = act && any_delta;  // no changed in-neighbour: not active in round t
-    if (act) {
+    if (PW && act) {
+      if (pw_words) {
+        const uint32_t deg =
+            whole ? (uint32_t)len : (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        my_mact += deg * pw_words;
+        my_work += (unsigned long long)deg * (unsigned long long)pw_seeds;
+      }
+    } else if (act) {
       uint32_t deg = 0;
       if (whole)
         deg = (uint32_t)len;
@@ -429,12 +469,15 @@ struct PullUnroll {
 // Activity (for m_active) follows the skip rule of the proof of Thm. 1: a
 // node is revisited in round t when it still has a zero bit (not saturated)
 // and some in-neighbour changed in round t-1 (a nonzero delta). Sparse rounds
-// count it when the row is claimed.
+// count it when the row is claimed (PW: here, per pass).
 //
 // With p.test_changed, an in-neighbour's changed bit (C_{t-1}, n bits, kept in
 // L2) is tested before its delta is gathered, so unchanged neighbours cost no
 // signature-sized read: worth it when the deltas are far larger than L2.
-template <int CW, int G>
+//
+// PW: PROPAGATE-S passes as the words of one signature; m_active is counted
+// per pass here (count_pass_words), in dense and sparse rounds alike.
+template <int CW, int G, bool PW>
 __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL_MIN_BLOCKS_WIDE)
     k_pull(Params p) {
   constexpr int UNR = PullUnroll<CW>::value;
@@ -449,10 +492,15 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
   uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
   uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
+  uint32_t *Kwcur = (t & 1) ? p.Kw1 : p.Kw0;
 
   const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * kBlock;
   for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
+  if constexpr (PW) {  // the per-pass claim bits of round t+1
+    uint32_t *Kwnext = (t & 1) ? p.Kw0 : p.Kw1;
+    for (int64_t i = gtid; i < p.nbm * p.Wp; i += nthreads) Kwnext[i] = 0u;
+  }
 
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5;
@@ -464,8 +512,8 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
   // of the graphs that chose a full sweep and take the others' work list
   if (mode != kModeSparse)
-    pull_dense<CW>(p, ctrl, Dprev, Cprev, F, Ccur, Kcur, lane, warp, nwarps, my_mact, my_work,
-                   my_scan, my_gath, my_items);
+    pull_dense<CW, PW>(p, ctrl, Dprev, Cprev, F, Ccur, Kcur, Kwcur, lane, warp, nwarps, my_mact,
+                   my_work, my_scan, my_gath, my_items);
   if (mode != kModeDense) {
     const int gl = lane & (G - 1);
     const int gw = lane / G;
@@ -506,6 +554,7 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
           if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
       }
       bool row_changed = false;
+      uint32_t pw_words = 0, pw_seeds = 0;
       for (int c = 0; c < nch; ++c) {
         uint64_t own[CW], acc[CW];
 #pragma unroll
@@ -522,7 +571,15 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
 #pragma unroll
           for (int k = 0; k < CW; ++k) acc[k] |= __shfl_xor_sync(kFullMask, acc[k], off);
         }
+        if constexpr (PW)
+          if (act && gl == 0) count_pass_words<CW>(p, v, c, whole, own, acc, Kwcur, pw_words, pw_seeds);
         if (act && gl == 0) row_changed |= finish_piece<CW>(p, v, c, whole, own, acc);
+      }
+      if (PW && pw_words) {  // passes as words: m_active here, not at the claim
+        const uint32_t deg =
+            whole ? (uint32_t)len : (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        my_mact += deg * pw_words;
+        my_work += (unsigned long long)deg * (unsigned long long)pw_seeds;
       }
       bool app = false;
       if (act && gl == 0 && row_changed) {
@@ -544,10 +601,10 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
 }
 
 using PullFn = void (*)(Params);
-PullFn pull_fn_cw1(int G);
-PullFn pull_fn_cw2(int G);
-PullFn pull_fn_cw4(int G);
-PullFn pull_fn_cw8(int G);
+PullFn pull_fn_cw1(int G, bool pw);
+PullFn pull_fn_cw2(int G, bool pw);
+PullFn pull_fn_cw4(int G, bool pw);
+PullFn pull_fn_cw8(int G, bool pw);
 // Wide rows (more than 8 words): a warp per row piece, for Wp words per row.
 PullFn pull_fn_wide(int Wp);
 

@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
   }
   if (p.rowbits)
     for (int64_t i = gtid; i < p.n; i += nth) p.rowbits[i] = 0u;
+  if (p.pass_words)
+    for (int64_t i = gtid; i < p.nbm * p.Wp; i += nth) {
+      p.Kw0[i] = 0u;
+      p.Kw1[i] = 0u;
+    }
   for (int64_t i = gtid; i < count_words; i += nth) p.counts[i] = 0u;
   unsigned long long *rsw = reinterpret_cast<unsigned long long *>(p.rs);
   for (int64_t i = gtid; i < rs_words; i += nth) rsw[i] = 0ULL;
@@ -394,8 +399,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
           if (claim[q]) {
             rb = __ldg(p.row_ptr + x[q]);
             indeg = __ldg(p.row_ptr + x[q] + 1) - rb;
-            my_mact += (unsigned long long)indeg;
-            my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
+            if (!p.pass_words) {  // passes as words: the pull counts each pass
+              my_mact += (unsigned long long)indeg;
+              my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
+            }
             np = (unsigned long long)((indeg + p.L - 1) / p.L);
           }
           warp_append_items(p.A, &ctrl->nA_next, x[q], rb, indeg, p.L, np, lane);
@@ -490,12 +497,12 @@ struct Plan {
   bool post_wide = false;  // k_post's tiled part A (rows of 16+ words, one graph)
 };
 
-static PullFn pick_pull(int CW, int G) {
+static PullFn pick_pull(int CW, int G, bool pw = false) {
   switch (CW) {
-    case 1: return pull_fn_cw1(G);
-    case 2: return pull_fn_cw2(G);
-    case 4: return pull_fn_cw4(G);
-    case 8: return pull_fn_cw8(G);
+    case 1: return pull_fn_cw1(G, pw);
+    case 2: return pull_fn_cw2(G, pw);
+    case 4: return pull_fn_cw4(G, pw);
+    case 8: return pull_fn_cw8(G, pw);
   }
   return nullptr;
 }
@@ -777,8 +784,10 @@ struct BatchSeg {
 
 // One pass: sp seeds of the call, columns [col0, col0+sp); or, with bs, all
 // seeds of a packed batch.
+// With pw, the sp seeds are ceil(sp/64) PROPAGATE-S passes of 64 planes run
+// side by side as the words of one signature (m_active counted per pass).
 static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bool eb,
-                          int hint, PassOut &po, const BatchSeg *bs = nullptr) {
+                          int hint, PassOut &po, const BatchSeg *bs = nullptr, bool pw = false) {
   pg_graph *g = cl.g;
   Workspace &w = g->ext_ws ? *g->ext_ws : g->ws;
   cudaStream_t st = cl.st;
@@ -787,6 +796,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   const int ncols = bs ? bs->ncols : sp;
   pg_status rc = make_plan(g, s_bits, cl.o, eb, pl);
   if (rc) return rc;
+  if (pw) {  // at most 8 words: never the wide-row kernel
+    if (pl.wide) return PG_EINVAL;
+    pl.pull = pick_pull(pl.CW, pl.G, true);
+    if (!pl.pull) return PG_EINVAL;
+  }
   if (bs) {  // a batch's columns: in shared memory when they fit
     pl.smem_counts = ncols <= kSmemCountMax;
     pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)ncols : 0;
@@ -807,6 +821,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     if ((rc = ensure(*b, sizeof(uint32_t) * nbm))) return rc;
   pl.post_wide = !bs && pl.Wp >= kWidePostWords;
   if (pl.post_wide && (rc = ensure(w.RB, sizeof(uint32_t) * n))) return rc;
+  if (pw && ((rc = ensure(w.KW0, sizeof(uint32_t) * nbm * pl.Wp)) ||
+             (rc = ensure(w.KW1, sizeof(uint32_t) * nbm * pl.Wp))))
+    return rc;
   if ((rc = ensure(w.F0, sizeof(int32_t) * n)) || (rc = ensure(w.F1, sizeof(int32_t) * n)) ||
       (rc = ensure(w.E, sizeof(unsigned long long) * e_cap)) ||
       (rc = ensure(w.A, sizeof(ulonglong2) * std::max<int64_t>(g->pieces.count, 1))) ||
@@ -845,6 +862,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.K1 = (uint32_t *)w.K1.p;
   p.Sat = (uint32_t *)w.Sat.p;
   p.rowbits = pl.post_wide ? (uint32_t *)w.RB.p : nullptr;
+  p.pass_words = pw ? 1 : 0;
+  p.Kw0 = pw ? (uint32_t *)w.KW0.p : nullptr;
+  p.Kw1 = pw ? (uint32_t *)w.KW1.p : nullptr;
   p.nbm = nbm;
   p.F0 = (int32_t *)w.F0.p;
   p.F1 = (int32_t *)w.F1.p;
@@ -1104,6 +1124,7 @@ constexpr int64_t kReplicaArcs = 1LL << 24;
 
 static int passes_together(const pg_graph *g, int npasses, const pg_options &o) {
   if (npasses < 2 || o.passes_together == 1) return 1;
+  if (o.passes_together == 0 && o.pass_words > 1) return 1;
   int K = o.passes_together > 1
               ? std::min(o.passes_together, npasses)
               : (int)std::min<int64_t>(npasses, kReplicaArcs / std::max<int64_t>(g->m, 1));
@@ -1119,6 +1140,22 @@ static int passes_together(const pg_graph *g, int npasses, const pg_options &o) 
   while (K > 1 && ((int64_t)K * per_copy > (int64_t)(fr / 4) || (int64_t)K * g->n >= 0x7FFFFFFFLL ||
                    (int64_t)K * g->m >= (1LL << kFsumBits)))
     --K;
+  return K;
+}
+
+// PROPAGATE-S passes per propagation as words of one signature (see
+// pg_options.pass_words): 1, 2, 4 or 8, as far as a quarter of the free
+// device memory holds the signatures (four buffers of n x words x 8 bytes).
+static int pass_words_for(const pg_graph *g, int npasses, int planes, const pg_options &o) {
+  if (planes != 64 || npasses < 2 || o.pass_words == 1) return 1;
+  int K = o.pass_words > 1 ? o.pass_words : 8;
+  while (K > 2 && K / 2 >= npasses) K /= 2;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  while (K > 1 && 4 * g->n * (int64_t)K * 8 > (int64_t)(fr / 4)) K /= 2;
   return K;
 }
 
@@ -1148,12 +1185,19 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
+  if (cl.o.pass_words < 0 || cl.o.pass_words > 8 ||
+      (cl.o.pass_words > 1 && (cl.o.pass_words & (cl.o.pass_words - 1))))
+    return PG_EINVAL;
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
   cl.counts_h = out->counts;
   const int planes =
       s_mode ? (cl.o.planes_per_pass > 0 ? std::min(cl.o.planes_per_pass, 64) : 64) : s;
-  const int widest = std::min(planes, s);
+  const int npasses = (s + planes - 1) / planes;
+  const int K = s_mode ? passes_together(g, npasses, cl.o) : 1;
+  const int KW = s_mode && K <= 1 ? pass_words_for(g, npasses, planes, cl.o) : 1;
+  const int step = KW > 1 ? 64 * KW : planes;  // seeds per propagation
+  const int widest = std::min(step, s);
   // counts window: up to max_rounds+1 rows, at most ~256 MB of counters
   int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * widest));
   if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
@@ -1163,8 +1207,6 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   int32_t T = 0, status = PG_OK;
   int passes = 0;
   int &hint = s_mode ? g->hint_s : g->hint_p;
-  const int npasses = (s + planes - 1) / planes;
-  const int K = s_mode ? passes_together(g, npasses, cl.o) : 1;
   if (K > 1) {
     // PROPAGATE-S passes K at a time, as one propagation over K copies of the
     // graph: pass k's planes live in copy k (its seeds shifted by k*n), its
@@ -1241,16 +1283,16 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
       st.post_launches += po.post_launches;
     }
   }
-  for (int b = 0; K <= 1 && b < s; b += planes) {
-    const int sp = std::min(planes, s - b);
+  for (int b = 0; K <= 1 && b < s; b += step) {
+    const int sp = std::min(step, s - b);
     PassOut po;
-    rc = run_pass(cl, seeds + b, sp, b, s_mode, hint, po);
+    rc = run_pass(cl, seeds + b, sp, b, s_mode && KW <= 1, hint, po, nullptr, KW > 1);
     if (rc == PG_OK && po.status == PG_OK) hint = std::min(po.rounds + 1, 64);
     if (rc) {
       cudaGetLastError();
       return rc;
     }
-    ++passes;
+    passes += KW > 1 ? (sp + 63) / 64 : 1;
     // rows that only some passes reached: the others' columns are zero there
     if (po.rounds < T) {
       for (int32_t t = po.rounds + 1; t <= std::min(T, out->max_rounds); ++t)
@@ -1287,7 +1329,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   st.sweeps = T + 1;
   st.passes = passes;
   Plan pl;
-  make_plan(g, std::min(planes, s), cl.o, s_mode, pl);
+  make_plan(g, widest, cl.o, s_mode && KW <= 1, pl);
   st.words_per_row = pl.Wp;
   st.group_lanes = pl.G;
   st.words_per_gather = pl.wide ? 0 : pl.CW;
@@ -1319,6 +1361,9 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
+  if (cl.o.pass_words < 0 || cl.o.pass_words > 8 ||
+      (cl.o.pass_words > 1 && (cl.o.pass_words & (cl.o.pass_words - 1))))
+    return PG_EINVAL;
   cl.s_total = ncols;
   cl.max_rounds = max_rounds;
   cl.counts_h = nullptr;
@@ -1396,7 +1441,7 @@ int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_
   const int64_t cap_rows =
       window_rows > 0 ? window_rows : std::max<int64_t>(64, (256LL << 20) / (4LL * s));
   const int64_t row_cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
-  return 4 * n * Wp * 8 + 5 * nbm * 4 + 3 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
+  return 4 * n * Wp * 8 + (5 + 2 * Wp) * nbm * 4 + 3 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
          pieces * 16 + row_cap * s * 4 + (row_cap + 2) * (int64_t)sizeof(RoundStats) +
          (int64_t)s * 8 + 4096;
 }
@@ -1428,6 +1473,7 @@ void pg_default_options(pg_options *o) {
   o->words_per_thread = 0;
   o->wide_rows = 0;
   o->passes_together = 0;
+  o->pass_words = 0;
 }
 
 pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,

@@ -3,16 +3,19 @@
 
 namespace pg {
 
-PullFn pull_fn_cw1(int G) {
+template <bool PW>
+static PullFn pick(int G) {
   switch (G) {
-    case 1: return &k_pull<1, 1>;
-    case 2: return &k_pull<1, 2>;
-    case 4: return &k_pull<1, 4>;
-    case 8: return &k_pull<1, 8>;
-    case 16: return &k_pull<1, 16>;
-    case 32: return &k_pull<1, 32>;
+    case 1: return &k_pull<1, 1, PW>;
+    case 2: return &k_pull<1, 2, PW>;
+    case 4: return &k_pull<1, 4, PW>;
+    case 8: return &k_pull<1, 8, PW>;
+    case 16: return &k_pull<1, 16, PW>;
+    case 32: return &k_pull<1, 32, PW>;
   }
   return nullptr;
 }
+
+PullFn pull_fn_cw1(int G, bool pw) { return pw ? pick<true>(G) : pick<false>(G); }
 
 }  // namespace pg

@@ -38,7 +38,7 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
   uint64_t want = 0;
   auto measure = [&](const pg_options &o, double *ms) -> pg_status {
     double t_min = 0.0;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {  // the best of three: the first may build a CUDA graph
       uint64_t h = 0;
       double t = 0.0;
       pg_status rc = run(o, &t, &h);
@@ -54,14 +54,6 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
   pg_status rc = measure(cur, &best);
   if (rc) return rc;
   r.default_ms = best;
-  const int W = s_mode ? 1 : (s_bits + 63) / 64;  // PROPAGATE-S: one word per node
-  const int cw_class = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
-  std::vector<int> wpt;
-  for (int c : {0, 1, 2, 4, 8})
-    if (c <= cw_class && cw_class > 1) wpt.push_back(c);
-  const int lanes[] = {0, 1, 2, 4, 8, 16, 32};
-  const float dens[] = {0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.5f};
-  const int tests[] = {0, 1, 2};
   auto try_value = [&](pg_options cand) -> pg_status {
     if (r.trials >= max_trials) return PG_OK;
     double t = 0.0;
@@ -74,6 +66,34 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
     }
     return PG_OK;
   };
+  const int npasses = (s_bits + 63) / 64;
+  if (s_mode && npasses > 1) {
+    // PROPAGATE-S, first the pass schedule: (copies, words) = one pass at a
+    // time, passes on copies of the graph, or passes as signature words
+    const int pairs[][2] = {{1, 1}, {2, 1}, {4, 1}, {0, 2}, {0, 4}, {0, 8}};
+    for (const auto &pr : pairs) {
+      if (pr[1] > 2 * npasses) continue;
+      if (pr[0] == cur.passes_together && pr[1] == cur.pass_words) continue;
+      pg_options o = cur;
+      o.passes_together = pr[0];
+      o.pass_words = pr[1];
+      if ((rc = try_value(o))) return rc;
+    }
+  }
+  // words per node of the runs that follow (PROPAGATE-S: one, or its passes
+  // as words when they may be)
+  int W = (s_bits + 63) / 64;
+  if (s_mode)
+    W = cur.pass_words > 1 ? std::min(cur.pass_words, npasses)
+        : cur.pass_words == 0 && cur.passes_together <= 1 ? std::min(8, npasses)
+                                                           : 1;
+  const int cw_class = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
+  std::vector<int> wpt;
+  for (int c : {0, 1, 2, 4, 8})
+    if (c <= cw_class && cw_class > 1) wpt.push_back(c);
+  const int lanes[] = {0, 1, 2, 4, 8, 16, 32};
+  const float dens[] = {0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.5f};
+  const int tests[] = {0, 1, 2};
   if (W > 8) {  // a warp per row piece, or lanes over 8-word chunks
     pg_options o = cur;
     o.wide_rows = cur.wide_rows == 2 ? 0 : 2;
@@ -104,14 +124,6 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
     pg_options o = cur;
     o.test_changed = tc;
     if ((rc = try_value(o))) return rc;
-  }
-  if (s_mode && s_bits > 64) {  // PROPAGATE-S: passes one at a time or together
-    for (int k : {1, 2, 4, 0}) {
-      if (k == cur.passes_together) continue;
-      pg_options o = cur;
-      o.passes_together = k;
-      if ((rc = try_value(o))) return rc;
-    }
   }
   r.best_ms = best;
   *inout = cur;

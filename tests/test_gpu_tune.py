@@ -209,3 +209,42 @@ def test_exact_mode_313_words():
     m = pg.metrics(res, g.n)
     for k in ("R_last", "avg_distance"):
         assert m[k] == pytest.approx(want["metrics"][k], rel=1e-12)
+
+
+# ------------------------------------------- PROPAGATE-S passes as words
+@functools.lru_cache(maxsize=None)
+def _pw_case(kind):
+    if kind == "rmat":  # hubs: rows cut into pieces
+        g = I.rmat(12, 10, 91, directed=True)
+    elif kind == "grid":  # many rounds: passes end at different rounds
+        g = I.grid(40, 40, 0.05, 92)
+    else:
+        g = I.er(3000, 6, 93)
+    seeds = I.seeds(g.n, 300, 94)  # 5 passes, the last of 44 seeds
+    want = oracle.run(g, seeds)
+    return g, seeds, want, _oracle_s_mactive(g, seeds, 64, want["rounds"])
+
+
+@pytest.mark.parametrize("kind", ["rmat", "grid", "er"])
+@pytest.mark.parametrize("words", [2, 4, 8])
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+def test_s_pass_words_identical(kind, words, direction):
+    """Passes side by side as signature words: counts and rounds as the
+    oracle's, m_active as the passes' own, summed (skip rule per pass)."""
+    g, seeds, want, mact = _pw_case(kind)
+    G = pg.Graph.from_inputs(g)
+    for lanes, wpt in ((0, 0), (1, 0), (1, 1), (4, 2)):  # lanes 1: many rows in pieces
+        res = pg.propagate_s(G, seeds, opts=pg.options(pass_words=words, direction=direction,
+                                                       group_lanes=lanes, words_per_thread=wpt))
+        assert res.rounds == want["rounds"], (lanes, wpt)
+        assert np.array_equal(res.counts, want["counts"]), (lanes, wpt)
+        assert np.array_equal(res.m_active, mact), (lanes, wpt)
+        assert G.last_stats()["passes"] == 5
+
+
+def test_s_pass_words_rejects_bad_values():
+    g, seeds, _, _ = _pw_case("er")
+    G = pg.Graph.from_inputs(g)
+    for bad in (3, 16, -1):
+        with pytest.raises(pg.PropagateError):
+            pg.propagate_s(G, seeds, opts=pg.options(pass_words=bad))
