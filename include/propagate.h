@@ -189,6 +189,9 @@ typedef struct {
   uint64_t seed_edge_traversals; /* sum over rounds and active rows of
                                s x in-degree (the benchmark's work measure;
                                s of the row's own graph in a batch) */
+  int32_t pass_words;        /* PROPAGATE-S: passes run side by side as the
+                                words of one signature (the pull instantiation
+                                k_pull<words, lanes, 1>); 1 otherwise */
 } pg_stats;
 
 /* Message for a status code (static storage). */

@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("ms_pull", ctypes.c_double), ("ms_post", ctypes.c_double),
                 ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
                 ("post_launches", ctypes.c_int32), ("test_changed", ctypes.c_int32),
-                ("words_per_gather", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64)]
+                ("words_per_gather", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64),
+                ("pass_words", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):

@@ -1332,6 +1332,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   make_plan(g, widest, cl.o, s_mode && KW <= 1, pl);
   st.words_per_row = pl.Wp;
   st.group_lanes = pl.G;
+  st.pass_words = KW;
   st.words_per_gather = pl.wide ? 0 : pl.CW;
   st.test_changed = cl.o.test_changed == 1 ||
                     (cl.o.test_changed == 0 && g->n * (int64_t)pl.Wp * 8 > (64LL << 20));
@@ -1407,6 +1408,7 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
     if (make_plan(g, bs ? bs->s_bits : nseeds, cl.o, false, pl) == PG_OK) {
       st.words_per_row = pl.Wp;
       st.group_lanes = pl.G;
+      st.pass_words = 1;
       st.words_per_gather = pl.wide ? 0 : pl.CW;
     }
   }
