@@ -298,6 +298,38 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       }
     }
     bool full = valid;
+    if ((Wp & 3) == 0) {  // 32-byte aligned rows: a row's 4 words per load
+      for (int w = 0; w < Wp; w += 4) {
+        uint64_t o[4] = {0ULL, 0ULL, 0ULL, 0ULL}, nw[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+        if (valid) {
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(xr + w);
+          const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(xr + w + 2);
+          o[0] = a.x;
+          o[1] = a.y;
+          o[2] = b.x;
+          o[3] = b.y;
+          ld_nc_256(nw, yr + w);
+        }
+        uint64_t d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = o[k] ^ nw[k];
+        if ((d[0] | d[1] | d[2] | d[3]) != 0ULL) {  // the deltas were zero before
+          store_words<4>(xr + w, nw);
+          store_words<4>(dr + w, d);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          full = full && ((nw[k] | ~valid_mask(w + k, sv)) == ~0ULL);
+          if (one_graph && __any_sync(kFullMask, d[k] != 0ULL)) {
+            const uint32_t n0 = __popc(transpose32((uint32_t)d[k], lane));
+            const uint32_t n1 = __popc(transpose32((uint32_t)(d[k] >> 32), lane));
+            const int c0 = c0w + (w + k) * 64 + lane;
+            if (n0) atomicAdd(&cdst[c0], n0);
+            if (n1) atomicAdd(&cdst[c0 + 32], n1);
+          }
+        }
+      }
+    } else {
     for (int w = 0; w < Wp; ++w) {
       uint64_t o = 0, nw = 0;
       if (valid) {
@@ -318,6 +350,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
         if (n1) atomicAdd(&cdst[c0 + 32], n1);
       }
     }
+    }
     if (full) set_bit(p.Sat, v);
   }
   }
@@ -329,9 +362,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       for (int k = lane; k < (Wp >> 1); k += 32) dr[k] = z;
     }
   } else {
+    const ulonglong2 z = make_ulonglong2(0ULL, 0ULL);
     for (int64_t r = gtid; r < nFprev; r += nth) {  // a thread per row, no division
       uint64_t *dr = Dprev + (size_t)Fprev[r] * Wp;
-      for (int w = 0; w < Wp; ++w) dr[w] = 0ULL;
+      if ((Wp & 1) == 0)
+        for (int w = 0; w < Wp; w += 2) *reinterpret_cast<ulonglong2 *>(dr + w) = z;
+      else
+        for (int w = 0; w < Wp; ++w) dr[w] = 0ULL;
     }
   }
   if (SMEM) {
