@@ -733,13 +733,13 @@ def kernel_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def oracle_sample(g, seeds, k, steps=1):
+def oracle_sample(g, seeds, k, steps=1, threads=None):
     """Times the oracle (one FIFO BFS per seed, threads over seeds) on the
     first k seeds. Its work is the method-defined count of that k-seed
     problem, k * sum_t m_active(t), with m_active computed by the oracle from
     the sample's own distances (nothing comes from the GPU path)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     sample = np.ascontiguousarray(seeds[:k])
     hist, _, dmat = oracle.seed_histograms(g, sample, threads=threads, with_distances=True)
     work = int(k) * int(oracle.m_active(g, dmat, hist.shape[1], threads=threads).sum())
@@ -752,13 +752,42 @@ def oracle_sample(g, seeds, k, steps=1):
     return work, times, threads
 
 
+# one host sweep of Alg. 1 reads every arc: beyond this many the bench skips it
+ALG1_MAX_ARCS = 1 << 28
+
+
 def cpu_baseline(g, seeds, s, k):
+    """The oracle's BFS on all host cores (and on one, over fewer seeds), and
+    the paper's own method, Alg. 1 swept on the host (oracle.propagate_p), on
+    the same k-seed sample and credited the same work."""
+    import oracle
     work, times, threads = oracle_sample(g, seeds, k)
     dt = times[0]
-    return {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"oracle BFS from {k} of the {s} seeds on the same graph "
-                      f"({dt:.2f} s wall on {threads} threads), credited that k-seed "
-                      f"problem's k*sum_t m_active(t)"}
+    k1 = min(4, k)
+    work1, times1, _ = oracle_sample(g, seeds, k1, threads=1)
+    out = {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"oracle BFS from {k} of the {s} seeds on the same graph "
+                     f"({dt:.2f} s wall on {threads} threads), credited that k-seed "
+                     f"problem's k*sum_t m_active(t)",
+           "value_1_thread": work1 / times1[0],
+           "sample_1_thread": f"oracle BFS from {k1} seeds on one thread ({times1[0]:.2f} s)"}
+    if g.m > ALG1_MAX_ARCS:
+        out["alg1_host"] = {"skipped": f"{g.m} arcs: a host sweep per round exceeds the "
+                                       f"bench's CPU budget"}
+        return out
+    sample = np.ascontiguousarray(seeds[:k])
+    oracle.propagate_p(g, sample, threads=threads)  # warm-up
+    ta = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.propagate_p(g, sample, threads=threads)
+        ta.append(time.perf_counter() - t0)
+    out["alg1_host"] = {"value": work / min(ta), "unit": UNIT, "cores": threads,
+                        "kind": "Alg. 1 on the host (oracle.propagate_p)",
+                        "sample": f"{k} of the {s} seeds as {k}-bit signatures, best of 3 "
+                                  f"after a warm-up ({min(ta):.2f} s), credited the same "
+                                  f"work as the BFS sample"}
+    return out
 
 
 def run_reference(args):

@@ -14,6 +14,9 @@ Functions (all cite the passage they state; see ``oracle.c`` for the C):
     proof of Thm. 1, restated from distances.
   - ``metrics``: diameter, effective diameter, average distance, reachable
     pairs and connectivity rate (Sec. 3; last steps of Alg. 1).
+  - ``propagate_p``: Alg. 1 itself on the host (s-bit signatures, sweep by
+    sweep), a second statement of the per-seed counts and the paper's own
+    method timed on the host cores.
 
 The one pin that is NOT available is the paper's accuracy claim (Thm. 3,
 Table 4): it needs the real datasets. Every function here is pinned by the
@@ -68,6 +71,8 @@ def _load():
             lib.or_apsp_floyd_warshall.argtypes = [i64, vp, vp, vp]
             lib.or_m_active.restype = ctypes.c_int
             lib.or_m_active.argtypes = [i64, vp, vp, vp, i64, i64, vp, ctypes.c_int]
+            lib.or_propagate_p.restype = ctypes.c_int
+            lib.or_propagate_p.argtypes = [i64, vp, vp, vp, i64, i64, vp, vp, ctypes.c_int]
             lib.or_metrics.restype = ctypes.c_int
             lib.or_metrics.argtypes = [vp, i64, i64, i64, i64, i64,
                                        ctypes.POINTER(MetricsOut)]
@@ -142,6 +147,21 @@ def m_active(g, dmat: np.ndarray, rounds: int, threads: int = 0) -> np.ndarray:
     _check(_load().or_m_active(n, rp.ctypes.data, col.ctypes.data, dmat.ctypes.data, s, rounds,
                                out.ctypes.data, _threads(threads)), "m_active")
     return out
+
+
+def propagate_p(g, seeds, cap: int | None = None, threads: int = 0):
+    """Alg. 1 on the host: returns (counts uint32[T+1, s], T), counts[t, i] =
+    the nodes seed i's bit reached in round t (its nodes at distance t)."""
+    n, rp, col = _csr(g)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    s = seeds.size
+    cap = int(cap if cap is not None else n)
+    counts = np.zeros((cap + 1, s), dtype=np.uint32)
+    T = ctypes.c_int32(0)
+    _check(_load().or_propagate_p(n, rp.ctypes.data, col.ctypes.data, seeds.ctypes.data, s, cap,
+                                  counts.ctypes.data, ctypes.byref(T), _threads(threads)),
+           "propagate_p")
+    return np.ascontiguousarray(counts[:T.value + 1]), int(T.value)
 
 
 def metrics(hist: np.ndarray, n: int, tau_num: int = 9, tau_den: int = 10) -> dict:

@@ -22,6 +22,9 @@
  *     distances alone.
  *   - The metrics of Sec. 3 (Preliminaries) and of the last steps of
  *     Algorithm 1, in FP64 from exact 64-bit integer sums.
+ *   - Algorithm 1 itself on the host, sweep by sweep over s-bit signatures:
+ *     a second statement of the per-seed counts (checked against the BFS)
+ *     and the paper's own method timed on the host cores.
  *
  * Graph input everywhere: a CSR over in-edges, row v lists every u with an
  * arc u -> v. Distances follow arcs forward from the seed.
@@ -435,5 +438,140 @@ int or_metrics(const int64_t *hist, int64_t s, int64_t cap, int64_t n, int64_t t
   out->R_last = R[T];
   out->dist_sum = dsum;
   free(R);
+  return OR_OK;
+}
+
+/* ---------------------------------------------- Algorithm 1 on the host */
+/*
+ * PROPAGATE-P as Algorithm 1 states it. Every node has an s-bit signature
+ * (W = ceil(s/64) words; seed i sets bit i of its own node). In each round
+ * every node whose signature still has a zero bit (the skip rule of the
+ * proof of Thm. 1) ORs the signatures of all its in-neighbours into its next
+ * signature; all reads see the previous round's signatures (Sig, then
+ * Sig = Sig_next). The bits a node gains in round t are the seeds at
+ * distance exactly t (Sec. 4, paragraph on collisions), counted per seed.
+ * The rounds stop when a round gains nothing; T is the last round that
+ * gained a bit.
+ */
+typedef struct {
+  int64_t n;
+  const int64_t *rp;
+  const int32_t *col;
+  int W;
+  int64_t s;
+  uint64_t last_mask; /* valid bits of word W-1 */
+  const uint64_t *sig;
+  uint64_t *nxt;
+  uint32_t *cnt; /* [workers][s] */
+  int64_t block;
+} or_pp_ctx;
+
+static void or_pp_item(void *p, int64_t item, int w) {
+  or_pp_ctx *c = (or_pp_ctx *)p;
+  const int W = c->W;
+  uint32_t *cnt = c->cnt + (size_t)w * (size_t)c->s;
+  int64_t v1 = (item + 1) * c->block;
+  if (v1 > c->n) v1 = c->n;
+  for (int64_t v = item * c->block; v < v1; ++v) {
+    const uint64_t *sv = c->sig + (size_t)v * W;
+    uint64_t *nv = c->nxt + (size_t)v * W;
+    int full = 1;
+    for (int k = 0; k < W; ++k) {
+      nv[k] = sv[k];
+      full = full && sv[k] == (k == W - 1 ? c->last_mask : ~0ULL);
+    }
+    if (full) continue;
+    for (int64_t j = c->rp[v]; j < c->rp[v + 1]; ++j) {
+      const uint64_t *su = c->sig + (size_t)c->col[j] * W;
+      for (int k = 0; k < W; ++k) nv[k] |= su[k];
+    }
+    for (int k = 0; k < W; ++k) {
+      uint64_t d = nv[k] ^ sv[k];
+      while (d) {
+        cnt[k * 64 + __builtin_ctzll(d)] += 1;
+        d &= d - 1;
+      }
+    }
+  }
+}
+
+/*
+ * counts: [cap+1][s] uint32, row t = per-seed nodes at distance exactly t
+ * (row 0 = 1 for every seed); *rounds = T. OR_ERANGE when a round beyond
+ * cap still gains bits. Seeds must be distinct and in range.
+ */
+int or_propagate_p(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *seeds,
+                   int64_t s, int64_t cap, uint32_t *counts, int32_t *rounds, int threads) {
+  int rc = or_check_csr(n, row_ptr, col);
+  if (rc) return rc;
+  if (!seeds || s < 1 || s > n || cap < 0 || !counts || !rounds) return OR_EINVAL;
+  if (threads < 1) threads = 1;
+  const int W = (int)((s + 63) / 64);
+  uint64_t *sig = (uint64_t *)calloc((size_t)n * W, sizeof(uint64_t));
+  uint64_t *nxt = (uint64_t *)calloc((size_t)n * W, sizeof(uint64_t));
+  uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)threads * (size_t)s);
+  if (!sig || !nxt || !cnt) {
+    free(sig);
+    free(nxt);
+    free(cnt);
+    return OR_ENOMEM;
+  }
+  unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+  int bad = !seen;
+  for (int64_t i = 0; !bad && i < s; ++i) {
+    const int32_t x = seeds[i];
+    bad = x < 0 || x >= n || seen[x];
+    if (!bad) {
+      seen[x] = 1;
+      sig[(size_t)x * W + (size_t)(i / 64)] |= 1ULL << (i % 64);
+      counts[i] = 1;
+    }
+  }
+  free(seen);
+  if (bad) {
+    free(sig);
+    free(nxt);
+    free(cnt);
+    return OR_EINVAL;
+  }
+  or_pp_ctx c;
+  c.n = n;
+  c.rp = row_ptr;
+  c.col = col;
+  c.W = W;
+  c.s = s;
+  c.last_mask = (s % 64) ? ((1ULL << (s % 64)) - 1ULL) : ~0ULL;
+  c.cnt = cnt;
+  c.block = 4096;
+  const int64_t items = (n + c.block - 1) / c.block;
+  int32_t T = 0;
+  for (int64_t t = 1;; ++t) {
+    memset(cnt, 0, sizeof(uint32_t) * (size_t)threads * (size_t)s);
+    c.sig = sig;
+    c.nxt = nxt;
+    rc = or_parallel(items, threads, or_pp_item, &c);
+    if (rc) break;
+    uint64_t total = 0;
+    for (int64_t i = 0; i < s; ++i) {
+      uint32_t a = 0;
+      for (int k = 0; k < threads; ++k) a += cnt[(size_t)k * (size_t)s + (size_t)i];
+      total += a;
+      if (t <= cap) counts[(size_t)t * (size_t)s + (size_t)i] = a;
+    }
+    uint64_t *tmp = sig; /* Sig = Sig_next */
+    sig = nxt;
+    nxt = tmp;
+    if (total == 0) break;
+    if (t > cap) {
+      rc = OR_ERANGE;
+      break;
+    }
+    T = (int32_t)t;
+  }
+  free(sig);
+  free(nxt);
+  free(cnt);
+  if (rc) return rc;
+  *rounds = T;
   return OR_OK;
 }

@@ -260,3 +260,33 @@ def test_metrics_avg_distance_excludes_self_pairs_includes_in_alt():
     assert m["avg_distance"] == pytest.approx(num / (25 - 5), rel=1e-15)
     assert m["avg_distance_incl_self"] == pytest.approx(num / 25, rel=1e-15)
     assert math.isclose(m["avg_distance"], 2.0)
+
+
+# ------------------------------------------------ Alg. 1 on the host
+@pytest.mark.parametrize("kind,s", [("rmat", 1), ("rmat", 100), ("rmat", 200), ("grid", 64),
+                                    ("er", 130), ("path", 7), ("iso", 40)])
+def test_host_alg1_equals_bfs(kind, s):
+    """Alg. 1 swept on s-bit signatures gains, in round t, exactly the seeds
+    at distance t: its per-seed counts are the BFS histograms (two
+    independent statements of Sec. 4's collision count)."""
+    g = {"rmat": lambda: I.rmat(10, 8, 71, directed=True),
+         "grid": lambda: I.grid(25, 25, 0.05, 72),
+         "er": lambda: I.er(1500, 5, 73),
+         "path": lambda: I.path(60, directed=True),
+         "iso": lambda: I.from_arcs(100, [0, 1, 5], [1, 2, 6])}[kind]()
+    seeds = I.seeds(g.n, min(s, g.n), 74)
+    counts, T = oracle.propagate_p(g, seeds)
+    want = oracle.run(g, seeds)
+    assert T == want["rounds"]
+    assert np.array_equal(counts, want["counts"])
+
+
+def test_host_alg1_path_closed_form_and_errors():
+    # directed path 0 -> 1 -> ... -> 9 from seed 0: one new node per round
+    g = I.path(10, directed=True)
+    counts, T = oracle.propagate_p(g, np.array([0], np.int32))
+    assert T == 9 and counts[:, 0].tolist() == [1] * 10
+    with pytest.raises(OverflowError):  # a round beyond cap still gains bits
+        oracle.propagate_p(g, np.array([0], np.int32), cap=4)
+    with pytest.raises(ValueError):  # a repeated seed
+        oracle.propagate_p(g, np.array([3, 3], np.int32))
