@@ -197,7 +197,7 @@ def kernel_name(st: dict) -> str:
     wp, cw = st["words_per_row"], st["words_per_gather"]
     if cw == 0:  # the wide-row kernel: words per lane held in registers
         nw = 1 if wp <= 32 else 2 if wp <= 64 else 3 if wp <= 96 else 4 if wp <= 128 else 0
-        return f"k_pull_wide<{nw}>"
+        return f"k_pull_wide<{nw}, {1 if st.get('pass_words', 1) > 1 else 0}>"
     return f"k_pull<{cw}, {st['group_lanes']}, {1 if st.get('pass_words', 1) > 1 else 0}>"
 
 

@@ -132,6 +132,7 @@ typedef struct {
                                (passes never exchange bits), as far as a
                                quarter of the free device memory holds the
                                copies; 1 = one pass at a time; 0 = automatic:
+                               when passes do not run as words (pass_words),
                                as many as keep the copies under 2^24 arcs
                                (small graphs, where one pass cannot fill the
                                GPU) */
@@ -140,11 +141,13 @@ typedef struct {
                                signature over the same graph (word k = pass
                                k's 64 one-bit planes; passes never exchange
                                bits, and counts, rounds and m_active are each
-                               pass's own). 1 = one word per node; 2, 4 or
-                               8 = that many passes per propagation, as far
-                               as a quarter of the free device memory holds
-                               them; 0 = automatic: up to 8 when the graph is
-                               too large for copies (passes_together) */
+                               pass's own). 1 = one word per node; K >= 2 =
+                               up to K passes per propagation; 0 = all of
+                               them. Either as far as a quarter of the free
+                               device memory holds four buffers of n x 8K
+                               bytes; copies of the graph (passes_together)
+                               then serve only passes of fewer planes or an
+                               explicit passes_together > 1 */
 } pg_options;
 
 #define PG_DIR_AUTO 0

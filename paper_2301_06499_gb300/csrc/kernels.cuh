@@ -606,6 +606,6 @@ PullFn pull_fn_cw2(int G, bool pw);
 PullFn pull_fn_cw4(int G, bool pw);
 PullFn pull_fn_cw8(int G, bool pw);
 // Wide rows (more than 8 words): a warp per row piece, for Wp words per row.
-PullFn pull_fn_wide(int Wp);
+PullFn pull_fn_wide(int Wp, bool pw = false);
 
 }  // namespace pg

@@ -833,9 +833,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   const int ncols = bs ? bs->ncols : sp;
   pg_status rc = make_plan(g, s_bits, cl.o, eb, pl);
   if (rc) return rc;
-  if (pw) {  // at most 8 words: never the wide-row kernel
-    if (pl.wide) return PG_EINVAL;
-    pl.pull = pick_pull(pl.CW, pl.G, true);
+  if (pw) {  // the instantiations that count m_active per pass
+    pl.pull = pl.wide ? pull_fn_wide(pl.Wp, true) : pick_pull(pl.CW, pl.G, true);
     if (!pl.pull) return PG_EINVAL;
   }
   if (bs) {  // a batch's columns: in shared memory when they fit
@@ -1161,7 +1160,6 @@ constexpr int64_t kReplicaArcs = 1LL << 24;
 
 static int passes_together(const pg_graph *g, int npasses, const pg_options &o) {
   if (npasses < 2 || o.passes_together == 1) return 1;
-  if (o.passes_together == 0 && o.pass_words > 1) return 1;
   int K = o.passes_together > 1
               ? std::min(o.passes_together, npasses)
               : (int)std::min<int64_t>(npasses, kReplicaArcs / std::max<int64_t>(g->m, 1));
@@ -1181,12 +1179,12 @@ static int passes_together(const pg_graph *g, int npasses, const pg_options &o) 
 }
 
 // PROPAGATE-S passes per propagation as words of one signature (see
-// pg_options.pass_words): 1, 2, 4 or 8, as far as a quarter of the free
-// device memory holds the signatures (four buffers of n x words x 8 bytes).
+// pg_options.pass_words): the requested number, else all of them, as far as
+// a quarter of the free device memory holds the signatures (four buffers of
+// n x words x 8 bytes).
 static int pass_words_for(const pg_graph *g, int npasses, int planes, const pg_options &o) {
-  if (planes != 64 || npasses < 2 || o.pass_words == 1) return 1;
-  int K = o.pass_words > 1 ? o.pass_words : 8;
-  while (K > 2 && K / 2 >= npasses) K /= 2;
+  if (planes != 64 || npasses < 2 || o.pass_words == 1 || o.passes_together > 1) return 1;
+  int K = o.pass_words > 1 ? std::min(o.pass_words, npasses) : npasses;
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
@@ -1222,17 +1220,16 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
-  if (cl.o.pass_words < 0 || cl.o.pass_words > 8 ||
-      (cl.o.pass_words > 1 && (cl.o.pass_words & (cl.o.pass_words - 1))))
-    return PG_EINVAL;
+  if (cl.o.pass_words < 0) return PG_EINVAL;
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
   cl.counts_h = out->counts;
   const int planes =
       s_mode ? (cl.o.planes_per_pass > 0 ? std::min(cl.o.planes_per_pass, 64) : 64) : s;
   const int npasses = (s + planes - 1) / planes;
-  const int K = s_mode ? passes_together(g, npasses, cl.o) : 1;
-  const int KW = s_mode && K <= 1 ? pass_words_for(g, npasses, planes, cl.o) : 1;
+  // PROPAGATE-S: passes as signature words where they can be, else copies
+  const int KW = s_mode ? pass_words_for(g, npasses, planes, cl.o) : 1;
+  const int K = s_mode && KW <= 1 ? passes_together(g, npasses, cl.o) : 1;
   const int step = KW > 1 ? 64 * KW : planes;  // seeds per propagation
   const int widest = std::min(step, s);
   // counts window: up to max_rounds+1 rows, at most ~256 MB of counters
@@ -1399,9 +1396,7 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
-  if (cl.o.pass_words < 0 || cl.o.pass_words > 8 ||
-      (cl.o.pass_words > 1 && (cl.o.pass_words & (cl.o.pass_words - 1))))
-    return PG_EINVAL;
+  if (cl.o.pass_words < 0) return PG_EINVAL;
   cl.s_total = ncols;
   cl.max_rounds = max_rounds;
   cl.counts_h = nullptr;

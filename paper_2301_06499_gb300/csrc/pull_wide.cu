@@ -20,7 +20,10 @@ namespace pg {
 // of four neighbours are in flight), re-reading the piece's columns (from
 // L1) in each pass.
 // Five resident blocks per SM (48 registers, no spills).
-template <int NW>
+//
+// PW: PROPAGATE-S passes as the words of one signature; m_active is counted
+// per pass here, in dense and sparse rounds alike (see count_pass_words).
+template <int NW, bool PW>
 __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
   constexpr int R = NW > 0 ? NW : 4;  // words per lane per pass
   Ctrl *ctrl = p.ctrl;
@@ -33,10 +36,15 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
   uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
   uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
   uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
+  uint32_t *Kwcur = (t & 1) ? p.Kw1 : p.Kw0;
 
   const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * kBlock;
   for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
+  if constexpr (PW) {  // the per-pass claim bits of round t+1
+    uint32_t *Kwnext = (t & 1) ? p.Kw0 : p.Kw1;
+    for (int64_t i = gtid; i < p.nbm * p.Wp; i += nthreads) Kwnext[i] = 0u;
+  }
 
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5;
@@ -65,6 +73,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
     const uint64_t *xr = p.X + (size_t)v * Wp;
     uint64_t *yr = p.Y + (size_t)v * Wp;
     bool any_delta = false, row_changed = false;
+    uint32_t pw_words = 0, pw_seeds = 0;  // PW: this lane's active passes
     for (int pass = 0; pass < passes; ++pass) {
       const int w0 = pass * 32 * R + lane;  // lane's first word of this pass
       uint64_t acc[R];
@@ -100,6 +109,14 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
         const int w = w0 + 32 * r;
         if (w >= Wp) continue;
         any_delta |= acc[r] != 0ULL;
+        if (PW && acc[r] && (whole || !set_bit(Kwcur + (size_t)w * (size_t)p.nbm, v))) {
+          // pass w is active in this row unless the row already holds all its bits
+          const uint64_t vm = valid_mask(w, p.s);
+          if ((__ldg(reinterpret_cast<const unsigned long long *>(xr) + w) | ~vm) != ~0ULL) {
+            ++pw_words;
+            pw_seeds += (uint32_t)__popcll(vm);
+          }
+        }
         if (whole) {
           const uint64_t own = __ldg(reinterpret_cast<const unsigned long long *>(xr) + w);
           const uint64_t nw = own | acc[r];
@@ -116,11 +133,25 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
     }
     any_delta = __any_sync(kFullMask, any_delta);
     row_changed = __any_sync(kFullMask, row_changed);
+    if constexpr (PW) {  // the row's active passes, summed over the lanes
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        pw_words += __shfl_xor_sync(kFullMask, pw_words, off);
+        pw_seeds += __shfl_xor_sync(kFullMask, pw_seeds, off);
+      }
+      if (lane == 0 && pw_words) {
+        const unsigned long long deg =
+            whole ? (unsigned long long)len
+                  : (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        my_mact += deg * pw_words;
+        my_work += deg * pw_seeds;
+      }
+    }
     bool app = false;
     if (lane == 0) {
       ++my_items;
       my_scan += (unsigned long long)len;
-      if (dense && any_delta) {  // active in round t (sparse rounds count at the claim)
+      if (!PW && dense && any_delta) {  // active in round t (sparse rounds count at the claim)
         unsigned long long deg = 0;
         if (whole)
           deg = (unsigned long long)len;
@@ -147,12 +178,15 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
   block_add<5>(vals, dsts);
 }
 
-PullFn pull_fn_wide(int Wp) {
-  if (Wp <= 32) return &k_pull_wide<1>;
-  if (Wp <= 64) return &k_pull_wide<2>;
-  if (Wp <= 96) return &k_pull_wide<3>;
-  if (Wp <= 128) return &k_pull_wide<4>;
-  return &k_pull_wide<0>;
+template <bool PW>
+static PullFn pick(int Wp) {
+  if (Wp <= 32) return &k_pull_wide<1, PW>;
+  if (Wp <= 64) return &k_pull_wide<2, PW>;
+  if (Wp <= 96) return &k_pull_wide<3, PW>;
+  if (Wp <= 128) return &k_pull_wide<4, PW>;
+  return &k_pull_wide<0, PW>;
 }
+
+PullFn pull_fn_wide(int Wp, bool pw) { return pw ? pick<true>(Wp) : pick<false>(Wp); }
 
 }  // namespace pg

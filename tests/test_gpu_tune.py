@@ -245,6 +245,32 @@ def test_s_pass_words_identical(kind, words, direction):
 def test_s_pass_words_rejects_bad_values():
     g, seeds, _, _ = _pw_case("er")
     G = pg.Graph.from_inputs(g)
-    for bad in (3, 16, -1):
+    for bad in (-1, -64):
         with pytest.raises(pg.PropagateError):
             pg.propagate_s(G, seeds, opts=pg.options(pass_words=bad))
+
+
+@functools.lru_cache(maxsize=None)
+def _wide_mact(kind, s):
+    g, seeds, want = _wide_case(kind, s)
+    return _oracle_s_mactive(g, seeds, 64, want["rounds"])
+
+
+@pytest.mark.parametrize("kind,s", [("rmat", 600), ("rmat", 2100), ("er", 8200)])
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
+def test_s_pass_words_wide(kind, s, direction):
+    """All passes at once as the words of one wide signature (the wide-row
+    kernel: registers for 10 and 33 words, 128-word sweeps for 129), rows
+    cut into pieces on the R-MAT hubs: counts and per-pass m_active."""
+    g, seeds, want = _wide_case(kind, s)
+    G = pg.Graph.from_inputs(g)
+    res = pg.propagate_s(G, seeds, opts=pg.options(direction=direction))
+    st = G.last_stats()
+    assert st["pass_words"] == -(-s // 64) and st["words_per_gather"] == 0
+    assert res.rounds == want["rounds"]
+    assert np.array_equal(res.counts, want["counts"])
+    assert np.array_equal(res.m_active, _wide_mact(kind, s))
+    # a few passes at a time: the same
+    res2 = pg.propagate_s(G, seeds, opts=pg.options(direction=direction, pass_words=3))
+    assert np.array_equal(res2.counts, want["counts"])
+    assert np.array_equal(res2.m_active, _wide_mact(kind, s))
