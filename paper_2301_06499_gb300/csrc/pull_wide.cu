@@ -109,16 +109,18 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
         const int w = w0 + 32 * r;
         if (w >= Wp) continue;
         any_delta |= acc[r] != 0ULL;
+        uint64_t own = 0ULL;
+        if (whole || (PW && acc[r]))
+          own = __ldg(reinterpret_cast<const unsigned long long *>(xr) + w);
         if (PW && acc[r] && (whole || !set_bit(Kwcur + (size_t)w * (size_t)p.nbm, v))) {
           // pass w is active in this row unless the row already holds all its bits
           const uint64_t vm = valid_mask(w, p.s);
-          if ((__ldg(reinterpret_cast<const unsigned long long *>(xr) + w) | ~vm) != ~0ULL) {
+          if ((own | ~vm) != ~0ULL) {
             ++pw_words;
             pw_seeds += (uint32_t)__popcll(vm);
           }
         }
         if (whole) {
-          const uint64_t own = __ldg(reinterpret_cast<const unsigned long long *>(xr) + w);
           const uint64_t nw = own | acc[r];
           if (nw != own) {
             yr[w] = nw;

@@ -274,3 +274,21 @@ def test_s_pass_words_wide(kind, s, direction):
     res2 = pg.propagate_s(G, seeds, opts=pg.options(direction=direction, pass_words=3))
     assert np.array_equal(res2.counts, want["counts"])
     assert np.array_equal(res2.m_active, _wide_mact(kind, s))
+
+
+def test_wide_rows_across_counts_windows():
+    """A counts window of 3 rounds on a grid of ~80 rounds, rows of 33 and
+    16 words: the window shifts many times, and the wide post kernel's
+    per-row bit counts (which decide saturation, hence m_active) carry
+    across the shifts."""
+    g = I.grid(40, 40, 0.05, 131)
+    for s in (2100, 1000):
+        seeds = I.seeds(g.n, s, 132)
+        want = oracle.run(g, seeds)
+        assert want["rounds"] > 30
+        G = pg.Graph.from_inputs(g)
+        for use_graphs in (1, 0):
+            res = pg.propagate_p(G, seeds, opts=pg.options(window_rows=3, use_graphs=use_graphs))
+            assert res.rounds == want["rounds"]
+            assert np.array_equal(res.counts, want["counts"])
+            assert np.array_equal(res.m_active, want["m_active"])
