@@ -304,3 +304,21 @@ def test_reverse_flag_counts_backward_balls(fn):
     assert np.array_equal(res.counts, want["counts"])
     fwd = oracle.run(g, seeds)
     assert not np.array_equal(fwd["counts"][:2], want["counts"][:2])  # the direction matters
+
+
+def test_graph_create_free_cycles():
+    """Graphs created and freed over and over (the end-to-end pattern), two
+    shapes alternating: every result stays exact."""
+    g1 = I.rmat(12, 8, 141, directed=True)
+    g2 = I.grid(50, 50, 0.05, 142)
+    s1 = I.seeds(g1.n, 300, 143)
+    s2 = I.seeds(g2.n, 100, 144)
+    w1, w2 = oracle.run(g1, s1), oracle.run(g2, s2)
+    for k in range(6):
+        for g, sd, w in ((g1, s1, w1), (g2, s2, w2)):
+            G = pg.Graph.from_inputs(g)
+            r = pg.propagate_p(G, sd)
+            rs = pg.propagate_s(G, sd)
+            assert r.rounds == w["rounds"] and np.array_equal(r.counts, w["counts"])
+            assert np.array_equal(rs.counts, w["counts"])
+            G.close()

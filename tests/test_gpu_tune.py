@@ -277,11 +277,11 @@ def test_s_pass_words_wide(kind, s, direction):
 
 
 def test_wide_rows_across_counts_windows():
-    """A counts window of 3 rounds on a grid of ~80 rounds, rows of 33 and
+    """A counts window of 3 rounds on a grid of ~120 rounds, rows of 33 and
     16 words: the window shifts many times, and the wide post kernel's
     per-row bit counts (which decide saturation, hence m_active) carry
     across the shifts."""
-    g = I.grid(40, 40, 0.05, 131)
+    g = I.grid(60, 60, 0.05, 131)
     for s in (2100, 1000):
         seeds = I.seeds(g.n, s, 132)
         want = oracle.run(g, seeds)
