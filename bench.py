@@ -331,8 +331,10 @@ def run_ours(args):
     tpath = os.path.join(ROOT, "profiles", "pull_traffic.json")
     if os.path.exists(tpath):
         tr = json.load(open(tpath))
-        if tr.get("workload") == args.workload and tr.get("kernel_hash") == kernel_hash():
-            traffic_table = tr.get("bytes_per_launch", {})
+        if tr.get("workload") == args.workload:
+            hashes = tr.get("kernel_hash", {})
+            traffic_table = {k: v for k, v in tr.get("bytes_per_launch", {}).items()
+                             if isinstance(hashes, dict) and hashes.get(k) == kernel_hash(k)}
 
     def roofline_of(name):
         ms, nl, byt = per_kernel[name]
@@ -719,17 +721,23 @@ def run_serve(args):
         torch.distributed.destroy_process_group()
 
 
-def kernel_hash() -> str:
-    """Hash of the sources that define the pull kernels (their device code
-    and the parameter block): a stored DRAM-traffic figure applies only to
-    the kernels it was captured from."""
+def kernel_hash(kernel: str) -> str:
+    """Hash of the sources that define one pull kernel instantiation (its
+    device code and the parameter block): a stored DRAM-traffic figure
+    applies only to the kernel it was captured from."""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2301_06499_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name in ("kernels.cuh", "common.cuh") or (name.startswith("pull_") and
-                                                       name.endswith(".cu")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    if kernel.startswith("k_pull_wide"):
+        own = "pull_wide.cu"
+    else:
+        m = re.match(r"k_pull<(\d+)", kernel)
+        own = f"pull_cw{m.group(1)}.cu" if m else ""
+    for name in ("common.cuh", "kernels.cuh", own):
+        path = os.path.join(csrc, name)
+        if name and os.path.exists(path):
+            h.update(open(path, "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -853,6 +861,34 @@ def profile_run(args):
     print(json.dumps({"workload": args.workload, "options": pg.options_dict(o), "calls": calls}))
 
 
+def write_traffic(workload: str, csvs: list) -> None:
+    """profiles/pull_traffic.json from ncu CSV captures of the pull kernels
+    (dram__bytes_read.sum and dram__bytes_write.sum): mean bytes per launch
+    of each kernel, with the hash of the sources it was built from."""
+    from paper_2301_06499_gb300 import ncu_summary
+    per = {}
+    for path in csvs:
+        per.update(ncu_summary.traffic(path))
+    out = {"workload": workload,
+           "kernel_hash": {k: kernel_hash(k) for k in per},
+           "bytes_per_launch": per,
+           "commands": [
+               "python bench.py --profile-run p",
+               "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--nvtx --nvtx-include bench_call/ --clock-control none -k regex:k_pull --csv "
+               "--log-file traffic_p.csv python bench.py --profile-run p",
+               "(the same two lines with --profile-run s -> traffic_s.csv)",
+               "python bench.py --workload " + workload +
+               " --write-traffic traffic_p.csv traffic_s.csv"],
+           "note": "mean dram__bytes_read.sum + dram__bytes_write.sum per launch over the pull "
+                   "launches of the call the bench times (NVTX range bench_call), with the "
+                   "autotuned schedule; a kernel's figure applies while the hash of its "
+                   "sources (common.cuh, kernels.cuh and its pull_*.cu) is unchanged"}
+    with open(os.path.join(ROOT, "profiles", "pull_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(per))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -871,10 +907,14 @@ def main():
                     help="launch every round kernel on the stream (no CUDA graph), e.g. under ncu")
     ap.add_argument("--profile-run", choices=["p", "s"],
                     help="only build the workload and run PROPAGATE-P/-S twice (for ncu)")
+    ap.add_argument("--write-traffic", nargs="+", metavar="CSV",
+                    help="write profiles/pull_traffic.json from ncu captures of the pull kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_run:
+    if args.write_traffic:
+        write_traffic(args.workload, args.write_traffic)
+    elif args.profile_run:
         profile_run(args)
     elif args.workload in SERVE_WORKLOADS:
         if args.impl == "reference":

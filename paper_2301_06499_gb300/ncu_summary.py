@@ -2,10 +2,10 @@
 
   python -m paper_2301_06499_gb300.ncu_summary launches <launches.csv>
       per kernel: launches, total device time, share (markdown table)
-  python -m paper_2301_06499_gb300.ncu_summary traffic <metrics.csv> <workload> <kernel_hash> [skip]
+  python -m paper_2301_06499_gb300.ncu_summary traffic <metrics.csv> [skip]
       per kernel: mean DRAM bytes (read + write) per launch, over its launches
-      after the first `skip` of that kernel (JSON, the form bench.py reads
-      from profiles/pull_traffic.json)
+      after the first `skip` of that kernel (JSON; `bench.py --write-traffic`
+      turns such captures into profiles/pull_traffic.json)
 """
 from __future__ import annotations
 
@@ -77,10 +77,9 @@ def main(argv):
         for k, v in res.items():
             print(f"| `{k}` | {v['launches']} | {v['total_ms']:.3f} | {v['share']:.3f} |")
         return 0
-    if len(argv) >= 4 and argv[0] == "traffic":
-        res = traffic(argv[1], int(argv[4]) if len(argv) > 4 else 0)
-        print(json.dumps({"workload": argv[2], "kernel_hash": argv[3],
-                          "bytes_per_launch": res}, indent=1))
+    if len(argv) >= 2 and argv[0] == "traffic":
+        res = traffic(argv[1], int(argv[2]) if len(argv) > 2 else 0)
+        print(json.dumps(res, indent=1))
         return 0
     print(__doc__)
     return 2
