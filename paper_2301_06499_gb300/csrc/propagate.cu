@@ -257,102 +257,102 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       if (gained && atomicAdd(p.rowbits + vl, gained) + gained == (uint32_t)s) set_bit(p.Sat, vl);
     }
   } else {
-  for (int64_t base = warp * 32; base < nF; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    const bool valid = i < nF;
-    const int32_t v = valid ? F[i] : 0;
-    uint64_t *xr = p.X + (size_t)v * Wp;
-    const uint64_t *yr = p.Y + (size_t)v * Wp;
-    uint64_t *dr = Dcur + (size_t)v * Wp;
-    // a batch of disjoint graphs: bit i of a node is its own graph's seed i
-    int sv = s, c0v = 0, gid = -1;
-    if (p.node_graph && valid) {
-      gid = p.node_graph[v];
-      sv = p.graph_s[gid];
-      c0v = p.graph_col0[gid];
-    }
-    const int gid0 = __shfl_sync(kFullMask, gid, 0);
-    const bool one_graph = !p.node_graph || __all_sync(kFullMask, !valid || gid == gid0);
-    const int c0w = __shfl_sync(kFullMask, c0v, 0);
-    if (!one_graph) {
-      // rows of several graphs in this warp: count each graph's lanes apart
-      // (the rows are not yet synced, so X ^ Y is still the delta)
-      unsigned todo = __ballot_sync(kFullMask, valid);
-      while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int gl = __shfl_sync(kFullMask, gid, leader);
-        const int cg = __shfl_sync(kFullMask, c0v, leader);
-        const bool mine = valid && gid == gl;
-        todo &= ~__ballot_sync(kFullMask, mine);
+    for (int64_t base = warp * 32; base < nF; base += nwarps * 32) {
+      const int64_t i = base + lane;
+      const bool valid = i < nF;
+      const int32_t v = valid ? F[i] : 0;
+      uint64_t *xr = p.X + (size_t)v * Wp;
+      const uint64_t *yr = p.Y + (size_t)v * Wp;
+      uint64_t *dr = Dcur + (size_t)v * Wp;
+      // a batch of disjoint graphs: bit i of a node is its own graph's seed i
+      int sv = s, c0v = 0, gid = -1;
+      if (p.node_graph && valid) {
+        gid = p.node_graph[v];
+        sv = p.graph_s[gid];
+        c0v = p.graph_col0[gid];
+      }
+      const int gid0 = __shfl_sync(kFullMask, gid, 0);
+      const bool one_graph = !p.node_graph || __all_sync(kFullMask, !valid || gid == gid0);
+      const int c0w = __shfl_sync(kFullMask, c0v, 0);
+      if (!one_graph) {
+        // rows of several graphs in this warp: count each graph's lanes apart
+        // (the rows are not yet synced, so X ^ Y is still the delta)
+        unsigned todo = __ballot_sync(kFullMask, valid);
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int gl = __shfl_sync(kFullMask, gid, leader);
+          const int cg = __shfl_sync(kFullMask, c0v, leader);
+          const bool mine = valid && gid == gl;
+          todo &= ~__ballot_sync(kFullMask, mine);
+          for (int w = 0; w < Wp; ++w) {
+            const uint64_t d =
+                mine ? (xr[w] ^ __ldg(reinterpret_cast<const unsigned long long *>(yr) + w)) : 0ULL;
+            if (__any_sync(kFullMask, d != 0ULL)) {
+              const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
+              const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
+              const int c0 = cg + w * 64 + lane;
+              if (n0) atomicAdd(&cdst[c0], n0);
+              if (n1) atomicAdd(&cdst[c0 + 32], n1);
+            }
+          }
+        }
+      }
+      bool full = valid;
+      if ((Wp & 3) == 0) {  // 32-byte aligned rows: a row's 4 words per load
+        for (int w = 0; w < Wp; w += 4) {
+          uint64_t o[4] = {0ULL, 0ULL, 0ULL, 0ULL}, nw[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+          if (valid) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(xr + w);
+            const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(xr + w + 2);
+            o[0] = a.x;
+            o[1] = a.y;
+            o[2] = b.x;
+            o[3] = b.y;
+            ld_nc_256(nw, yr + w);
+          }
+          uint64_t d[4];
+  #pragma unroll
+          for (int k = 0; k < 4; ++k) d[k] = o[k] ^ nw[k];
+          if ((d[0] | d[1] | d[2] | d[3]) != 0ULL) {  // the deltas were zero before
+            store_words<4>(xr + w, nw);
+            store_words<4>(dr + w, d);
+          }
+  #pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            full = full && ((nw[k] | ~valid_mask(w + k, sv)) == ~0ULL);
+            if (one_graph && __any_sync(kFullMask, d[k] != 0ULL)) {
+              const uint32_t n0 = __popc(transpose32((uint32_t)d[k], lane));
+              const uint32_t n1 = __popc(transpose32((uint32_t)(d[k] >> 32), lane));
+              const int c0 = c0w + (w + k) * 64 + lane;
+              if (n0) atomicAdd(&cdst[c0], n0);
+              if (n1) atomicAdd(&cdst[c0 + 32], n1);
+            }
+          }
+        }
+      } else {
         for (int w = 0; w < Wp; ++w) {
-          const uint64_t d =
-              mine ? (xr[w] ^ __ldg(reinterpret_cast<const unsigned long long *>(yr) + w)) : 0ULL;
-          if (__any_sync(kFullMask, d != 0ULL)) {
+          uint64_t o = 0, nw = 0;
+          if (valid) {
+            o = xr[w];
+            nw = __ldg(reinterpret_cast<const unsigned long long *>(yr) + w);
+          }
+          const uint64_t d = o ^ nw;
+          if (d) {
+            xr[w] = nw;
+            dr[w] = d;
+          }
+          full = full && ((nw | ~valid_mask(w, sv)) == ~0ULL);
+          if (one_graph && __any_sync(kFullMask, d != 0ULL)) {
             const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
             const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
-            const int c0 = cg + w * 64 + lane;
+            const int c0 = c0w + w * 64 + lane;
             if (n0) atomicAdd(&cdst[c0], n0);
             if (n1) atomicAdd(&cdst[c0 + 32], n1);
           }
         }
       }
+      if (full) set_bit(p.Sat, v);
     }
-    bool full = valid;
-    if ((Wp & 3) == 0) {  // 32-byte aligned rows: a row's 4 words per load
-      for (int w = 0; w < Wp; w += 4) {
-        uint64_t o[4] = {0ULL, 0ULL, 0ULL, 0ULL}, nw[4] = {0ULL, 0ULL, 0ULL, 0ULL};
-        if (valid) {
-          const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(xr + w);
-          const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(xr + w + 2);
-          o[0] = a.x;
-          o[1] = a.y;
-          o[2] = b.x;
-          o[3] = b.y;
-          ld_nc_256(nw, yr + w);
-        }
-        uint64_t d[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = o[k] ^ nw[k];
-        if ((d[0] | d[1] | d[2] | d[3]) != 0ULL) {  // the deltas were zero before
-          store_words<4>(xr + w, nw);
-          store_words<4>(dr + w, d);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          full = full && ((nw[k] | ~valid_mask(w + k, sv)) == ~0ULL);
-          if (one_graph && __any_sync(kFullMask, d[k] != 0ULL)) {
-            const uint32_t n0 = __popc(transpose32((uint32_t)d[k], lane));
-            const uint32_t n1 = __popc(transpose32((uint32_t)(d[k] >> 32), lane));
-            const int c0 = c0w + (w + k) * 64 + lane;
-            if (n0) atomicAdd(&cdst[c0], n0);
-            if (n1) atomicAdd(&cdst[c0 + 32], n1);
-          }
-        }
-      }
-    } else {
-    for (int w = 0; w < Wp; ++w) {
-      uint64_t o = 0, nw = 0;
-      if (valid) {
-        o = xr[w];
-        nw = __ldg(reinterpret_cast<const unsigned long long *>(yr) + w);
-      }
-      const uint64_t d = o ^ nw;
-      if (d) {
-        xr[w] = nw;
-        dr[w] = d;
-      }
-      full = full && ((nw | ~valid_mask(w, sv)) == ~0ULL);
-      if (one_graph && __any_sync(kFullMask, d != 0ULL)) {
-        const uint32_t n0 = __popc(transpose32((uint32_t)d, lane));
-        const uint32_t n1 = __popc(transpose32((uint32_t)(d >> 32), lane));
-        const int c0 = c0w + w * 64 + lane;
-        if (n0) atomicAdd(&cdst[c0], n0);
-        if (n1) atomicAdd(&cdst[c0 + 32], n1);
-      }
-    }
-    }
-    if (full) set_bit(p.Sat, v);
-  }
   }
   // the deltas of round t-1 were read by the pull of round t: clear them
   if constexpr (WIDE) {  // a warp per row, 16 bytes a lane
