@@ -861,7 +861,7 @@ def profile_run(args):
     print(json.dumps({"workload": args.workload, "options": pg.options_dict(o), "calls": calls}))
 
 
-def write_traffic(workload: str, csvs: list) -> None:
+def write_traffic(workload: str, csvs: list, out_path: str | None = None) -> dict:
     """profiles/pull_traffic.json from ncu CSV captures of the pull kernels
     (dram__bytes_read.sum and dram__bytes_write.sum): mean bytes per launch
     of each kernel, with the hash of the sources it was built from."""
@@ -884,9 +884,10 @@ def write_traffic(workload: str, csvs: list) -> None:
                    "launches of the call the bench times (NVTX range bench_call), with the "
                    "autotuned schedule; a kernel's figure applies while the hash of its "
                    "sources (common.cuh, kernels.cuh and its pull_*.cu) is unchanged"}
-    with open(os.path.join(ROOT, "profiles", "pull_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "pull_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(per))
+    return out
 
 
 def main():
