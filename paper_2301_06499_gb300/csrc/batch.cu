@@ -15,7 +15,7 @@
 #include <mutex>
 #include <vector>
 
-#include "common.cuh"
+#include "host.cuh"
 
 struct pg_batch {
   struct Item {

@@ -5,7 +5,7 @@
 
 #include <vector>
 
-#include "common.cuh"
+#include "host.cuh"
 
 namespace pg {
 
@@ -468,11 +468,54 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
   return rc;
 }
 
+// The workspace's buffers in arena order.
+static std::vector<DevBuf *> workspace_parts(Workspace &w) {
+  return {&w.X,  &w.Y,  &w.D0,     &w.D1, &w.C0,   &w.C1,   &w.K0,    &w.K1,
+          &w.Sat, &w.RB, &w.KW0,   &w.KW1, &w.F0,  &w.F1,   &w.E,     &w.A,
+          &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum, &w.gthr};
+}
+
+pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, size_t>> &needs) {
+  constexpr size_t kAlign = 256;
+  bool fits = w.arena.p != nullptr;
+  for (const auto &nd : needs)
+    if (!nd.first->p || nd.first->bytes < std::max<size_t>(nd.second, 16)) fits = false;
+  if (fits) return PG_OK;
+  std::vector<DevBuf *> parts = workspace_parts(w);
+  std::vector<size_t> cap(parts.size());
+  for (size_t i = 0; i < parts.size(); ++i) cap[i] = parts[i]->p ? parts[i]->bytes : 0;
+  for (const auto &nd : needs) {
+    const size_t want = std::max<size_t>(nd.second, 16);
+    size_t i = 0;
+    while (i < parts.size() && parts[i] != nd.first) ++i;
+    if (i == parts.size()) return PG_EINVAL;  // not a buffer of this workspace
+    cap[i] = std::max(cap[i], want);
+  }
+  size_t total = 0;
+  for (size_t c : cap) total += (c + kAlign - 1) / kAlign * kAlign;
+  for (DevBuf *b : parts) {  // the old layout is void from here on
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+  pg_status rc = ensure(w.arena, total);
+  if (rc) return rc;
+  char *base = (char *)w.arena.p;
+  size_t off = 0;
+  for (size_t i = 0; i < parts.size(); ++i) {
+    if (!cap[i]) continue;
+    parts[i]->p = base + off;
+    parts[i]->bytes = cap[i];
+    off += (cap[i] + kAlign - 1) / kAlign * kAlign;
+  }
+  return PG_OK;
+}
+
 void release_workspace(Workspace &w) {
-  for (DevBuf *b : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB, &w.KW0, &w.KW1, &w.F0,
-                    &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum,
-                    &w.gthr})
-    release(*b);
+  release(w.arena);
+  for (DevBuf *b : workspace_parts(w)) {  // they pointed into the arena
+    b->p = nullptr;
+    b->bytes = 0;
+  }
   if (w.ctrl_h) cudaFreeHost(w.ctrl_h);
   w.ctrl_h = nullptr;
   for (auto &e : w.ev)
@@ -483,14 +526,7 @@ void release_workspace(Workspace &w) {
   w.tev.clear();
 }
 
-int64_t workspace_held(const Workspace &w) {
-  int64_t b = 0;
-  for (const DevBuf *x : {&w.X, &w.Y, &w.D0, &w.D1, &w.C0, &w.C1, &w.K0, &w.K1, &w.Sat, &w.RB, &w.KW0, &w.KW1,
-                          &w.F0, &w.F1, &w.E, &w.A, &w.counts, &w.rs, &w.ctrl, &w.seeds,
-                          &w.seed_bits, &w.gfsum, &w.gthr})
-    b += (int64_t)x->bytes;
-  return b;
-}
+int64_t workspace_held(const Workspace &w) { return (int64_t)w.arena.bytes; }
 
 // K copies of a CSR side by side: copy k's rows are k*n.., its arcs k*m..,
 // its column indices shifted by k*n.

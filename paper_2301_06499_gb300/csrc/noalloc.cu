@@ -23,7 +23,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "common.cuh"
+#include "host.cuh"
 
 namespace pg {
 namespace {

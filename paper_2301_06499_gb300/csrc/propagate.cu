@@ -7,6 +7,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host.cuh"
 #include "kernels.cuh"
 
 namespace pg {
@@ -849,28 +850,30 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   const int64_t nbm = (n + 31) / 32;
   const int32_t row_cap = cl.row_cap;
   const int64_t e_cap = n + g->m / kExpandArcs + 1;
-  size_t sig_bytes = sizeof(uint64_t) * (size_t)n * pl.Wp;
-  if ((rc = ensure(w.X, sig_bytes)) || (rc = ensure(w.Y, sig_bytes)) ||
-      (rc = ensure(w.D0, sig_bytes)) || (rc = ensure(w.D1, sig_bytes)))
-    return rc;
-  for (DevBuf *b : {&w.C0, &w.C1, &w.K0, &w.K1, &w.Sat})
-    if ((rc = ensure(*b, sizeof(uint32_t) * nbm))) return rc;
+  const size_t sig_bytes = sizeof(uint64_t) * (size_t)n * pl.Wp;
+  const size_t bm_bytes = sizeof(uint32_t) * (size_t)nbm;
   pl.post_wide = !bs && pl.Wp >= kWidePostWords;
-  if (pl.post_wide && (rc = ensure(w.RB, sizeof(uint32_t) * n))) return rc;
-  if (pw && ((rc = ensure(w.KW0, sizeof(uint32_t) * nbm * pl.Wp)) ||
-             (rc = ensure(w.KW1, sizeof(uint32_t) * nbm * pl.Wp))))
-    return rc;
-  if ((rc = ensure(w.F0, sizeof(int32_t) * n)) || (rc = ensure(w.F1, sizeof(int32_t) * n)) ||
-      (rc = ensure(w.E, sizeof(unsigned long long) * e_cap)) ||
-      (rc = ensure(w.A, sizeof(ulonglong2) * std::max<int64_t>(g->pieces.count, 1))) ||
-      (rc = ensure(w.counts, sizeof(uint32_t) * (size_t)row_cap * ncols)) ||
-      (rc = ensure(w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2))) ||
-      (rc = ensure(w.ctrl, sizeof(Ctrl))) || (rc = ensure(w.seeds, sizeof(int32_t) * sp)) ||
-      (bs && (rc = ensure(w.seed_bits, sizeof(int32_t) * sp))) ||
-      (bs && g->nseg > 0 &&
-       ((rc = ensure(w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg)) ||
-        (rc = ensure(w.gthr, sizeof(unsigned long long) * (size_t)g->nseg)))))
-    return rc;
+  std::vector<std::pair<DevBuf *, size_t>> needs = {
+      {&w.X, sig_bytes}, {&w.Y, sig_bytes}, {&w.D0, sig_bytes}, {&w.D1, sig_bytes},
+      {&w.C0, bm_bytes}, {&w.C1, bm_bytes}, {&w.K0, bm_bytes}, {&w.K1, bm_bytes},
+      {&w.Sat, bm_bytes},
+      {&w.F0, sizeof(int32_t) * (size_t)n}, {&w.F1, sizeof(int32_t) * (size_t)n},
+      {&w.E, sizeof(unsigned long long) * (size_t)e_cap},
+      {&w.A, sizeof(ulonglong2) * (size_t)std::max<int64_t>(g->pieces.count, 1)},
+      {&w.counts, sizeof(uint32_t) * (size_t)row_cap * (size_t)ncols},
+      {&w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2)},
+      {&w.ctrl, sizeof(Ctrl)}, {&w.seeds, sizeof(int32_t) * (size_t)sp}};
+  if (pl.post_wide) needs.push_back({&w.RB, sizeof(uint32_t) * (size_t)n});
+  if (pw) {
+    needs.push_back({&w.KW0, bm_bytes * (size_t)pl.Wp});
+    needs.push_back({&w.KW1, bm_bytes * (size_t)pl.Wp});
+  }
+  if (bs) needs.push_back({&w.seed_bits, sizeof(int32_t) * (size_t)sp});
+  if (bs && g->nseg > 0) {
+    needs.push_back({&w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg});
+    needs.push_back({&w.gthr, sizeof(unsigned long long) * (size_t)g->nseg});
+  }
+  if ((rc = carve_workspace(w, needs))) return rc;
   if (!w.ctrl_h) {
     if (cudaMallocHost((void **)&w.ctrl_h, 2 * sizeof(Ctrl)) != cudaSuccess) {
       w.ctrl_h = nullptr;

@@ -32,7 +32,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "common.cuh"
+#include "host.cuh"
 
 namespace {
 

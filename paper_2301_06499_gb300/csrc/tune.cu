@@ -8,7 +8,7 @@
 #include <cstring>
 #include <vector>
 
-#include "common.cuh"
+#include "host.cuh"
 
 namespace pg {
 
