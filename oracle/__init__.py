@@ -72,7 +72,7 @@ def _load():
             lib.or_m_active.restype = ctypes.c_int
             lib.or_m_active.argtypes = [i64, vp, vp, vp, i64, i64, vp, ctypes.c_int]
             lib.or_propagate_p.restype = ctypes.c_int
-            lib.or_propagate_p.argtypes = [i64, vp, vp, vp, i64, i64, vp, vp, ctypes.c_int]
+            lib.or_propagate_p.argtypes = [i64, vp, vp, vp, i64, i64, vp, vp, vp, ctypes.c_int]
             lib.or_metrics.restype = ctypes.c_int
             lib.or_metrics.argtypes = [vp, i64, i64, i64, i64, i64,
                                        ctypes.POINTER(MetricsOut)]
@@ -149,19 +149,26 @@ def m_active(g, dmat: np.ndarray, rounds: int, threads: int = 0) -> np.ndarray:
     return out
 
 
-def propagate_p(g, seeds, cap: int | None = None, threads: int = 0):
+def propagate_p(g, seeds, cap: int | None = None, threads: int = 0,
+                with_m_active: bool = False):
     """Alg. 1 on the host: returns (counts uint32[T+1, s], T), counts[t, i] =
-    the nodes seed i's bit reached in round t (its nodes at distance t)."""
+    the nodes seed i's bit reached in round t (its nodes at distance t), and
+    with ``with_m_active`` also m_active uint64[T+2] as the sweeps find it."""
     n, rp, col = _csr(g)
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     s = seeds.size
     cap = int(cap if cap is not None else n)
     counts = np.zeros((cap + 1, s), dtype=np.uint32)
+    mact = np.zeros(cap + 2, dtype=np.uint64)
     T = ctypes.c_int32(0)
     _check(_load().or_propagate_p(n, rp.ctypes.data, col.ctypes.data, seeds.ctypes.data, s, cap,
-                                  counts.ctypes.data, ctypes.byref(T), _threads(threads)),
+                                  counts.ctypes.data, ctypes.byref(T), mact.ctypes.data,
+                                  _threads(threads)),
            "propagate_p")
-    return np.ascontiguousarray(counts[:T.value + 1]), int(T.value)
+    out = (np.ascontiguousarray(counts[:T.value + 1]), int(T.value))
+    if with_m_active:
+        return out + (np.ascontiguousarray(mact[:T.value + 2]),)
+    return out
 
 
 def metrics(hist: np.ndarray, n: int, tau_num: int = 9, tau_den: int = 10) -> dict:

@@ -451,7 +451,10 @@ int or_metrics(const int64_t *hist, int64_t s, int64_t cap, int64_t n, int64_t t
  * Sig = Sig_next). The bits a node gains in round t are the seeds at
  * distance exactly t (Sec. 4, paragraph on collisions), counted per seed.
  * The rounds stop when a round gains nothing; T is the last round that
- * gained a bit.
+ * gained a bit. Along the way each round's m_active is the in-degree sum of
+ * the nodes the round revisits: those still missing a bit with an
+ * in-neighbour that gained one in the previous round (a seed gains its own
+ * bit in round 0), the skip rule of the proof of Thm. 1 taken literally.
  */
 typedef struct {
   int64_t n;
@@ -462,7 +465,10 @@ typedef struct {
   uint64_t last_mask; /* valid bits of word W-1 */
   const uint64_t *sig;
   uint64_t *nxt;
-  uint32_t *cnt; /* [workers][s] */
+  const unsigned char *chg; /* node gained a bit in the previous round */
+  unsigned char *chg_next;  /* ... in this round */
+  uint32_t *cnt;            /* [workers][s] */
+  uint64_t *mact;           /* [workers] */
   int64_t block;
 } or_pp_ctx;
 
@@ -480,13 +486,18 @@ static void or_pp_item(void *p, int64_t item, int w) {
       nv[k] = sv[k];
       full = full && sv[k] == (k == W - 1 ? c->last_mask : ~0ULL);
     }
+    c->chg_next[v] = 0;
     if (full) continue;
+    int active = 0;
     for (int64_t j = c->rp[v]; j < c->rp[v + 1]; ++j) {
       const uint64_t *su = c->sig + (size_t)c->col[j] * W;
       for (int k = 0; k < W; ++k) nv[k] |= su[k];
+      active = active || c->chg[c->col[j]];
     }
+    if (active) c->mact[w] += (uint64_t)(c->rp[v + 1] - c->rp[v]);
     for (int k = 0; k < W; ++k) {
       uint64_t d = nv[k] ^ sv[k];
+      if (d) c->chg_next[v] = 1;
       while (d) {
         cnt[k * 64 + __builtin_ctzll(d)] += 1;
         d &= d - 1;
@@ -497,11 +508,14 @@ static void or_pp_item(void *p, int64_t item, int w) {
 
 /*
  * counts: [cap+1][s] uint32, row t = per-seed nodes at distance exactly t
- * (row 0 = 1 for every seed); *rounds = T. OR_ERANGE when a round beyond
- * cap still gains bits. Seeds must be distinct and in range.
+ * (row 0 = 1 for every seed); *rounds = T; m_active (may be NULL):
+ * [cap+2] uint64, entries 0..T+1 written (entry T+1 is the final sweep that
+ * gains nothing). OR_ERANGE when a round beyond cap still gains bits. Seeds
+ * must be distinct and in range.
  */
 int or_propagate_p(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *seeds,
-                   int64_t s, int64_t cap, uint32_t *counts, int32_t *rounds, int threads) {
+                   int64_t s, int64_t cap, uint32_t *counts, int32_t *rounds, uint64_t *m_active,
+                   int threads) {
   int rc = or_check_csr(n, row_ptr, col);
   if (rc) return rc;
   if (!seeds || s < 1 || s > n || cap < 0 || !counts || !rounds) return OR_EINVAL;
@@ -510,30 +524,31 @@ int or_propagate_p(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
   uint64_t *sig = (uint64_t *)calloc((size_t)n * W, sizeof(uint64_t));
   uint64_t *nxt = (uint64_t *)calloc((size_t)n * W, sizeof(uint64_t));
   uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)threads * (size_t)s);
-  if (!sig || !nxt || !cnt) {
-    free(sig);
-    free(nxt);
-    free(cnt);
-    return OR_ENOMEM;
-  }
-  unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
-  int bad = !seen;
+  uint64_t *mact = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)threads);
+  unsigned char *chg = (unsigned char *)calloc((size_t)n, 1);
+  unsigned char *chg_next = (unsigned char *)calloc((size_t)n, 1);
+  int bad = !sig || !nxt || !cnt || !mact || !chg || !chg_next;
+  if (bad) rc = OR_ENOMEM;
   for (int64_t i = 0; !bad && i < s; ++i) {
     const int32_t x = seeds[i];
-    bad = x < 0 || x >= n || seen[x];
+    bad = x < 0 || x >= n || chg[x]; /* chg marks the seeds met so far */
+    if (bad) rc = OR_EINVAL;
     if (!bad) {
-      seen[x] = 1;
+      chg[x] = 1; /* a seed gains its own bit in round 0 */
       sig[(size_t)x * W + (size_t)(i / 64)] |= 1ULL << (i % 64);
       counts[i] = 1;
     }
   }
-  free(seen);
   if (bad) {
     free(sig);
     free(nxt);
     free(cnt);
-    return OR_EINVAL;
+    free(mact);
+    free(chg);
+    free(chg_next);
+    return rc;
   }
+  if (m_active) m_active[0] = 0;
   or_pp_ctx c;
   c.n = n;
   c.rp = row_ptr;
@@ -542,25 +557,34 @@ int or_propagate_p(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
   c.s = s;
   c.last_mask = (s % 64) ? ((1ULL << (s % 64)) - 1ULL) : ~0ULL;
   c.cnt = cnt;
+  c.mact = mact;
   c.block = 4096;
   const int64_t items = (n + c.block - 1) / c.block;
   int32_t T = 0;
   for (int64_t t = 1;; ++t) {
     memset(cnt, 0, sizeof(uint32_t) * (size_t)threads * (size_t)s);
+    memset(mact, 0, sizeof(uint64_t) * (size_t)threads);
     c.sig = sig;
     c.nxt = nxt;
+    c.chg = chg;
+    c.chg_next = chg_next;
     rc = or_parallel(items, threads, or_pp_item, &c);
     if (rc) break;
-    uint64_t total = 0;
+    uint64_t total = 0, ma = 0;
     for (int64_t i = 0; i < s; ++i) {
       uint32_t a = 0;
       for (int k = 0; k < threads; ++k) a += cnt[(size_t)k * (size_t)s + (size_t)i];
       total += a;
       if (t <= cap) counts[(size_t)t * (size_t)s + (size_t)i] = a;
     }
+    for (int k = 0; k < threads; ++k) ma += mact[k];
+    if (m_active && t <= cap + 1) m_active[t] = ma;
     uint64_t *tmp = sig; /* Sig = Sig_next */
     sig = nxt;
     nxt = tmp;
+    unsigned char *tc = chg;
+    chg = chg_next;
+    chg_next = tc;
     if (total == 0) break;
     if (t > cap) {
       rc = OR_ERANGE;
@@ -571,6 +595,9 @@ int or_propagate_p(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
   free(sig);
   free(nxt);
   free(cnt);
+  free(mact);
+  free(chg);
+  free(chg_next);
   if (rc) return rc;
   *rounds = T;
   return OR_OK;

@@ -275,10 +275,13 @@ def test_host_alg1_equals_bfs(kind, s):
          "path": lambda: I.path(60, directed=True),
          "iso": lambda: I.from_arcs(100, [0, 1, 5], [1, 2, 6])}[kind]()
     seeds = I.seeds(g.n, min(s, g.n), 74)
-    counts, T = oracle.propagate_p(g, seeds)
+    counts, T, mact = oracle.propagate_p(g, seeds, with_m_active=True)
     want = oracle.run(g, seeds)
     assert T == want["rounds"]
     assert np.array_equal(counts, want["counts"])
+    # m_active as the sweeps find it (changed flags, saturation) equals the
+    # one restated from BFS distances
+    assert np.array_equal(mact, want["m_active"])
 
 
 def test_host_alg1_path_closed_form_and_errors():
