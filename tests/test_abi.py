@@ -83,3 +83,40 @@ def test_pg_metrics_p4_worked_example():
     assert m["eff_diameter"] == 3 and m["diameter"] == 3
     assert m["eff_diameter_interp"] == pytest.approx(2.2, rel=1e-14)
     assert m["reachable_pairs"] == 16.0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror in _abi.py has the C header's size and field
+    offsets (compiled with the host C compiler against include/propagate.h),
+    so no field of the boundary is read at the wrong place."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = {"pg_options": _abi.Options, "pg_counts": _abi.Counts,
+             "pg_metrics_out": _abi.MetricsOut, "pg_stats": _abi.Stats,
+             "pg_tune_report": _abi.TuneReport, "pg_batch_stats": _abi.BatchStats,
+             "pg_server_config": _abi.ServerConfig, "pg_request_info": _abi.RequestInfo,
+             "pg_server_stats": _abi.ServerStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "propagate.h"',
+             "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, cls in pairs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
