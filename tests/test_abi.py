@@ -120,3 +120,29 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_argument_checks_before_any_device_work():
+    """Bad arguments are refused with PG_EINVAL before the device is touched,
+    and without a GPU a valid graph is refused with PG_ECUDA: the library has
+    no host fallback for the propagation."""
+    L = _abi.lib()
+    out = ctypes.c_void_p()
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    assert L.pg_graph_from_csr(None, None, 10, 0, 1, 0, None, ctypes.byref(out)) == _abi.PG_EINVAL
+    assert L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, 0, 2, 1, 0, None,
+                               ctypes.byref(out)) == _abi.PG_EINVAL
+    assert L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, 2, -1, 1, 0, None,
+                               ctypes.byref(out)) == _abi.PG_EINVAL
+    c = _abi.Counts(s=1, max_rounds=0, rounds=0, reserved=0, counts=None, m_active=None)
+    assert L.pg_propagate_p(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
+    assert L.pg_propagate_s(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
+    assert L.pg_batch_create(None) == _abi.PG_EINVAL
+    assert L.pg_server_create(None, None) == _abi.PG_EINVAL
+    assert L.pg_autotune(None, None, 1, 0, 1, None, None, None) == _abi.PG_EINVAL
+    import torch
+    if not torch.cuda.is_available():
+        rc = L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, 2, 2, 1, 0, None,
+                                 ctypes.byref(out))
+        assert rc == _abi.PG_ECUDA
