@@ -181,11 +181,13 @@ def metrics(hist: np.ndarray, n: int, tau_num: int = 9, tau_den: int = 10) -> di
     return {f: getattr(out, f) for f, _ in MetricsOut._fields_}
 
 
-def run(g, seeds, threads: int = 0, tau=(9, 10), with_m_active: bool = True) -> dict:
+def run(g, seeds, threads: int = 0, tau=(9, 10), with_m_active: bool = True,
+        with_distances: bool = False) -> dict:
     """Everything the GPU path returns, for one graph and seed set:
     counts (uint32[T+1, s], row t = per-seed new nodes at hop t), rounds T,
-    m_active (uint64[T+2], the final empty sweep included) and metrics."""
-    if with_m_active:
+    m_active (uint64[T+2], the final empty sweep included) and metrics; with
+    ``with_distances`` also "dmat", the node-major distances int32[n, s]."""
+    if with_m_active or with_distances:
         hist, ecc, dmat = seed_histograms(g, seeds, threads=threads, with_distances=True)
     else:
         hist, ecc = seed_histograms(g, seeds, threads=threads)
@@ -197,5 +199,6 @@ def run(g, seeds, threads: int = 0, tau=(9, 10), with_m_active: bool = True) -> 
     }
     if with_m_active:
         res["m_active"] = m_active(g, dmat, T + 1, threads=threads)
-        del dmat
+    if with_distances:
+        res["dmat"] = dmat
     return res

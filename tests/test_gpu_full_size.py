@@ -30,17 +30,30 @@ def _metrics_close(res, want, n):
         assert got[k] == pytest.approx(want[k], rel=1e-12, abs=0.0), k
 
 
+def _passes_m_active(g, dmat, rounds, planes=64):
+    """PROPAGATE-S's m_active: each pass's own (its seed block's distances),
+    summed over the passes."""
+    total = np.zeros(rounds + 2, dtype=np.uint64)
+    for b in range(0, dmat.shape[1], planes):
+        sub = np.ascontiguousarray(dmat[:, b:b + planes])
+        part = oracle.m_active(g, sub, int(sub.max()) + 1)
+        total[:part.size] += part
+    return total
+
+
 def test_benchmark_workload_rmat22_directed_s256():
     g = I.rmat(22, 16, 2, directed=True)
     seeds = I.seeds(g.n, 256, 2)
-    want = oracle.run(g, seeds)
+    want = oracle.run(g, seeds, with_distances=True)
+    mact_s = _passes_m_active(g, want.pop("dmat"), want["rounds"])
     G = pg.Graph.from_inputs(g)
     res_timed = pg.propagate_p(G, seeds, opts=pg.options(timing=1))  # bench's timed region
     _same(res_timed, want)
     _metrics_close(res_timed, want["metrics"], g.n)
     _same(pg.propagate_p(G, seeds), want)  # CUDA-graph loop
-    res_s = pg.propagate_s(G, seeds, opts=pg.options(timing=1))
+    res_s = pg.propagate_s(G, seeds, opts=pg.options(timing=1))  # 4 passes as words
     _same(res_s, want, mact=False)
+    assert np.array_equal(res_s.m_active, mact_s)  # each pass's own m_active, summed
     assert res_s.seed_edge_traversals > 0
 
 
