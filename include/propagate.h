@@ -245,12 +245,18 @@ pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts
 /*
  * PROPAGATE-S (Algorithm 2, Sec. 4.2): seeds are processed in passes of
  * planes_per_pass independent 1-bit planes (plane k of a node is bit k of its
- * word); in each round only nodes with an unset plane pull, and a node stops
- * scanning its in-neighbours as soon as all its planes are set (with one
- * plane per pass: at the first set in-neighbour, as in Algorithm 2). The
- * counts are per seed and identical to PROPAGATE-P's (Sec. 5, "both
- * algorithms produce the same results"). Arguments and errors as
- * pg_propagate_p; m_active is summed over passes.
+ * word); in each round only nodes with an unset plane pull, and a node whose
+ * planes are all set is not scanned again (Algorithm 2's break at the first
+ * set in-neighbour, with one plane per pass, becomes this skip when a node's
+ * in-neighbours are read in parallel pieces). Passes are independent: by
+ * default they run side by side, as the words of one signature over the
+ * graph (pg_options.pass_words) or on copies of it (passes_together), each
+ * pass keeping its own counts, rounds and m_active; pass_words = 1 with
+ * passes_together = 1 runs them one after another, Algorithm 2's schedule
+ * and memory footprint. The counts are per seed and identical to
+ * PROPAGATE-P's (Sec. 5, both algorithms give the same results). Arguments
+ * and errors as pg_propagate_p; m_active is each pass's own, summed over
+ * the passes.
  */
 pg_status pg_propagate_s(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,
                          const pg_options *opt, void *stream);
