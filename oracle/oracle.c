@@ -201,8 +201,9 @@ static void or_hist_item(void *p, int64_t i, int w) {
 /*
  * Per-seed distance histograms: hist[i*cap + d] = |{v : d(seeds[i], v) = d}|
  * for d < cap, and ecc[i] = max finite distance from seeds[i]. These are the
- * exact per-seed, per-round collision counts of PROPAGATE (Sec. 4, Alg. 1
- * line "Count += ||Sig_next(u) XOR Sig(u)||" restricted to seed i).
+ * exact per-seed, per-round collision counts of PROPAGATE (Sec. 4, Alg. 1:
+ * the round's count adds, over all nodes, the popcount of the XOR of the new
+ * and the old signature; here restricted to bit i, seed i's).
  * dmat, if not NULL, receives the node-major distance matrix
  * dmat[v*s + i] = d(seeds[i], v) (-1 if unreachable).
  * Returns OR_ERANGE if some distance is >= cap (hist then holds the prefix).
