@@ -1,7 +1,7 @@
-// PROPAGATE-P and PROPAGATE-S drivers: seed initialisation (Alg. 1 lines
-// setting Sig(x_i)[i] = 1; Alg. 2 per-seed plane set-up), the post kernel of
-// every round (collision count, buffer sync, next work list, fixpoint test)
-// and the host round loop.
+// PROPAGATE-P and PROPAGATE-S drivers: seed initialisation (Alg. 1's start,
+// seed i's bit set on its own node; Alg. 2's per-seed plane set-up), the post
+// kernel of every round (collision count, buffer sync, next work list,
+// fixpoint test) and the host round loop.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
