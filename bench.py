@@ -6,10 +6,13 @@ metrics from the counts. Work per step is the method-defined seed-edge
 traversal count: each of the two runs solves the problem whose work is
 sum_t s * m_active(t) (m_active from the PROPAGATE-P run).
 
-Default workload: directed R-MAT, scale 22 (4,194,304 nodes), edge factor 16,
-(a, b, c, d) = (.57, .19, .19, .05), RNG seed 2, duplicates removed, CSR over
-in-edges; s = 256 seeds (4 words per node), uniform without replacement (RNG
-seed 2). --workload selects the other shapes (see WORKLOADS).
+Default workload: undirected R-MAT, scale 26 (67,108,864 nodes), edge factor
+16, (a, b, c, d) = (.57, .19, .19, .05), RNG seed 2, symmetrised, duplicates
+removed (~2.1 B arcs, int64 row pointers); s = 512 seeds (8 words, 64 bytes
+per node), uniform without replacement (RNG seed 2): the stand-in for the
+paper's largest in-memory graphs (Sec. 5, Table 1). --workload selects the
+other shapes (see WORKLOADS), e.g. the directed R-MAT of scale 22 with
+s = 256 (rmat22_directed_s256).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -191,6 +194,19 @@ def pull_bytes(st: dict) -> float:
             + st["rows_gathered"] * w + st["changed_rows"] * w)
 
 
+def round_bytes(st: dict, s: int, s_mode: bool) -> float:
+    """Algorithmic bytes of a call's rounds by the method's own work counts:
+    per active row (|A_t|, the rows a round revisits) 8 B of row bounds plus
+    its signature read and written (2 s/8 B); per active in-arc (m_active(t))
+    a 4 B column index plus the neighbour's s/8 B signature; per changed row
+    (|F_t|) a 4 B frontier entry. PROPAGATE-S works in passes of 64 one-bit
+    planes, so its unit signature is 64 bits (8 B) and its active rows and
+    arcs are counted per pass."""
+    sb = min(64, s) / 8.0 if s_mode else s / 8.0
+    return (st["active_rows"] * (8.0 + 2.0 * sb) + st["m_active_total"] * (4.0 + sb)
+            + st["changed_rows"] * 4.0)
+
+
 def kernel_name(st: dict) -> str:
     """Name of the pull kernel instantiation a call used (words per gather,
     lanes per group, PROPAGATE-S passes as words), as ncu prints it."""
@@ -199,6 +215,14 @@ def kernel_name(st: dict) -> str:
         nw = 1 if wp <= 32 else 2 if wp <= 64 else 3 if wp <= 96 else 4 if wp <= 128 else 0
         return f"k_pull_wide<{nw}, {1 if st.get('pass_words', 1) > 1 else 0}>"
     return f"k_pull<{cw}, {st['group_lanes']}, {1 if st.get('pass_words', 1) > 1 else 0}>"
+
+
+DEFAULT_WORKLOAD = "rmat26_undirected_s512"
+# steps (and warm-ups) of the batched-vs-plain comparison the default line carries
+BATCH_STEPS = 3
+# seeds of the oracle's timed sample per workload (one BFS per host thread;
+# the scale-26 graph takes seconds per BFS): default 64
+CPU_SEEDS = {"rmat26_undirected_s512": 16}
 
 
 def run_ours(args):
@@ -287,11 +311,13 @@ def run_ours(args):
             times.append(e0.elapsed_time(e2))
             p_ms.append(e0.elapsed_time(e1))
             s_ms.append(e1.elapsed_time(e2))
-            for st in (stp, sts):
-                k = per_kernel.setdefault(kernel_name(st), [0.0, 0, 0.0])
+            for st, s_mode in ((stp, False), (sts, True)):
+                k = per_kernel.setdefault(kernel_name(st), [0.0, 0, 0.0, 0.0, 0.0])
                 k[0] += st["ms_pull"]
                 k[1] += st["pull_launches"]
                 k[2] += pull_bytes(st)
+                k[3] += round_bytes(st, s, s_mode)
+                k[4] += st["ms_post"]
                 post_ms += st["ms_post"]
                 launches += st["launches"]
         torch.cuda.nvtx.range_pop()
@@ -311,7 +337,7 @@ def run_ours(args):
     rp_pinned = torch.from_numpy(np.array(g.row_ptr)).pin_memory().numpy()
     col_pinned = torch.from_numpy(np.array(g.col)).pin_memory().numpy()
     e2e_ms = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(args.steps, args.e2e_steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = pg.Graph.from_csr(rp_pinned, col_pinned, g.n, directed=g.directed, stream=sptr)
@@ -324,11 +350,7 @@ def run_ours(args):
     e2e_total = reduce_max(sum(e2e_ms), world, dev)
     e2e_value = reduce_sum(float(work_step * len(e2e_ms)), world, dev) / (e2e_total / 1e3)
 
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
-                else "fallback 6.8 TB/s (profiling recipe)")
+    peak, peak_src = _peak()
     traffic_table = {}
     tpath = os.path.join(ROOT, "profiles", "pull_traffic.json")
     if os.path.exists(tpath):
@@ -339,13 +361,20 @@ def run_ours(args):
                              if isinstance(hashes, dict) and hashes.get(k) == kernel_hash(k)}
 
     def roofline_of(name):
-        ms, nl, byt = per_kernel[name]
-        ach = (byt / max(nl, 1)) / ((ms / max(nl, 1)) / 1e3) / 1e9
+        ms, nl, design, alg, post = per_kernel[name]
+        nl = max(nl, 1)
+        ach = (alg / nl) / ((ms / nl) / 1e3) / 1e9
+        design_ach = (design / nl) / ((ms / nl) / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": traffic_table.get(name), "kernel": name,
-                "algorithmic_bytes_per_launch": byt / max(nl, 1),
-                "ms_per_launch": ms / max(nl, 1), "launches": nl,
-                "share_of_step": ms / max(sum(times), 1e-9), "peak_source": peak_src}
+                "algorithmic_bytes_per_launch": alg / nl,
+                "bytes_basis": "per round |A_t|(8+s/4) + m_active(t)(4+s/8) + |F_t|*4 "
+                               "(s = 64 per pass for PROPAGATE-S), from the library's own "
+                               "per-round counters, divided by this kernel's time",
+                "ms_per_launch": ms / nl, "launches": nl,
+                "share_of_step": ms / max(sum(times), 1e-9), "peak_source": peak_src,
+                "round_frac": (alg / ((ms + post) / 1e3) / 1e9) / peak,
+                "design_bytes_per_launch": design / nl, "design_frac": design_ach / peak}
 
     ranked = sorted(per_kernel, key=lambda k: -per_kernel[k][0])
     roofline = roofline_of(ranked[0])
@@ -365,7 +394,16 @@ def run_ours(args):
                    "options": tuned or "library defaults (--tune 0)"},
         "parts": {"propagate_p_ms": statistics.mean(p_ms), "propagate_s_ms": statistics.mean(s_ms),
                   "propagate_p_seed_edges_per_s": work_p / (statistics.mean(p_ms) / 1e3),
-                  "propagate_s_seed_edges_per_s": work_p / (statistics.mean(s_ms) / 1e3)},
+                  "propagate_s_seed_edges_per_s": work_p / (statistics.mean(s_ms) / 1e3),
+                  "propagate_s_own_seed_edges_per_s":
+                      sts["seed_edge_traversals"] / (statistics.mean(s_ms) / 1e3),
+                  "propagate_s_own_work_note": "PROPAGATE-S's own per-pass work "
+                      "(sum over its 64-plane passes of 64 * m_active), beside the "
+                      "method-defined PROPAGATE-P work both runs are credited with",
+                  "p_rounds": {"rounds": rp.rounds, "dense_rounds": stp["dense_rounds"],
+                               "m_active_total": stp["m_active_total"],
+                               "active_rows": stp["active_rows"],
+                               "changed_rows": stp["changed_rows"]}},
         "roofline": roofline,
         "roofline_other_kernels": others,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -373,33 +411,36 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if args.batched and args.workload == DEFAULT_WORKLOAD:
+        # the metric's own comparison, batched vs plain, on the mixed workload
+        # of 512 graphs (library default schedules, fewer steps than the
+        # headline so that the whole run stays within minutes)
+        G.close()
+        torch.cuda.empty_cache()
+        out["batched"] = measure_batch("mix512_batched", rank, world, dev, BATCH_STEPS,
+                                       BATCH_STEPS, 0, args.tune_trials, 1, peak, peak_src)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(g, seeds, s, args.cpu_seeds)
+        out["cpu_baseline"] = cpu_baseline(g, seeds, s, cpu_seeds(args))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_batch(args):
+def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, e2e_steps,
+                  peak, peak_src):
     """Batched PROPAGATE-P over the mixed workload against the plain loop
-    (one pg_propagate_p per graph on the same resident graphs): value is the
-    batched seed-edge traversals/s, with the plain loop's beside it; every
-    graph's counts must be identical both ways."""
+    (one pg_propagate_p per graph on the same resident graphs), over the
+    same graphs and seeds; every graph's counts must be identical both ways.
+    Returns the batched and plain throughputs, the dominant kernel's
+    roofline (a timed run of each width class), an end-to-end figure and an
+    oracle baseline on a sample of the mix."""
     import ctypes
     import torch
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
     import paper_2301_06499_gb300 as pg
     from paper_2301_06499_gb300 import inputs as I
 
-    count, n_lo, n_hi, seed = BATCH_WORKLOADS[args.workload]
+    count, n_lo, n_hi, seed = BATCH_WORKLOADS[workload]
     t0 = time.perf_counter()
     items = I.mix(count, n_lo, n_hi, seed + 1000 * rank)  # each rank its own replica
     gen_s = time.perf_counter() - t0
@@ -422,23 +463,23 @@ def run_batch(args):
         return res, work, launches
 
     def batched():
-        batch.run(opts=None if args.tune else opts, stream=sptr)
+        batch.run(opts=None if tune else opts, stream=sptr)
         return batch.stats()
 
     t0 = time.perf_counter()
     batch.run(opts=opts, stream=sptr)  # packs the graphs (host union + upload), untimed
     pack_s = time.perf_counter() - t0
-    tune = None
-    if args.tune:  # the autotuner picks each width class's schedule, untimed
+    tuned = None
+    if tune:  # the autotuner picks each width class's schedule, untimed
         t0 = time.perf_counter()
-        tune = batch.tune(max_trials=args.tune_trials, stream=sptr)
-        tune["tune_s"] = time.perf_counter() - t0
-        tune["classes"] = [{"graphs": ng, "words_per_thread": o["words_per_thread"],
-                            "group_lanes": o["group_lanes"],
-                            "dense_threshold": round(o["dense_threshold"], 3),
-                            "test_changed": o["test_changed"]}
-                           for ng, o in batch.group_options()]
-    for _ in range(args.warmup):
+        tuned = batch.tune(max_trials=tune_trials, stream=sptr)
+        tuned["tune_s"] = time.perf_counter() - t0
+        tuned["classes"] = [{"graphs": ng, "words_per_thread": o["words_per_thread"],
+                             "group_lanes": o["group_lanes"],
+                             "dense_threshold": round(o["dense_threshold"], 3),
+                             "test_changed": o["test_changed"]}
+                            for ng, o in batch.group_options()]
+    for _ in range(warmup):
         res_p, work, plain_launches = plain()
         bst = batched()
     for k, r in enumerate(res_p):
@@ -448,7 +489,7 @@ def run_batch(args):
 
     def timed(fn):
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -469,15 +510,41 @@ def run_batch(args):
         torch.distributed.barrier()
     b_total = reduce_max(sum(b_ms), world, dev)
     p_total = reduce_max(sum(p_ms), world, dev)
-    total_work = reduce_sum(float(work * args.steps), world, dev)
+    total_work = reduce_sum(float(work * steps), world, dev)
     value = total_work / (b_total / 1e3)
     plain_value = total_work / (p_total / 1e3)
+
+    # the dominant pull kernel of the batched run: one more run with
+    # per-kernel events (plain launches, library default schedule), per class
+    batch.run(opts=pg.options(timing=1), stream=sptr)
+    classes = []
+    for gi, st in enumerate(batch.group_stats()):
+        s_cls = 64 * st["words_per_row"]
+        classes.append({"kernel": kernel_name(st), "s": s_cls, "ms_pull": st["ms_pull"],
+                        "pull_launches": st["pull_launches"], "ms_post": st["ms_post"],
+                        "bytes": round_bytes(st, s_cls, False)})
+    roofline = None
+    timed_classes = [c for c in classes if c["pull_launches"] > 0 and c["ms_pull"] > 0]
+    if timed_classes:
+        top = max(timed_classes, key=lambda c: c["ms_pull"])
+        ach = top["bytes"] / (top["ms_pull"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "kernel": top["kernel"],
+                    "width_class_s": top["s"],
+                    "algorithmic_bytes_per_launch": top["bytes"] / top["pull_launches"],
+                    "ms_per_launch": top["ms_pull"] / top["pull_launches"],
+                    "launches": top["pull_launches"], "peak_source": peak_src,
+                    "bytes_basis": "per round |A_t|(8+s/4) + m_active(t)(4+s/8) + |F_t|*4 "
+                                   "over the width class's packed union (s = the class's "
+                                   "seeds per graph), divided by its pull kernel's time",
+                    "note": "a run with per-launch events (plain launches, library default "
+                            "schedule) after the timed steps"}
 
     # end to end with host buffers: pack, upload, run, read every result back
     h2d = sum(it.graph.row_ptr.nbytes + it.graph.col.nbytes + it.seeds.nbytes for it in items)
     d2h = sum(r.counts.nbytes for r in res_p)
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(max(1, min(steps, e2e_steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with pg.Batch() as b2:
@@ -490,13 +557,30 @@ def run_batch(args):
     e2e_total = reduce_max(sum(e2e_ms), world, dev)
     e2e_value = reduce_sum(float(work * len(e2e_ms)), world, dev) / (e2e_total / 1e3)
 
+    # the oracle on a sample of the mix: its first graphs, 8 seeds each
+    cpu = None
+    if rank == 0:
+        import oracle
+        wk, tt, nk = 0, 0.0, 0
+        for it in items:
+            if tt > 10.0:
+                break
+            w1, t1, threads = oracle_sample(it.graph, it.seeds, min(8, it.s), steps=1)
+            wk += w1
+            tt += min(t1)
+            nk += 1
+        cpu = {"value": wk / tt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"oracle BFS from 8 seeds of each of the mix's first {nk} graphs "
+                         f"({tt:.2f} s), credited each sample's own k*sum_t m_active(t)"}
+
     widths = sorted({(it.s + 63) // 64 for it in items})
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": b_total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": args.workload,
+        "value": value, "ms_per_step": b_total / steps,
+        "plain": {"value": plain_value, "ms_per_step": p_total / steps,
+                  "gpu_launches": int(plain_launches)},
+        "batched_over_plain": plain_value and value / plain_value,
+        "counts_identical": True,
+        "config": {"workload": workload,
                    "description": f"{count} graphs, n log-uniform in [{n_lo:g}, {n_hi:g}], "
                                   f"ER/R-MAT/grid (RNG {seed}), s from eps in {{0.1, 0.2}}",
                    "sum_n": int(sum(it.graph.n for it in items)),
@@ -504,24 +588,60 @@ def run_batch(args):
                    "sum_s": int(sum(it.s for it in items)), "signature_words": widths,
                    "groups": bst["groups"], "batched_rounds": bst["sweeps"],
                    "seed_edge_traversals_per_step": int(work),
-                   "generate_s": gen_s, "pack_s": pack_s,
+                   "generate_s": gen_s, "pack_s": pack_s, "steps": steps, "warmup": warmup,
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world} (independent mixes)"},
-        "plain": {"value": plain_value, "ms_per_step": p_total / args.steps,
-                  "gpu_launches": int(plain_launches)},
-        "batched_over_plain": plain_value and value / plain_value,
-        "autotune": tune,
-        "roofline": None,
+        "autotune": tuned,
+        "width_classes": classes,
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / len(e2e_ms)},
         "gpu_launches": int(bst["launches"]),
         "clocks": clk.summary(),
+        "cpu_baseline": cpu,
     }
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     batch.close()
     for G in graphs:
         G.close()
+    return out
+
+
+def _peak():
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+           else "fallback 6.8 TB/s (profiling recipe)")
+    return peak, src
+
+
+def run_batch(args):
+    """The mixed workload alone: batched seed-edge traversals/s, with the
+    plain loop's beside it (see measure_batch)."""
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, peak_src = _peak()
+    r = measure_batch(args.workload, rank, world, dev, args.steps, args.warmup, args.tune,
+                      args.tune_trials, args.e2e_steps, peak, peak_src)
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": r["config"], "plain": r["plain"],
+        "batched_over_plain": r["batched_over_plain"], "autotune": r["autotune"],
+        "width_classes": r["width_classes"], "roofline": r["roofline"], "e2e": r["e2e"],
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        "cpu_baseline": r["cpu_baseline"],
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -744,29 +864,43 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()[:12]
 
 
+def cpu_seeds(args) -> int:
+    return args.cpu_seeds or CPU_SEEDS.get(args.workload, 64)
+
+
+# distance capacity of the oracle's histograms (R-MAT and ER eccentricities are
+# tens; the 4096^2 grid's is ~8,000): the oracle reports an overflow
+HIST_CAP = 1 << 15
+
+
 def oracle_sample(g, seeds, k, steps=1, threads=None, budget_s=None):
     """Times the oracle (one FIFO BFS per seed, threads over seeds) on the
-    first k seeds, `steps` times after the run that also records distances
-    (the warm-up), or fewer once budget_s seconds are spent. Its work is the
-    method-defined count of that k-seed problem, k * sum_t m_active(t), with
-    m_active computed by the oracle from the sample's own distances (nothing
-    comes from the GPU path)."""
+    first k seeds: the run that also records distances, then up to `steps`
+    more runs while the total stays within budget_s seconds. Returns the
+    work, every run's time (the first is the distance-recording run) and the
+    threads. The work is the method-defined count of that k-seed problem,
+    k * sum_t m_active(t), with m_active computed by the oracle from the
+    sample's own distances (nothing comes from the GPU path)."""
     import oracle
     threads = threads or os.cpu_count() or 1
     sample = np.ascontiguousarray(seeds[:k])
-    hist, _, dmat = oracle.seed_histograms(g, sample, threads=threads, with_distances=True)
+    t0 = time.perf_counter()
+    hist, _, dmat = oracle.seed_histograms(g, sample, cap=min(g.n, HIST_CAP), threads=threads,
+                                           with_distances=True)
+    times = [time.perf_counter() - t0]
     work = int(k) * int(oracle.m_active(g, dmat, hist.shape[1], threads=threads).sum())
     del dmat
-    times = []
     for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle.seed_histograms(g, sample, threads=threads)
-        times.append(time.perf_counter() - t0)
         if budget_s is not None and sum(times) > budget_s:
             break
+        t0 = time.perf_counter()
+        oracle.seed_histograms(g, sample, cap=min(g.n, HIST_CAP), threads=threads)
+        times.append(time.perf_counter() - t0)
     return work, times, threads
 
 
+# wall-clock bound of the reference arm's oracle runs
+REF_BUDGET_S = 240.0
 # one host sweep of Alg. 1 reads every arc: beyond this many the bench skips it
 ALG1_MAX_ARCS = 1 << 28
 
@@ -777,16 +911,20 @@ def cpu_baseline(g, seeds, s, k):
     the same k-seed sample and credited the same work."""
     import oracle
     work, times, threads = oracle_sample(g, seeds, k, steps=5, budget_s=15.0)
-    dt = min(times)
-    k1 = min(4, k)
-    work1, times1, _ = oracle_sample(g, seeds, k1, steps=5, threads=1, budget_s=10.0)
+    dt = min(times[1:] or times)
+    how = (f"best of {len(times) - 1} after a warm-up" if len(times) > 1 else
+           "one run (it also records the distances the work count needs; a run takes "
+           "longer than the bench's CPU budget)")
     out = {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": f"oracle BFS from {k} of the {s} seeds on the same graph, best of "
-                     f"{len(times)} after a warm-up ({dt:.2f} s wall on {threads} threads), "
-                     f"credited that k-seed problem's k*sum_t m_active(t)",
-           "value_1_thread": work1 / min(times1),
-           "sample_1_thread": f"oracle BFS from {k1} seeds on one thread, best of "
-                              f"{len(times1)} ({min(times1):.2f} s)"}
+           "sample": f"oracle BFS from {k} of the {s} seeds on the same graph, {how} "
+                     f"({dt:.2f} s wall on {threads} threads, the oracle's own CSR check and "
+                     f"transpose included), credited that k-seed problem's k*sum_t m_active(t)"}
+    if g.m <= ALG1_MAX_ARCS:
+        k1 = min(4, k)
+        work1, times1, _ = oracle_sample(g, seeds, k1, steps=5, threads=1, budget_s=10.0)
+        t1 = min(times1[1:] or times1)
+        out["value_1_thread"] = work1 / t1
+        out["sample_1_thread"] = f"oracle BFS from {k1} seeds on one thread ({t1:.2f} s)"
     if g.m > ALG1_MAX_ARCS:
         out["alg1_host"] = {"skipped": f"{g.m} arcs: a host sweep per round exceeds the "
                                        f"bench's CPU budget"}
@@ -816,18 +954,27 @@ def run_reference(args):
     g = make_graph(spec)
     from paper_2301_06499_gb300 import inputs as I
     seeds = I.seeds(g.n, s, seed_stream(args.workload, 0))
-    k = args.cpu_seeds
-    oracle_sample(g, seeds, k, steps=args.warmup)
-    work, times, threads = oracle_sample(g, seeds, k, steps=args.steps)
-    value = work * len(times) / sum(times)
+    k = cpu_seeds(args)
+    # run 0 records distances (for the work count) and is a warm-up; runs
+    # 1..W-1 are warm-ups; the next K are timed, within REF_BUDGET_S seconds
+    work, times, threads = oracle_sample(g, seeds, k, steps=args.warmup - 1 + args.steps,
+                                         budget_s=REF_BUDGET_S)
+    warm = min(args.warmup, len(times) - 1)
+    timed = times[warm:]
+    value = work * len(timed) / sum(timed)
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "steps": len(timed), "warmup": warm,
+        "ms_per_step": 1e3 * sum(timed) / len(timed), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m, "s": s},
+        "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m, "s": s,
+                   "steps_requested": args.steps, "warmup_requested": args.warmup,
+                   "time_bound": f"runs stop once {REF_BUDGET_S:.0f} s are spent (one oracle "
+                                 f"run over the scale-26 graph takes about a minute); at least "
+                                 f"one run is timed"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"oracle BFS from {k} of the {s} seeds per step, credited "
+                         "sample": f"oracle BFS from {k} of the {s} seeds per step (the "
+                                   f"oracle's own CSR check and transpose included), credited "
                                    f"that k-seed problem's k*sum_t m_active(t)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -870,7 +1017,7 @@ def write_traffic(workload: str, csvs: list, out_path: str | None = None) -> dic
     """profiles/pull_traffic.json from ncu CSV captures of the pull kernels
     (dram__bytes_read.sum and dram__bytes_write.sum): mean bytes per launch
     of each kernel, with the hash of the sources it was built from."""
-    from paper_2301_06499_gb300 import ncu_summary
+    import ncu_summary
     per = {}
     for path in csvs:
         per.update(ncu_summary.traffic(path))
@@ -902,12 +1049,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) +
-                    sorted(SERVE_WORKLOADS), default="rmat22_directed_s256")
+                    sorted(SERVE_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--slots", type=int, default=4, help="server slots (serving workload)")
     ap.add_argument("--tune", type=int, default=1,
                     help="1 = let the autotuner pick the schedule options before timing")
     ap.add_argument("--tune-trials", type=int, default=16)
-    ap.add_argument("--cpu-seeds", type=int, default=64)
+    ap.add_argument("--cpu-seeds", type=int, default=0,
+                    help="seeds of the oracle's timed sample (0 = per workload: 16 on the "
+                         "scale-26 graph, else 64)")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="1 = the default workload's line also carries the batched-vs-plain "
+                         "comparison on the 512-graph mix (key 'batched')")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="end-to-end steps (graph upload + both runs + metrics), at most --steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch every round kernel on the stream (no CUDA graph), e.g. under ncu")

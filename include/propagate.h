@@ -64,6 +64,17 @@ typedef struct pg_graph pg_graph;
                              library pulls over the out-edge transpose it
                              builds. Directed graphs only (undirected graphs
                              are their own transpose). */
+#define PG_RELABEL 8u     /* renumber the nodes internally, high in-degree
+                             first (buckets of 16 per octave of degree, each
+                             in the original order): the most gathered rows
+                             then share cache lines and stay in L2. Seeds are
+                             still given, and counts returned, in the
+                             caller's ids and order; every output is
+                             unchanged. Without PG_RELABEL or PG_KEEP_ORDER
+                             the library relabels graphs of at least 2^16
+                             nodes whose largest in-degree is at least 16
+                             times the mean (skewed, power-law degrees) */
+#define PG_KEEP_ORDER 16u /* never relabel */
 
 /*
  * Per-round, per-seed counts. Caller-owned host buffers.
@@ -166,6 +177,36 @@ typedef struct {
   uint64_t dist_sum;             /* sum_r r (R[r]-R[r-1]) */
 } pg_metrics_out;
 
+/*
+ * Progressive sampling. Sec. 4.2 notes that the seed-by-seed variant can keep
+ * adding seeds until the estimates settle, and Sec. 6 lists this progressive
+ * sampling as one of its uses; the paper gives no stopping rule. Thm. 3 puts
+ * the sample a fixed accuracy needs at the order ln n / eps^2. This call
+ * draws seeds uniformly without replacement from a seeded SplitMix64 stream
+ * (its first distinct values, so a smaller sample is a prefix of a larger
+ * one), runs PROPAGATE-P on blocks of `block` seeds, appends each block's
+ * per-seed count columns (seeds never interact, so they equal one call over
+ * all drawn seeds), and stops at ceil(ln n / eps^2) seeds (capped at n; the
+ * constant 1 is this library's reading) or, with stable_tol > 0, as soon as
+ * the average distance and the interpolated effective diameter (tau = 9/10)
+ * both moved by less than stable_tol (relative) over two consecutive blocks.
+ *  seeds    host int32[out->s] out: the drawn seeds in draw order
+ *  s_drawn  out: seeds drawn (columns of counts written)
+ *  out      out->s (in) = the caller's column capacity, at least
+ *           min(n, ceil(ln n / eps^2)); counts[t * out->s + i] for i <
+ *           *s_drawn as pg_counts (zero elsewhere); m_active (optional) sums
+ *           each block's own m_active; out->rounds = the largest T
+ *  history  pg_metrics_out[max_history] (may be NULL if max_history = 0):
+ *           the metrics over all seeds drawn after each block
+ *  blocks   out (may be NULL): blocks run
+ * Errors: PG_EINVAL (arguments, eps <= 0, too few columns), PG_ERANGE (a
+ * block needed more than out->max_rounds rounds), else as pg_propagate_p.
+ */
+pg_status pg_progressive(pg_graph *g, double eps, int32_t block, double stable_tol,
+                         uint64_t rng_seed, int32_t *seeds, int32_t *s_drawn, pg_counts *out,
+                         pg_metrics_out *history, int32_t max_history, int32_t *blocks,
+                         const pg_options *opt, void *stream);
+
 /* Work and timing of the last propagate call on a graph (for benchmarks). */
 typedef struct {
   int32_t sweeps;            /* rounds executed, the final empty one included */
@@ -195,6 +236,10 @@ typedef struct {
   int32_t pass_words;        /* PROPAGATE-S: passes run side by side as the
                                 words of one signature (the pull instantiation
                                 k_pull<words, lanes, 1>); 1 otherwise */
+  int32_t reserved;
+  uint64_t active_rows;      /* sum over rounds of |A_t|, the rows a round had
+                                to revisit (those m_active sums the in-degrees
+                                of); PROPAGATE-S: summed over passes */
 } pg_stats;
 
 /* Message for a status code (static storage). */
@@ -223,6 +268,10 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
 
 /* Frees the graph and its cached workspace. NULL is allowed. */
 void pg_graph_free(pg_graph *g);
+
+/* *relabelled = 1 if the library renumbered g's nodes internally
+ * (PG_RELABEL, or by default on a skewed graph), else 0. */
+pg_status pg_graph_is_relabelled(const pg_graph *g, int32_t *relabelled);
 
 /* n and m of a graph. */
 pg_status pg_graph_info(const pg_graph *g, int64_t *n, int64_t *m);
@@ -322,7 +371,10 @@ pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t algo
  *  stream        cudaStream_t; the call returns when the counts are written
  * Limits: 4 * n * ceil(s/64) 64-bit words plus a small header must fit the
  * scratch (with s <= 64, n up to about one million); larger problems return
- * PG_ETOOBIG. Errors: PG_EINVAL (arguments, seeds, CSR), PG_ERANGE, PG_ECUDA.
+ * PG_ETOOBIG. Errors: PG_EINVAL (arguments, seeds, CSR), PG_ERANGE (rows
+ * 0..max_rounds written, *rounds = max_rounds + 1), PG_ECUDA (a launch or
+ * copy failed). The call waits on the stream after validation and after every
+ * round (it reads the round's changed flag back to the host).
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture. All calls share
  * the array and each clears what it uses; calls whose GPU work overlaps (on

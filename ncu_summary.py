@@ -1,8 +1,8 @@
 """Summaries of Nsight Compute CSV output (``ncu --csv --log-file ...``).
 
-  python -m paper_2301_06499_gb300.ncu_summary launches <launches.csv>
+  python ncu_summary.py launches <launches.csv>
       per kernel: launches, total device time, share (markdown table)
-  python -m paper_2301_06499_gb300.ncu_summary traffic <metrics.csv> [skip]
+  python ncu_summary.py traffic <metrics.csv> [skip]
       per kernel: mean DRAM bytes (read + write) per launch, over its launches
       after the first `skip` of that kernel (JSON; `bench.py --write-traffic`
       turns such captures into profiles/pull_traffic.json)

@@ -73,11 +73,14 @@ class Graph:
 
     @classmethod
     def from_csr(cls, row_ptr, col, n: int | None = None, directed: bool = True,
-                 stream=None, reverse: bool = False) -> "Graph":
+                 stream=None, reverse: bool = False, relabel: bool | None = None) -> "Graph":
         """row_ptr int64[n+1] and col int32[m] as numpy arrays (copied from the
         host) or CUDA torch tensors (used in place). reverse=True counts balls
-        grown backward (nodes reaching each seed; PG_REVERSE)."""
+        grown backward (nodes reaching each seed; PG_REVERSE). relabel: True =
+        PG_RELABEL, False = PG_KEEP_ORDER, None = the library's default."""
         rev = _abi.PG_REVERSE if reverse else 0
+        if relabel is not None:
+            rev |= _abi.PG_RELABEL if relabel else _abi.PG_KEEP_ORDER
         L = _abi.lib()
         h = ctypes.c_void_p()
         st = stream if stream is not None else _current_stream()
@@ -103,10 +106,18 @@ class Graph:
         return cls(h, int(n), int(m), keep)
 
     @classmethod
-    def from_inputs(cls, g, stream=None, reverse: bool = False) -> "Graph":
+    def from_inputs(cls, g, stream=None, reverse: bool = False,
+                    relabel: bool | None = None) -> "Graph":
         """From a generated graph (``inputs.Graph``) held in host memory."""
         return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream,
-                            reverse=reverse)
+                            reverse=reverse, relabel=relabel)
+
+    @property
+    def relabelled(self) -> bool:
+        r = ctypes.c_int32()
+        _abi.check(_abi.lib().pg_graph_is_relabelled(self._h, ctypes.byref(r)),
+                   "pg_graph_is_relabelled")
+        return bool(r.value)
 
     def rounds_bound(self) -> int:
         r = ctypes.c_int32()
@@ -441,43 +452,37 @@ class Server:
 
 def progressive(g: "Graph", eps: float, rng_seed: int = 0, block: int = 256,
                 stable_tol: float | None = None, opts=None, stream=None):
-    """Progressive sampling: PROPAGATE-P over seed blocks drawn uniformly
-    without replacement, until the sample reaches ceil(ln n / eps^2) seeds
-    (the order of Thm. 3's sample size, constant 1) or, with stable_tol set,
-    until average distance and effective diameter (interpolated) both move by
-    less than stable_tol (relative) over two consecutive blocks. Seeds never
-    interact, so the counts equal one call with all the drawn seeds.
+    """pg_progressive: PROPAGATE-P over seed blocks drawn uniformly without
+    replacement until ceil(ln n / eps^2) seeds, or, with stable_tol, until the
+    estimates settle (see include/propagate.h).
 
-    Returns (Result over all drawn seeds, seeds, history of metrics)."""
+    Returns (Result over all drawn seeds, seeds, per-block metrics)."""
     n = g.n
-    target = min(n, int(np.ceil(np.log(max(n, 2)) / (eps * eps))))
-    order = np.random.default_rng(rng_seed).permutation(n).astype(np.int32)
-    cols, drawn, hist, T = [], 0, [], 0
-    calm = 0
-    while drawn < target:
-        sd = order[drawn:min(drawn + block, target)]
-        r = propagate_p(g, sd, opts=opts, stream=stream)
-        cols.append(r.counts)
-        drawn += sd.size
-        T = max(T, r.rounds)
-        counts = np.zeros((T + 1, drawn), dtype=np.uint32)
-        c0 = 0
-        for c in cols:
-            counts[:c.shape[0], c0:c0 + c.shape[1]] = c
-            c0 += c.shape[1]
-        res = Result(rounds=T, counts=counts, m_active=np.zeros(T + 2, dtype=np.uint64),
-                     s=drawn, n=n)
-        m = metrics(res, n)
-        if hist and stable_tol is not None:
-            prev = hist[-1]
-            d1 = abs(m["avg_distance"] - prev["avg_distance"]) / max(prev["avg_distance"], 1e-300)
-            d2 = (abs(m["eff_diameter_interp"] - prev["eff_diameter_interp"]) /
-                  max(prev["eff_diameter_interp"], 1e-300))
-            calm = calm + 1 if max(d1, d2) < stable_tol else 0
-        hist.append(dict(m, seeds=drawn))
-        if calm >= 2:
-            break
-    return res, order[:drawn].copy(), hist
+    cols = max(1, min(n, int(np.ceil(np.log(max(n, 2)) / (eps * eps)))))
+    st = stream if stream is not None else _current_stream()
+    o = opts if opts is not None else options()
+    cap = min(g.rounds_bound(), 65535, max(1024, (1 << 30) // (4 * cols)))
+    seeds = np.zeros(cols, dtype=np.int32)
+    counts = np.zeros((cap + 1, cols), dtype=np.uint32)
+    mact = np.zeros(cap + 2, dtype=np.uint64)
+    hist = (_abi.MetricsOut * (-(-cols // block)))()
+    c = _abi.Counts(s=cols, max_rounds=cap, rounds=0, reserved=0, counts=counts.ctypes.data,
+                    m_active=mact.ctypes.data)
+    drawn, nblk = ctypes.c_int32(0), ctypes.c_int32(0)
+    _abi.check(_abi.lib().pg_progressive(g._h, float(eps), int(block),
+                                         float(stable_tol or 0.0), int(rng_seed),
+                                         seeds.ctypes.data, ctypes.byref(drawn), ctypes.byref(c),
+                                         hist, len(hist), ctypes.byref(nblk), ctypes.byref(o), st),
+               "pg_progressive")
+    k, T = int(drawn.value), int(c.rounds)
+    res = Result(rounds=T, counts=np.ascontiguousarray(counts[:T + 1, :k]),
+                 m_active=mact[:T + 2].copy(), s=k, n=n)
+    history = []
+    for b in range(int(nblk.value)):
+        h = {f: getattr(hist[b], f) for f, _ in _abi.MetricsOut._fields_}
+        h["seeds"] = min(k, (b + 1) * block) if b + 1 < nblk.value else k
+        history.append(h)
+    return res, seeds[:k].copy(), history
 
 
 def metrics(res: Result, n: int | None = None, tau=(9, 10)) -> dict:

@@ -18,6 +18,8 @@ PG_NOALLOC_MAX_SEEDS = 1024
 PG_DEVICE_PTRS = 1
 PG_BORROW = 2
 PG_REVERSE = 4
+PG_RELABEL = 8
+PG_KEEP_ORDER = 16
 PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
 PG_ALG_P, PG_ALG_S = 0, 1
 
@@ -57,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
                 ("post_launches", ctypes.c_int32), ("test_changed", ctypes.c_int32),
                 ("words_per_gather", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64),
-                ("pass_words", ctypes.c_int32)]
+                ("pass_words", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("active_rows", ctypes.c_uint64)]
 
 
 class TuneReport(ctypes.Structure):
@@ -109,6 +112,7 @@ SIGNATURES = {
                                          _vp, ctypes.POINTER(_vp)]),
     "pg_graph_free": (None, [_vp]),
     "pg_graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pg_graph_is_relabelled": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "pg_query_rounds_bound": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "pg_propagate_p": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(Counts),
                                       ctypes.POINTER(Options), _vp]),
@@ -117,6 +121,10 @@ SIGNATURES = {
     "pg_metrics": (ctypes.c_int, [ctypes.POINTER(Counts), _i64, _i32, _i32,
                                   ctypes.POINTER(MetricsOut)]),
     "pg_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "pg_progressive": (ctypes.c_int, [_vp, ctypes.c_double, _i32, ctypes.c_double,
+                                      ctypes.c_uint64, _vp, ctypes.POINTER(_i32),
+                                      ctypes.POINTER(Counts), ctypes.POINTER(MetricsOut), _i32,
+                                      ctypes.POINTER(_i32), ctypes.POINTER(Options), _vp]),
     "pg_propagate_p_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i32, _vp, _i32,
                                               ctypes.POINTER(_i32), _vp]),
     "pg_autotune": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, ctypes.POINTER(Options),

@@ -114,7 +114,9 @@ pg_status build_groups(pg_batch *b, cudaStream_t st) {
       a0 += it.m;
     }
     rp[(size_t)n] = a0;
-    pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, 0, st, &gr.g);
+    // the union keeps its node order: each graph's nodes stay one block
+    pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, PG_KEEP_ORDER, st,
+                                     &gr.g);
     if (rc) return rc;
     rc = ensure(gr.node_graph, sizeof(int32_t) * (size_t)n);
     if (!rc) {  // the packed graph knows its parts (sliced-ELL chunks per graph)

@@ -39,7 +39,7 @@ struct Ctrl {
   int32_t dense_rounds;
   int32_t row_base;      // round held in row 0 of the device counts window
   int32_t iters;         // post launches of this pass (termination guard)
-  int32_t pad;
+  int32_t ndense;        // packed batch: graphs swept whole in round t (in dlist)
   unsigned long long nF_prev;  // |F_{t-1}|
 };
 
@@ -52,6 +52,7 @@ struct RoundStats {
   unsigned long long items;
   unsigned long long changed;
   unsigned long long fsum;
+  unsigned long long rows;     // active rows |A_t| (PROPAGATE-S passes as words: row x pass)
 };
 
 // Everything the round kernels need, passed by value.
@@ -98,6 +99,15 @@ struct Params {
   unsigned long long *gfsum;
   const unsigned long long *gthr;
   int32_t nseg;               // batch: graphs in the union
+  // batch: first sliced-ELL chunk of each graph [nseg + 1]; the graphs swept
+  // whole in the next round (dlist, ctrl->ndense of them) and the exclusive
+  // prefix of their chunk counts (dpref), written by the post kernel
+  const int64_t *seg_chunk0;
+  int32_t *dlist;
+  int64_t *dpref;
+  const int32_t *perm;  // relabelled graph: caller id -> internal id (else null)
+  int64_t perm_n;       // nodes of the relabelled graph (replicas: a seed k*perm_n + x
+                        // of copy k maps to k*perm_n + perm[x])
   RoundStats *rs;       // [row_cap + 2], slot = round - row_base
   Ctrl *ctrl;
   int32_t max_rounds;

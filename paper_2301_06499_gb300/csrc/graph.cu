@@ -383,8 +383,10 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
                                        cudaMemcpyDeviceToHost, st));
     if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
     std::vector<int32_t> chunk_seg;
+    std::vector<int64_t> chunk0((size_t)g->nseg + 1, 0);
     unsigned long long base = 0;
     for (int32_t k = 0; rc == PG_OK && k < g->nseg; ++k) {
+      chunk0[(size_t)k] = (int64_t)(base / 32);
       unsigned long long run = base;
       for (int32_t b = 0; b <= Lmax; ++b) {
         const unsigned long long c = h[(size_t)k * (Lmax + 1) + b];
@@ -396,6 +398,11 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
       base += padded;
     }
     nchunks = (int64_t)(base / 32);
+    chunk0[(size_t)g->nseg] = nchunks;
+    if (rc == PG_OK) rc = ensure(sl.chunk0, sizeof(int64_t) * chunk0.size());
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(sl.chunk0.p, chunk0.data(), sizeof(int64_t) * chunk0.size(),
+                                       cudaMemcpyHostToDevice, st));
     if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
     if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
     if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
@@ -420,6 +427,7 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
     if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));  // h outlives the copy
   } else {
     release(sl.seg);
+    release(sl.chunk0);
     rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * (Lmax + 2), st));
     if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
     if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
@@ -551,6 +559,168 @@ __global__ void k_fill_graph_of(int32_t *node_graph, int64_t n, int K) {
     node_graph[i] = (int32_t)(i / n);
 }
 
+// ------------------------------------------------------------ relabelling
+// A permutation of the node ids that puts high in-degree nodes first, in
+// buckets of 16 per octave of degree (exact below 32), each bucket in the
+// original id order (a stable counting sort). The counts are per seed, so
+// they do not depend on node ids: the library maps each seed through the
+// permutation and returns the same counts, m_active and metrics. What
+// changes is where the rows sit in memory: the most gathered rows (a
+// neighbour's delta is read once per arc to it) share cache lines and stay
+// in L2, and a dense sweep's rows, already grouped by length, become
+// consecutive ids, so their own signatures are read and written together.
+constexpr int kRelabelOct = 37;                          // degrees below 2^37
+constexpr int kRelabelBuckets = kRelabelOct * 16 + 1;    // + degree 0
+constexpr int kRelabelTile = 8192;                       // nodes per block
+
+__device__ __forceinline__ int degree_bucket(int64_t d) {
+  if (d <= 0) return kRelabelBuckets - 1;  // isolated nodes last
+  const int lg = 63 - __clzll((unsigned long long)d);
+  const int sub = lg >= 4 ? (int)((d >> (lg - 4)) & 15) : (int)((d << (4 - lg)) & 15);
+  return (kRelabelBuckets - 2) - (lg * 16 + sub);  // higher degree, smaller bucket
+}
+
+// Bucket sizes per tile of kRelabelTile nodes, bucket-major: H[b * tiles + tile].
+__global__ void __launch_bounds__(kBlock) k_relabel_hist(const int64_t *rp, int64_t n,
+                                                         int64_t tiles, int64_t *H) {
+  __shared__ uint32_t h[kRelabelBuckets];
+  for (int b = threadIdx.x; b < kRelabelBuckets; b += kBlock) h[b] = 0u;
+  __syncthreads();
+  const int64_t v0 = (int64_t)blockIdx.x * kRelabelTile;
+  for (int i = threadIdx.x; i < kRelabelTile; i += kBlock) {
+    const int64_t v = v0 + i;
+    if (v < n) atomicAdd(&h[degree_bucket(rp[v + 1] - rp[v])], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kRelabelBuckets; b += kBlock)
+    H[(int64_t)b * tiles + blockIdx.x] = h[b];
+}
+
+// Stable scatter: node v goes to H[b * tiles + tile] (scanned) plus the number
+// of earlier nodes of its tile in the same bucket. The tile is walked in id
+// order, kBlock nodes per step; within a step, warps count their bucket
+// peers (match_any) and add the counts of the warps before them.
+__global__ void __launch_bounds__(kBlock) k_relabel_scatter(const int64_t *rp, int64_t n,
+                                                            int64_t tiles, const int64_t *H,
+                                                            int32_t *new_of, int32_t *old_of) {
+  constexpr int kWarps = kBlock / 32;
+  __shared__ int64_t base[kRelabelBuckets];
+  __shared__ uint16_t wcnt[kWarps][kRelabelBuckets];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int b = threadIdx.x; b < kRelabelBuckets; b += kBlock)
+    base[b] = H[(int64_t)b * tiles + blockIdx.x];
+  const int64_t v0 = (int64_t)blockIdx.x * kRelabelTile;
+  for (int i0 = 0; i0 < kRelabelTile; i0 += kBlock) {
+    const int64_t v = v0 + i0 + threadIdx.x;
+    const bool valid = v < n;
+    const int b = valid ? degree_bucket(rp[v + 1] - rp[v]) : -1;
+    const unsigned peers = __match_any_sync(kFullMask, b);
+    const unsigned below = peers & ((1u << lane) - 1u);
+    __syncthreads();  // the previous step's counts are read and added
+    for (int k = threadIdx.x; k < kWarps * kRelabelBuckets; k += kBlock)
+      (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    if (valid && below == 0u) wcnt[w][b] = (uint16_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+      int64_t pos = base[b] + __popc(below);
+      for (int k = 0; k < w; ++k) pos += wcnt[k][b];
+      new_of[v] = (int32_t)pos;
+      old_of[pos] = (int32_t)v;
+    }
+    __syncthreads();
+    for (int bb = threadIdx.x; bb < kRelabelBuckets; bb += kBlock) {
+      int64_t add = 0;
+      for (int k = 0; k < kWarps; ++k) add += wcnt[k][bb];
+      base[bb] += add;
+    }
+  }
+}
+
+// In-degree of each new row (the exclusive scan of this gives the row pointers).
+__global__ void k_relabel_degrees(const int64_t *rp, const int32_t *old_of, int64_t n,
+                                  int64_t *nrp) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = old_of[r];
+    nrp[r] = rp[v + 1] - rp[v];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) nrp[n] = 0;
+}
+
+// A warp per new row (new ids in order, so the longest rows start first):
+// its arcs in the original order, each source renamed.
+__global__ void __launch_bounds__(kBlock) k_relabel_arcs(const int64_t *rp, const int32_t *col,
+                                                         const int32_t *new_of,
+                                                         const int32_t *old_of, int64_t n,
+                                                         const int64_t *nrp, int32_t *ncol) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+    const int32_t v = old_of[r];
+    const int64_t b = rp[v], d = rp[v + 1] - b, o = nrp[r];
+    int64_t k = lane;
+    for (; k + 96 < d; k += 128) {  // four independent renames in flight
+      const int32_t a0 = col[b + k], a1 = col[b + k + 32], a2 = col[b + k + 64],
+                    a3 = col[b + k + 96];
+      const int32_t c0 = new_of[a0], c1 = new_of[a1], c2 = new_of[a2], c3 = new_of[a3];
+      ncol[o + k] = c0;
+      ncol[o + k + 32] = c1;
+      ncol[o + k + 64] = c2;
+      ncol[o + k + 96] = c3;
+    }
+    for (; k < d; k += 32) ncol[o + k] = new_of[col[b + k]];
+  }
+}
+
+// Relabels g's in-CSR in place (new arrays, owned by g) and keeps the map
+// from original to new ids in g->perm.
+static pg_status relabel_by_degree(pg_graph *g, cudaStream_t st) {
+  const int64_t n = g->n, m = g->m;
+  const int64_t tiles = (n + kRelabelTile - 1) / kRelabelTile;
+  int64_t *H = nullptr, *nrp = nullptr;
+  int32_t *old_of = nullptr, *ncol = nullptr;
+  pg_status rc = ensure(g->perm, sizeof(int32_t) * (size_t)n);
+  if (!rc) rc = cuda_status(cudaMallocAsync((void **)&H, sizeof(int64_t) * (size_t)(tiles * kRelabelBuckets), st));
+  if (!rc) rc = cuda_status(cudaMallocAsync((void **)&old_of, sizeof(int32_t) * (size_t)n, st));
+  if (!rc) rc = cuda_status(cudaMalloc((void **)&nrp, sizeof(int64_t) * (size_t)(n + 1)));
+  if (!rc) rc = cuda_status(cudaMalloc((void **)&ncol, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1)));
+  if (!rc) {
+    k_relabel_hist<<<(unsigned)tiles, kBlock, 0, st>>>(g->row_ptr, n, tiles, H);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (!rc) rc = exclusive_scan_i64(H, tiles * kRelabelBuckets, st);
+  if (!rc) {
+    k_relabel_scatter<<<(unsigned)tiles, kBlock, 0, st>>>(g->row_ptr, n, tiles, H,
+                                                          (int32_t *)g->perm.p, old_of);
+    k_relabel_degrees<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, old_of, n, nrp);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (!rc) rc = exclusive_scan_i64(nrp, n + 1, st);
+  if (!rc && m > 0) {
+    k_relabel_arcs<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, (const int32_t *)g->perm.p,
+                                                        old_of, n, nrp, ncol);
+    rc = cuda_status(cudaGetLastError());
+  }
+  if (H) cudaFreeAsync(H, st);
+  if (old_of) cudaFreeAsync(old_of, st);
+  if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+  if (rc) {
+    if (nrp) cudaFree(nrp);
+    if (ncol) cudaFree(ncol);
+    release(g->perm);
+    return rc;
+  }
+  if (g->owns_in) {
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+  }
+  g->row_ptr = nrp;
+  g->col = ncol;
+  g->owns_in = true;
+  return PG_OK;
+}
+
 pg_status make_replicas(pg_graph *g, int K, cudaStream_t st) {
   if (g->rep && g->rep_K == K) return PG_OK;
   drop_replicas(g);
@@ -631,6 +801,7 @@ pg_status make_view(pg_graph *master, cudaStream_t st, pg_graph **out) {
     v->mean_degree = master->mean_degree;
     v->max_degree = master->max_degree;
     v->sell = master->sell;
+    v->perm_ptr = (const int32_t *)master->perm.p;
   }
   v->owns_in = v->owns_out = v->owns_sell = false;
   *out = v;
@@ -681,10 +852,12 @@ void pg_graph_free(pg_graph *g) {
     free_graph_arrays(g);
     release(g->pieces.list);
     if (g->owns_sell)
-      for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len, &g->sell.seg})
+      for (DevBuf *b : {&g->sell.items, &g->sell.col, &g->sell.off, &g->sell.len, &g->sell.seg,
+                        &g->sell.chunk0})
         release(*b);
     drop_replicas(g);
     release_workspace(g->ws);
+    release(g->perm);
   }
   delete g;
 }
@@ -762,6 +935,16 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
   if (rc == PG_OK && err_h) rc = PG_EINVAL;
   g->max_degree = (int64_t)mx_h;
   g->mean_degree = (double)m / (double)n;
+  // relabel (hubs first) when asked, or by default when the in-degrees are
+  // skewed (a power-law graph) and the graph is large enough for locality
+  // to matter; a lattice or a uniform random graph keeps its order
+  const bool relabel = !(flags & PG_KEEP_ORDER) &&
+                       ((flags & PG_RELABEL) ||
+                        (n >= (1LL << 16) && (double)g->max_degree >= 16.0 * g->mean_degree));
+  if (rc == PG_OK && relabel && m > 0) {
+    rc = relabel_by_degree(g, st);
+    if (rc == PG_OK) g->perm_ptr = (const int32_t *)g->perm.p;
+  }
   if (rc == PG_OK) {
     if (!directed) {
       g->out_ptr = g->row_ptr;
@@ -816,10 +999,17 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
     cudaGetLastError();
     free_graph_arrays(g);
     release(g->pieces.list);
+    release(g->perm);
     delete g;
     return rc;
   }
   *out = g;
+  return PG_OK;
+}
+
+pg_status pg_graph_is_relabelled(const pg_graph *g, int32_t *relabelled) {
+  if (!g || !relabelled) return PG_EINVAL;
+  *relabelled = g->perm_ptr != nullptr;
   return PG_OK;
 }
 

@@ -22,7 +22,7 @@ struct DevBuf {
 struct Workspace {
   DevBuf arena;
   DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, KW0, KW1, F0, F1, E, A, counts, rs, ctrl, seeds,
-      seed_bits, gfsum, gthr;
+      seed_bits, gfsum, gthr, dlist, dpref;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -48,6 +48,7 @@ struct SellList {
   DevBuf off;    // int64 per chunk
   DevBuf len;    // int32 per chunk (its longest piece)
   DevBuf seg;    // int32 per chunk: its graph, for a packed batch (else empty)
+  DevBuf chunk0; // int64 per graph + 1: a packed batch's first chunk of each graph
   int64_t nchunks = 0;
   int64_t slots = 0;  // total col entries
 };
@@ -75,6 +76,10 @@ struct pg_graph {
   pg::DevBuf rep_graph_of, rep_graph_s, rep_graph_col0;
   double mean_degree = 0.0;
   int64_t max_degree = 0;
+  // node relabelling (hubs first): original id -> internal id, owned here;
+  // perm_ptr is that map (a view's is its master's), null when not relabelled
+  pg::DevBuf perm;
+  const int32_t *perm_ptr = nullptr;
   pg::PieceList pieces;
   pg::SellList sell;
   pg::Workspace ws;

@@ -314,13 +314,27 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
                                            unsigned long long &my_work,
                                            uint32_t &my_scan,
                                            uint32_t &my_gath,
-                                           uint32_t &my_items) {
+                                           uint32_t &my_items,
+                                           uint32_t &my_rows) {
   constexpr int U = CW <= 2 ? PG_DENSE_UNROLL_NARROW : PG_DENSE_UNROLL_WIDE;
   constexpr bool kPrefetch = CW <= 2;
   constexpr bool kPipe = CW <= 4;  // at 8 words the registers are not there
   const size_t Wp = (size_t)p.Wp;
   const int nch = p.Wp / CW;
-  int64_t c = warp;
+  // the chunks to sweep: all of them, or (a packed batch with a dense list)
+  // those of the graphs in a full sweep; iteration i handles chunk_at(i)
+  const int nd = p.dlist ? ctrl->ndense : 0;
+  const int64_t nchunks = p.dlist ? p.dpref[nd] : p.sell_chunks;
+  auto chunk_at = [&](int64_t i) -> int64_t {
+    if (!p.dlist) return i;
+    int lo = 0, hi = nd - 1;  // the last k with dpref[k] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.dpref[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return __ldg(p.seg_chunk0 + p.dlist[lo]) + (i - p.dpref[lo]);
+  };
+  int64_t ci = warp;
   ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
   int clen_next = 0;
   int64_t off_next = 0;
@@ -330,13 +344,15 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
     for (int q = 0; q < U; ++q)
       u0[q] = q < len_of ? __ldg(p.sell_col + off + lane + 32LL * q) : -1;
   };
-  if (kPrefetch && c < p.sell_chunks) {
+  if (kPrefetch && ci < nchunks) {
+    const int64_t c = chunk_at(ci);
     it_next = p.sell_items[c * 32 + lane];
     clen_next = __ldg(p.sell_len + c);
     off_next = __ldg(p.sell_off + c);
     first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
   }
-  for (; c < p.sell_chunks; c += nwarps) {
+  for (; ci < nchunks; ci += nwarps) {
+    const int64_t c = chunk_at(ci);
     if (!kPrefetch) {
       it_next = p.sell_items[c * 32 + lane];
       clen_next = __ldg(p.sell_len + c);
@@ -345,15 +361,15 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
     const ulonglong2 it = it_next;
     const int clen = clen_next;
     const int32_t *cc = p.sell_col + off_next + lane;
-    const int64_t cn = c + nwarps;
-    const bool has_next = kPrefetch && cn < p.sell_chunks;
+    const bool has_next = kPrefetch && ci + nwarps < nchunks;
+    const int64_t cn = has_next ? chunk_at(ci + nwarps) : 0;
     if (has_next) {
       it_next = p.sell_items[cn * 32 + lane];
       clen_next = __ldg(p.sell_len + cn);
       off_next = __ldg(p.sell_off + cn);
     }
     // a packed batch: only the graphs whose own frontier chose a full sweep
-    if (p.gfsum) {
+    if (p.gfsum && !p.dlist) {
       const int gs = __ldg(p.sell_seg + c);
       if (p.gfsum[(size_t)((ctrl->t - 1) & 1) * (size_t)p.nseg + gs] <= __ldg(p.gthr + gs)) {
         if (has_next) first_batch((int)(it_next.y & 0x7FFFFFFFULL), off_next);
@@ -426,13 +442,17 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
             whole ? (uint32_t)len : (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
         my_mact += deg * pw_words;
         my_work += (unsigned long long)deg * (unsigned long long)pw_seeds;
+        my_rows += pw_words;
       }
     } else if (act) {
       uint32_t deg = 0;
-      if (whole)
+      if (whole) {
         deg = (uint32_t)len;
-      else if (!set_bit(Kcur, v))
+        ++my_rows;
+      } else if (!set_bit(Kcur, v)) {
         deg = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+        ++my_rows;
+      }
       my_mact += deg;
       my_work += (unsigned long long)deg * (unsigned long long)seeds_of(p, v);
     }
@@ -455,6 +475,139 @@ template <int CW>
 struct PullUnroll {
   static constexpr int value = CW <= 2 ? 8 : (CW == 4 ? 4 : 2);
 };
+
+// Buffers of round t, chosen by the round's parity, and the next round's
+// claim bitmaps cleared by the pull (shared by every pull kernel).
+struct RoundBufs {
+  const uint64_t *Dprev;
+  const uint32_t *Cprev;
+  int32_t *F;
+  uint32_t *Ccur, *Kcur, *Kwcur;
+};
+
+__device__ __forceinline__ RoundBufs pull_begin(const Params &p, int t, int64_t gtid,
+                                                int64_t nthreads) {
+  RoundBufs r;
+  r.Dprev = (t & 1) ? p.D0 : p.D1;
+  r.Cprev = (t & 1) ? p.C0 : p.C1;
+  r.F = (t & 1) ? p.F1 : p.F0;
+  r.Ccur = (t & 1) ? p.C1 : p.C0;
+  r.Kcur = (t & 1) ? p.K1 : p.K0;
+  r.Kwcur = (t & 1) ? p.Kw1 : p.Kw0;
+  uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
+  for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
+  if (p.pass_words) {  // the per-pass claim bits of round t+1
+    uint32_t *Kwnext = (t & 1) ? p.Kw0 : p.Kw1;
+    for (int64_t i = gtid; i < p.nbm * p.Wp; i += nthreads) Kwnext[i] = 0u;
+  }
+  return r;
+}
+
+// Sparse (and mixed) rounds: a group of G lanes per piece of the work list
+// the previous post kernel built, UNR arcs per lane issued together.
+template <int CW, int G, bool PW>
+__device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const RoundBufs &rb,
+                                            int lane, int64_t warp, int64_t nwarps,
+                                            uint32_t &my_mact, unsigned long long &my_work,
+                                            uint32_t &my_scan, uint32_t &my_gath,
+                                            uint32_t &my_items, uint32_t &my_rows) {
+  constexpr int UNR = PullUnroll<CW>::value;
+  constexpr int GPW = 32 / G;
+  const uint64_t *Dprev = rb.Dprev;
+  const uint32_t *Cprev = rb.Cprev;
+  int32_t *F = rb.F;
+  uint32_t *Ccur = rb.Ccur;
+  uint32_t *Kwcur = rb.Kwcur;
+  const int gl = lane & (G - 1);
+  const int gw = lane / G;
+  const int64_t nitems = (int64_t)ctrl->nA;
+  const int nch = p.Wp / CW;
+  const size_t Wp = (size_t)p.Wp;
+  constexpr bool kPrefetch = CW <= 2;  // next item loaded during this one
+  ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
+  if (kPrefetch && warp * GPW + gw < nitems) it_next = p.A[warp * GPW + gw];
+  for (int64_t base = warp * GPW; base < nitems; base += nwarps * GPW) {
+    const int64_t item = base + gw;
+    bool act = false, whole = true;
+    int32_t v = 0;
+    int64_t b = 0;
+    int len = 0;
+    if (item < nitems) {
+      const ulonglong2 it = kPrefetch ? it_next : p.A[item];
+      if (kPrefetch && item + nwarps * GPW < nitems) it_next = p.A[item + nwarps * GPW];
+      b = (int64_t)it.x;
+      v = (int32_t)(it.y >> 32);
+      whole = (it.y & 0x80000000ULL) != 0ULL;
+      len = (int)(it.y & 0x7FFFFFFFULL);
+      act = true;
+    }
+    if (gl == 0 && act) {
+      ++my_items;
+      my_scan += (uint32_t)len;
+    }
+    int32_t u[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      const int j = gl + q * G;
+      u[q] = (act && j < len) ? __ldg(p.col + b + j) : -1;
+    }
+    if (p.test_changed) {
+#pragma unroll
+      for (int q = 0; q < UNR; ++q)
+        if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
+    }
+    bool row_changed = false;
+    uint32_t pw_words = 0, pw_seeds = 0;
+    for (int c = 0; c < nch; ++c) {
+      uint64_t own[CW], acc[CW];
+#pragma unroll
+      for (int k = 0; k < CW; ++k) own[k] = acc[k] = 0;
+      if (act && gl == 0 && whole) load_words<CW>(own, p.X + (size_t)v * Wp + c * CW);
+#pragma unroll
+      for (int q = 0; q < UNR; ++q)
+        if (u[q] >= 0) {
+          or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
+          if (c == 0) ++my_gath;
+        }
+#pragma unroll
+      for (int off = G >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < CW; ++k) acc[k] |= __shfl_xor_sync(kFullMask, acc[k], off);
+      }
+      if constexpr (PW)
+        if (act && gl == 0) count_pass_words<CW>(p, v, c, whole, own, acc, Kwcur, pw_words, pw_seeds);
+      if (act && gl == 0) row_changed |= finish_piece<CW>(p, v, c, whole, own, acc);
+    }
+    if (PW && pw_words) {  // passes as words: m_active here, not at the claim
+      const uint32_t deg =
+          whole ? (uint32_t)len : (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+      my_mact += deg * pw_words;
+      my_work += (unsigned long long)deg * (unsigned long long)pw_seeds;
+      my_rows += pw_words;
+    }
+    bool app = false;
+    if (act && gl == 0 && row_changed) {
+      if (whole) {
+        atomicOr(Ccur + (v >> 5), 1u << (v & 31));
+        app = true;
+      } else {
+        app = !set_bit(Ccur, v);
+      }
+    }
+    frontier_append(p, ctrl, F, v, app, lane);
+  }
+}
+
+// Per-block sums of a pull launch's work counters into round t's slot.
+__device__ __forceinline__ void pull_end(const Params &p, Ctrl *ctrl, int t, uint32_t my_mact,
+                                         unsigned long long my_work, uint32_t my_scan,
+                                         uint32_t my_gath, uint32_t my_items, uint32_t my_rows) {
+  RoundStats *r = p.rs + (t - ctrl->row_base);
+  const unsigned long long vals[6] = {my_mact, my_work, my_scan, my_gath, my_items, my_rows};
+  unsigned long long *const dsts[6] = {&r->m_active, &r->work,  &r->scanned,
+                                       &r->gathered, &r->items, &r->rows};
+  block_add<6>(vals, dsts);
+}
 
 // Pull kernel of round t.
 //
@@ -480,124 +633,29 @@ struct PullUnroll {
 template <int CW, int G, bool PW>
 __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL_MIN_BLOCKS_WIDE)
     k_pull(Params p) {
-  constexpr int UNR = PullUnroll<CW>::value;
-  constexpr int GPW = 32 / G;
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
   const int t = ctrl->t;
   const int mode = ctrl->mode;
-  const uint64_t *Dprev = (t & 1) ? p.D0 : p.D1;
-  const uint32_t *Cprev = (t & 1) ? p.C0 : p.C1;
-  int32_t *F = (t & 1) ? p.F1 : p.F0;
-  uint32_t *Ccur = (t & 1) ? p.C1 : p.C0;
-  uint32_t *Kcur = (t & 1) ? p.K1 : p.K0;
-  uint32_t *Knext = (t & 1) ? p.K0 : p.K1;
-  uint32_t *Kwcur = (t & 1) ? p.Kw1 : p.Kw0;
-
   const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * kBlock;
-  for (int64_t i = gtid; i < p.nbm; i += nthreads) Knext[i] = 0u;
-  if constexpr (PW) {  // the per-pass claim bits of round t+1
-    uint32_t *Kwnext = (t & 1) ? p.Kw0 : p.Kw1;
-    for (int64_t i = gtid; i < p.nbm * p.Wp; i += nthreads) Kwnext[i] = 0u;
-  }
-
+  const RoundBufs rb = pull_begin(p, t, gtid, nthreads);
   const int lane = threadIdx.x & 31;
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = nthreads >> 5;
   // per-thread work counters: a thread sees at most tens of thousands of
   // arcs per launch, so 32 bits hold all but the seed-weighted work
-  uint32_t my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0;
+  uint32_t my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0, my_rows = 0;
   unsigned long long my_work = 0;
   // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
   // of the graphs that chose a full sweep and take the others' work list
   if (mode != kModeSparse)
-    pull_dense<CW, PW>(p, ctrl, Dprev, Cprev, F, Ccur, Kcur, Kwcur, lane, warp, nwarps, my_mact,
-                   my_work, my_scan, my_gath, my_items);
-  if (mode != kModeDense) {
-    const int gl = lane & (G - 1);
-    const int gw = lane / G;
-    const int64_t nitems = (int64_t)ctrl->nA;
-    const int nch = p.Wp / CW;
-    const size_t Wp = (size_t)p.Wp;
-    constexpr bool kPrefetch = CW <= 2;  // next item loaded during this one
-    ulonglong2 it_next = make_ulonglong2(0ULL, 0ULL);
-    if (kPrefetch && warp * GPW + gw < nitems) it_next = p.A[warp * GPW + gw];
-    for (int64_t base = warp * GPW; base < nitems; base += nwarps * GPW) {
-      const int64_t item = base + gw;
-      bool act = false, whole = true;
-      int32_t v = 0;
-      int64_t b = 0;
-      int len = 0;
-      if (item < nitems) {
-        const ulonglong2 it = kPrefetch ? it_next : p.A[item];
-        if (kPrefetch && item + nwarps * GPW < nitems) it_next = p.A[item + nwarps * GPW];
-        b = (int64_t)it.x;
-        v = (int32_t)(it.y >> 32);
-        whole = (it.y & 0x80000000ULL) != 0ULL;
-        len = (int)(it.y & 0x7FFFFFFFULL);
-        act = true;
-      }
-      if (gl == 0 && act) {
-        ++my_items;
-        my_scan += (uint32_t)len;
-      }
-      int32_t u[UNR];
-#pragma unroll
-      for (int q = 0; q < UNR; ++q) {
-        const int j = gl + q * G;
-        u[q] = (act && j < len) ? __ldg(p.col + b + j) : -1;
-      }
-      if (p.test_changed) {
-#pragma unroll
-        for (int q = 0; q < UNR; ++q)
-          if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
-      }
-      bool row_changed = false;
-      uint32_t pw_words = 0, pw_seeds = 0;
-      for (int c = 0; c < nch; ++c) {
-        uint64_t own[CW], acc[CW];
-#pragma unroll
-        for (int k = 0; k < CW; ++k) own[k] = acc[k] = 0;
-        if (act && gl == 0 && whole) load_words<CW>(own, p.X + (size_t)v * Wp + c * CW);
-#pragma unroll
-        for (int q = 0; q < UNR; ++q)
-          if (u[q] >= 0) {
-            or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
-            if (c == 0) ++my_gath;
-          }
-#pragma unroll
-        for (int off = G >> 1; off > 0; off >>= 1) {
-#pragma unroll
-          for (int k = 0; k < CW; ++k) acc[k] |= __shfl_xor_sync(kFullMask, acc[k], off);
-        }
-        if constexpr (PW)
-          if (act && gl == 0) count_pass_words<CW>(p, v, c, whole, own, acc, Kwcur, pw_words, pw_seeds);
-        if (act && gl == 0) row_changed |= finish_piece<CW>(p, v, c, whole, own, acc);
-      }
-      if (PW && pw_words) {  // passes as words: m_active here, not at the claim
-        const uint32_t deg =
-            whole ? (uint32_t)len : (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
-        my_mact += deg * pw_words;
-        my_work += (unsigned long long)deg * (unsigned long long)pw_seeds;
-      }
-      bool app = false;
-      if (act && gl == 0 && row_changed) {
-        if (whole) {
-          atomicOr(Ccur + (v >> 5), 1u << (v & 31));
-          app = true;
-        } else {
-          app = !set_bit(Ccur, v);
-        }
-      }
-      frontier_append(p, ctrl, F, v, app, lane);
-    }
-  }
-  RoundStats *r = p.rs + (t - ctrl->row_base);
-  const unsigned long long vals[5] = {my_mact, my_work, my_scan, my_gath, my_items};
-  unsigned long long *const dsts[5] = {&r->m_active, &r->work, &r->scanned, &r->gathered,
-                                       &r->items};
-  block_add<5>(vals, dsts);
+    pull_dense<CW, PW>(p, ctrl, rb.Dprev, rb.Cprev, rb.F, rb.Ccur, rb.Kcur, rb.Kwcur, lane, warp,
+                       nwarps, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
+  if (mode != kModeDense)
+    pull_sparse<CW, G, PW>(p, ctrl, rb, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
+                           my_items, my_rows);
+  pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 
 using PullFn = void (*)(Params);

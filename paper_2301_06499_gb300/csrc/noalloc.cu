@@ -47,7 +47,8 @@ __device__ __forceinline__ uint64_t na_valid(int w, int s) {
 }
 
 // err bits: 1 row_ptr[0] != 0, 2 non-monotone / past m, 4 col out of range,
-// 16 row_ptr[n] != m.
+// 16 row_ptr[n] != m. Rows and arcs are checked by separate grid-stride
+// loops, so a long row does not serialise on one thread.
 __global__ void k_na_validate(const int64_t *rp, const int32_t *col, int64_t n, int64_t m,
                               unsigned long long *hdr) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -56,15 +57,14 @@ __global__ void k_na_validate(const int64_t *rp, const int32_t *col, int64_t n, 
     if (rp[0] != 0) atomicOr(&hdr[0], 1ULL);
     if (rp[n] != m) atomicOr(&hdr[0], 16ULL);
   }
+  bool bad_row = false, bad_col = false;
   for (int64_t v = tid; v < n; v += nth) {
     const int64_t b = rp[v], e = rp[v + 1];
-    if (b > e || b < 0 || e > m) {
-      atomicOr(&hdr[0], 2ULL);
-      continue;
-    }
-    for (int64_t j = b; j < e; ++j)
-      if (col[j] < 0 || col[j] >= n) atomicOr(&hdr[0], 4ULL);
+    bad_row |= b > e || b < 0 || e > m;
   }
+  for (int64_t j = tid; j < m; j += nth) bad_col |= col[j] < 0 || col[j] >= n;
+  if (bad_row) atomicOr(&hdr[0], 2ULL);
+  if (bad_col) atomicOr(&hdr[0], 4ULL);
 }
 
 // Clears the signatures, deltas and the caller's counts; round 0 puts seed
@@ -108,8 +108,13 @@ __global__ void k_na_pull(unsigned long long *sc, const int64_t *rp, const int32
 
 // Round t, one thread per node: d = X ^ Y is the round's new bits; count them
 // per seed into row t, keep them as the deltas of round t, and set X = Y.
+// Per-seed counts gather in shared memory (s <= PG_NOALLOC_MAX_SEEDS) and go
+// to the caller's row with one global add per seed and block.
 __global__ void k_na_post(unsigned long long *sc, int64_t n, int Wp, int s, int t,
                           uint32_t *counts, int count_row) {
+  __shared__ uint32_t cnt[kMaxSeeds];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) cnt[i] = 0u;
+  __syncthreads();
   unsigned long long *base = sc + kHeaderWords + kSeedWords;
   unsigned long long *X = base;
   const unsigned long long *Y = base + (size_t)n * Wp;
@@ -124,15 +129,17 @@ __global__ void k_na_post(unsigned long long *sc, int64_t n, int Wp, int s, int 
       if (!d) continue;
       any = true;
       X[k] = Y[k];
-      if (count_row >= 0) {
-        while (d) {
-          const int bit = __ffsll((long long)d) - 1;
-          atomicAdd(&counts[(size_t)count_row * s + w * 64 + bit], 1u);
-          d &= d - 1ULL;
-        }
+      while (d) {
+        const int bit = __ffsll((long long)d) - 1;
+        atomicAdd(&cnt[w * 64 + bit], 1u);
+        d &= d - 1ULL;
       }
     }
   }
+  __syncthreads();
+  if (count_row >= 0)
+    for (int i = threadIdx.x; i < s; i += blockDim.x)
+      if (cnt[i]) atomicAdd(&counts[(size_t)count_row * s + i], cnt[i]);
   if (any) atomicOr(&sc[1], 1ULL);
 }
 
@@ -191,6 +198,7 @@ extern "C" pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_
     e = cudaMemcpyAsync(sc + kHeaderWords, seeds, sizeof(int32_t) * s, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e);
   k_na_validate<<<blocks, 256, 0, st>>>(row_ptr, col, n, m, sc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
   e = cudaMemcpyAsync(hdr, sc, sizeof(hdr), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e);
@@ -199,11 +207,14 @@ extern "C" pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_
   k_na_init<<<blocks, 256, 0, st>>>(sc, n, W, s, counts, count_words);
   k_na_seed<<<1, 256, 0, st>>>(sc, n, W, s);
   k_na_post<<<blocks, 256, 0, st>>>(sc, n, W, s, 0, counts, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
   int32_t T = 0;
   for (int32_t t = 1;; ++t) {
     k_na_clear_flag<<<1, 1, 0, st>>>(sc);
     k_na_pull<<<blocks, 256, 0, st>>>(sc, row_ptr, col, n, W, t);
     k_na_post<<<blocks, 256, 0, st>>>(sc, n, W, s, t, counts, t <= max_rounds ? t : -1);
+    // a failed launch must not read back as "no change" (a silent PG_OK)
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     e = cudaMemcpyAsync(hdr + 1, sc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);

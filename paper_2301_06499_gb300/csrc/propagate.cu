@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     c->dense_rounds = 0;
     c->row_base = 0;
     c->iters = 0;
+    c->ndense = 0;
     c->nF_prev = 0ULL;
   }
 }
@@ -103,6 +104,10 @@ __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
     bool first = false;
     if (i < sp) {
       x = seeds[i];
+      if (p.perm) {  // the caller's id of a relabelled graph (of its copy k)
+        const int64_t k = (int64_t)x / p.perm_n;
+        x = (int32_t)(k * p.perm_n + __ldg(p.perm + ((int64_t)x - k * p.perm_n)));
+      }
       const int bit = seed_bit ? seed_bit[i] : i;  // a batch: the seed's index in its graph
       atomicOr(reinterpret_cast<unsigned long long *>(p.Y + (size_t)x * p.Wp + (bit >> 6)),
                1ULL << (bit & 63));
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     unsigned long long *gf_next = p.gfsum + (size_t)((t + 1) & 1) * (size_t)p.nseg;
     for (int64_t i = gtid; i < p.nseg; i += nth) gf_next[i] = 0ULL;
   }
-  unsigned long long my_mact = 0, my_work = 0;
+  unsigned long long my_mact = 0, my_work = 0, my_rows = 0;
   if (expand) {
     // one thread per expansion piece of LE out-arcs, UNR arcs at a time
     constexpr int UNR = 4;
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
             if (!p.pass_words) {  // passes as words: the pull counts each pass
               my_mact += (unsigned long long)indeg;
               my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
+              ++my_rows;
             }
             np = (unsigned long long)((indeg + p.L - 1) / p.L);
           }
@@ -450,9 +456,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
   }
   RoundStats *rnext = p.rs + row + 1;
   {
-    const unsigned long long vals[2] = {my_mact, my_work};
-    unsigned long long *const dsts[2] = {&rnext->m_active, &rnext->work};
-    block_add<2>(vals, dsts);
+    const unsigned long long vals[3] = {my_mact, my_work, my_rows};
+    unsigned long long *const dsts[3] = {&rnext->m_active, &rnext->work, &rnext->rows};
+    block_add<3>(vals, dsts);
   }
 
   // C. last block hands over
@@ -463,6 +469,54 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     am_last = atomicAdd(&ctrl->blocks_done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
+  if (am_last && p.dlist) {
+    // a packed batch: the graphs whose frontier chose a full sweep of round
+    // t+1, in graph order, and the prefix of their chunk counts, so that the
+    // next pull walks only their chunks (a finished graph costs nothing)
+    __shared__ long long wsum[kBlock / 32][2];
+    __shared__ long long carry[2];
+    const unsigned long long *gf = p.gfsum + (size_t)(t & 1) * (size_t)p.nseg;
+    const int wl = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+    __syncthreads();
+    for (int g0 = 0; g0 < p.nseg; g0 += kBlock) {
+      const int g = g0 + threadIdx.x;
+      const bool d = g < p.nseg && gf[g] > __ldg(p.gthr + g);
+      long long v[2] = {d ? 1 : 0, d ? (long long)(p.seg_chunk0[g + 1] - p.seg_chunk0[g]) : 0};
+      long long ex[2];
+      for (int k = 0; k < 2; ++k) {
+        long long x = v[k];
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long y = __shfl_up_sync(kFullMask, x, off);
+          if (lane >= off) x += y;
+        }
+        ex[k] = x - v[k];
+        if (lane == 31) wsum[wl][k] = x;
+      }
+      __syncthreads();
+      for (int k = 0; k < 2; ++k) {
+        long long before = carry[k];
+        for (int w = 0; w < wl; ++w) before += wsum[w][k];
+        ex[k] += before;
+      }
+      if (d) {
+        p.dlist[ex[0]] = g;
+        p.dpref[ex[0]] = ex[1];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int w = 0; w < kBlock / 32; ++w) {
+          carry[0] += wsum[w][0];
+          carry[1] += wsum[w][1];
+        }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      p.dpref[carry[0]] = carry[1];
+      ctrl->ndense = (int32_t)carry[0];
+    }
+    __syncthreads();
+  }
   if (am_last && threadIdx.x == 0) {
     __threadfence();
     RoundStats *r = p.rs + row;
@@ -662,6 +716,8 @@ struct Call {
   WindowSink sink = nullptr;
   void *sink_ctx = nullptr;
   std::vector<uint32_t> stage;
+  const int32_t *perm = nullptr;  // relabelled graph: caller id -> internal id
+  int64_t perm_n = 0;
 };
 
 static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_base, int32_t rows,
@@ -700,6 +756,7 @@ static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_ba
       d.items += tmp[i].items;
       d.changed += tmp[i].changed;
       d.fsum += tmp[i].fsum;
+      d.rows += tmp[i].rows;
     }
   }
   return cuda_status(cudaStreamSynchronize(cl.st));
@@ -872,6 +929,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   if (bs && g->nseg > 0) {
     needs.push_back({&w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg});
     needs.push_back({&w.gthr, sizeof(unsigned long long) * (size_t)g->nseg});
+    needs.push_back({&w.dlist, sizeof(int32_t) * (size_t)g->nseg});
+    needs.push_back({&w.dpref, sizeof(int64_t) * ((size_t)g->nseg + 1)});
   }
   if ((rc = carve_workspace(w, needs))) return rc;
   if (!w.ctrl_h) {
@@ -930,6 +989,14 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.gthr = seg ? (const unsigned long long *)w.gthr.p : nullptr;
   p.nseg = seg ? g->nseg : 0;
   p.sell_seg = seg && !pl.wide ? (const int32_t *)g->sell.seg.p : nullptr;
+  // the dense sweep of a packed batch walks only the chunks of the graphs in
+  // a full sweep (dlist, built by the post kernel)
+  const bool dl = seg && !pl.wide && p.sell_chunks > 0 && g->sell.chunk0.p;
+  p.seg_chunk0 = dl ? (const int64_t *)g->sell.chunk0.p : nullptr;
+  p.dlist = dl ? (int32_t *)w.dlist.p : nullptr;
+  p.dpref = dl ? (int64_t *)w.dpref.p : nullptr;
+  p.perm = cl.perm;
+  p.perm_n = cl.perm_n;
   p.rs = (RoundStats *)w.rs.p;
   p.ctrl = (Ctrl *)w.ctrl.p;
   p.max_rounds = cl.max_rounds;
@@ -1227,6 +1294,8 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
   cl.counts_h = out->counts;
+  cl.perm = g->perm_ptr;
+  cl.perm_n = g->n;
   const int planes =
       s_mode ? (cl.o.planes_per_pass > 0 ? std::min(cl.o.planes_per_pass, 64) : 64) : s;
   const int npasses = (s + planes - 1) / planes;
@@ -1276,6 +1345,8 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
       cr.s_total = s;
       cr.max_rounds = cl.max_rounds;
       cr.counts_h = cl.counts_h;
+      cr.perm = cl.perm;
+      cr.perm_n = cl.perm_n;
       int64_t rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ns));
       if (cl.o.window_rows > 0) rows = cl.o.window_rows;
       cr.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)out->max_rounds + 1, rows));
@@ -1300,6 +1371,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
         d.items += x.items;
         d.changed += x.changed;
         d.fsum += x.fsum;
+        d.rows += x.rows;
       }
       // rows that only some groups reached: the others' columns are zero there
       if (po.rounds < T) {
@@ -1362,6 +1434,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
     st.items += r.items;
     st.changed_rows += r.changed;
     st.frontier_arcs += r.fsum;
+    st.active_rows += r.rows;
   }
   st.sweeps = T + 1;
   st.passes = passes;
@@ -1405,6 +1478,8 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
   cl.counts_h = nullptr;
   cl.sink = sink;
   cl.sink_ctx = sink_ctx;
+  cl.perm = g->perm_ptr;
+  cl.perm_n = g->n;
   int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ncols));
   if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
   cl.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
@@ -1428,6 +1503,7 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
     st.items += r.items;
     st.changed_rows += r.changed;
     st.frontier_arcs += r.fsum;
+    st.active_rows += r.rows;
   }
   st.sweeps = po.rounds + 1;
   st.passes = 1;

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
   const int64_t nwarps = nthreads >> 5;
   const int Wp = p.Wp;
   const int passes = NW > 0 ? 1 : (Wp + 32 * R - 1) / (32 * R);
-  unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0;
+  unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0,
+                     my_rows = 0;
   // dense: every row's pieces; sparse: the claimed pieces; mixed (a packed
   // batch): the pieces of graphs that chose a full sweep, then the claimed ones
   const int64_t ndense = mode != kModeSparse ? p.nPall : 0;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
                   : (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
         my_mact += deg * pw_words;
         my_work += deg * pw_seeds;
+        my_rows += pw_words;
       }
     }
     bool app = false;
@@ -155,10 +157,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
       my_scan += (unsigned long long)len;
       if (!PW && dense && any_delta) {  // active in round t (sparse rounds count at the claim)
         unsigned long long deg = 0;
-        if (whole)
+        if (whole) {
           deg = (unsigned long long)len;
-        else if (!set_bit(Kcur, v))
+          ++my_rows;
+        } else if (!set_bit(Kcur, v)) {
           deg = (unsigned long long)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+          ++my_rows;
+        }
         my_mact += deg;
         my_work += deg * (unsigned long long)seeds_of(p, v);
       }
@@ -174,10 +179,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
     frontier_append(p, ctrl, F, v, app, lane);
   }
   RoundStats *r = p.rs + (t - ctrl->row_base);
-  const unsigned long long vals[5] = {my_mact, my_work, my_scan, my_gath, my_items};
-  unsigned long long *const dsts[5] = {&r->m_active, &r->work, &r->scanned, &r->gathered,
-                                       &r->items};
-  block_add<5>(vals, dsts);
+  const unsigned long long vals[6] = {my_mact, my_work, my_scan, my_gath, my_items, my_rows};
+  unsigned long long *const dsts[6] = {&r->m_active, &r->work,  &r->scanned,
+                                       &r->gathered, &r->items, &r->rows};
+  block_add<6>(vals, dsts);
 }
 
 template <bool PW>

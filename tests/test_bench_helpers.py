@@ -50,3 +50,12 @@ def test_write_traffic_from_ncu_csv(tmp_path):
     assert stored == out
     assert stored["bytes_per_launch"]["k_pull<4, 16, 1>"] == 500e6  # mean of 400 and 600 MB
     assert stored["kernel_hash"]["k_pull<4, 16, 1>"] == bench.kernel_hash("k_pull<4, 16, 1>")
+
+
+def test_round_bytes_follow_the_per_round_formula():
+    """|A|(8 + 2 s/8) + m_active (4 + s/8) + |F| 4 for PROPAGATE-P; per pass of
+    64 planes (8-byte signatures) for PROPAGATE-S."""
+    st = {"active_rows": 10, "m_active_total": 100, "changed_rows": 7}
+    assert bench.round_bytes(st, 512, False) == 10 * (8 + 128) + 100 * (4 + 64) + 7 * 4
+    assert bench.round_bytes(st, 512, True) == 10 * (8 + 16) + 100 * (4 + 8) + 7 * 4
+    assert bench.round_bytes(st, 32, True) == 10 * (8 + 8) + 100 * (4 + 4) + 7 * 4

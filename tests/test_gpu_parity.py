@@ -322,3 +322,111 @@ def test_graph_create_free_cycles():
             assert r.rounds == w["rounds"] and np.array_equal(r.counts, w["counts"])
             assert np.array_equal(rs.counts, w["counts"])
             G.close()
+
+
+# ------------------------------------------------------------- relabelling
+@functools.lru_cache(maxsize=None)
+def _relabel_cases():
+    return [
+        (I.rmat(12, 8, 151, directed=True), 130, 152),
+        (I.rmat(13, 16, 153, directed=False), 512, 154),
+        (I.star(5000), 65, 155),
+        (I.grid(90, 70, 0.05, 156), 64, 157),
+        (I.er(3000, 6, 158), 257, 159),
+        (I.path(1500), 3, 160),
+    ]
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_relabel_gives_identical_counts(case):
+    """PG_RELABEL renumbers the nodes internally (hubs first); seeds go in and
+    counts come out in the caller's ids and order, so counts, m_active and
+    metrics equal the oracle's on the graph as given, for P, S and every
+    direction."""
+    g, s, sd = _relabel_cases()[case]
+    seeds = I.seeds(g.n, s, sd)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g, relabel=True)
+    assert G.relabelled
+    for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+        res = pg.propagate_p(G, seeds, opts=pg.options(direction=direction))
+        _assert_same(res, want)
+    _assert_metrics(res, want["metrics"], g.n)
+    res_s = pg.propagate_s(G, seeds)
+    assert res_s.rounds == want["rounds"] and np.array_equal(res_s.counts, want["counts"])
+    assert np.array_equal(res_s.m_active,
+                          _oracle_s_mactive(g, seeds, 64, want["rounds"])[:res_s.m_active.size])
+
+
+def test_relabel_with_reverse_and_graph_copies():
+    """A relabelled directed graph pulled over its transpose (PG_REVERSE), and
+    PROPAGATE-S passes run over copies of a relabelled graph (each copy's
+    seeds mapped through the same permutation)."""
+    g = I.rmat(12, 8, 91, directed=True)
+    seeds = I.seeds(g.n, 100, 92)
+    want = oracle.run(_transpose(g), seeds)
+    G = pg.Graph.from_inputs(g, reverse=True, relabel=True)
+    res = pg.propagate_p(G, seeds)
+    assert res.rounds == want["rounds"] and np.array_equal(res.counts, want["counts"])
+    g2 = I.rmat(11, 8, 161, directed=False)
+    s2 = I.seeds(g2.n, 200, 162)
+    want2 = _oracle_p(g2, s2)
+    G2 = pg.Graph.from_inputs(g2, relabel=True)
+    r2 = pg.propagate_s(G2, s2, opts=pg.options(planes_per_pass=16, passes_together=4))
+    assert r2.rounds == want2["rounds"] and np.array_equal(r2.counts, want2["counts"])
+
+
+def test_relabel_default_follows_the_degree_skew():
+    """By default a large skewed graph (R-MAT) is relabelled and a lattice is
+    not; PG_KEEP_ORDER turns it off; the counts are the same either way."""
+    g = I.rmat(17, 8, 171, directed=False)
+    seeds = I.seeds(g.n, 128, 172)
+    G = pg.Graph.from_inputs(g)
+    K = pg.Graph.from_inputs(g, relabel=False)
+    assert G.relabelled and not K.relabelled
+    a, b = pg.propagate_p(G, seeds), pg.propagate_p(K, seeds)
+    assert a.rounds == b.rounds and np.array_equal(a.counts, b.counts)
+    assert np.array_equal(a.m_active, b.m_active)
+    h, _ = oracle.seed_histograms(g, seeds[:8])
+    assert np.array_equal(a.counts[:h.shape[1], :8].T, h.astype(np.uint32))
+    assert not a.counts[h.shape[1]:, :8].any()
+    grid = I.grid(400, 300, 0.05, 173)
+    assert not pg.Graph.from_inputs(grid).relabelled
+
+
+def _active_rows_from_distances(g, seeds):
+    """|A_t| per round from the oracle's BFS distances: rows with a zero bit
+    before round t and an in-neighbour at distance t-1 from some seed (the
+    rows whose in-degrees m_active sums)."""
+    hist, _, dmat = oracle.seed_histograms(g, seeds, with_distances=True)
+    T = hist.shape[1] - 1
+    rp, col = np.asarray(g.row_ptr), np.asarray(g.col)
+    deg = np.diff(rp)
+    rows = np.repeat(np.arange(g.n), deg)
+    out = np.zeros(T + 2, dtype=np.int64)
+    for t in range(1, T + 2):
+        changed = (dmat == t - 1).any(axis=1)
+        unsat = ((dmat > t - 1) | (dmat < 0)).any(axis=1)
+        hit = np.zeros(g.n, dtype=bool)
+        hit[rows[changed[col]]] = True
+        out[t] = int((hit & unsat).sum())
+    return out
+
+
+@pytest.mark.parametrize("which", ["er", "rmat_directed", "grid"])
+def test_active_rows_match_distances(which):
+    """pg_stats.active_rows (the |A_t| of the per-round byte count) equals the
+    count restated from the oracle's distances, in every direction."""
+    if which == "er":
+        g, seeds = _cfg1()[0], _cfg1()[1]
+    elif which == "rmat_directed":
+        g = I.rmat(12, 8, 181, directed=True)
+        seeds = I.seeds(g.n, 130, 182)
+    else:
+        g = I.grid(60, 50, 0.05, 183)
+        seeds = I.seeds(g.n, 64, 184)
+    want = int(_active_rows_from_distances(g, seeds).sum())
+    G = pg.Graph.from_inputs(g)
+    for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+        pg.propagate_p(G, seeds, opts=pg.options(direction=direction))
+        assert G.last_stats()["active_rows"] == want, direction
