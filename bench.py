@@ -51,6 +51,12 @@ WORKLOADS = {
                       "4096x4096 grid, 5% edges deleted, s=128"),
     "rmat26_undirected_s512": (dict(kind="rmat", scale=26, ef=16, seed=2, directed=False), 512,
                                "undirected R-MAT scale 26, edge factor 16, s=512"),
+    # the same graph with its arc arrays in pinned host memory, read over the
+    # CPU-GPU link (PG_HOST_CSR): the out-of-core configuration
+    "rmat26_undirected_s512_hostcsr": (dict(kind="rmat", scale=26, ef=16, seed=2, directed=False,
+                                            host_csr=True), 512,
+                                       "undirected R-MAT scale 26, edge factor 16, s=512, arc "
+                                       "arrays in host memory"),
     "rmat23_undirected_s512": (dict(kind="rmat", scale=23, ef=16, seed=2, directed=False), 512,
                                "undirected R-MAT scale 23, edge factor 16, s=512 (profiling "
                                "stand-in for scale 26)"),
@@ -81,7 +87,8 @@ SERVE_WORKLOADS = {
                         variants=4),
 }
 SEED_RNG = {"rmat22_directed_s256": 2, "er1e4_s64": 1, "grid4096_s128": 3,
-            "rmat26_undirected_s512": 2, "rmat23_undirected_s512": 2, "er1e6_s5568": 7,
+            "rmat26_undirected_s512": 2, "rmat26_undirected_s512_hostcsr": 2,
+            "rmat23_undirected_s512": 2, "er1e6_s5568": 7,
             "exact_er1e5": 9, "exact_er3e4": 9}
 
 
@@ -222,7 +229,7 @@ DEFAULT_WORKLOAD = "rmat26_undirected_s512"
 BATCH_STEPS = 3
 # seeds of the oracle's timed sample per workload (one BFS per host thread;
 # the scale-26 graph takes seconds per BFS): default 64
-CPU_SEEDS = {"rmat26_undirected_s512": 16}
+CPU_SEEDS = {"rmat26_undirected_s512": 16, "rmat26_undirected_s512_hostcsr": 16}
 
 
 def run_ours(args):
@@ -245,7 +252,8 @@ def run_ours(args):
     seeds = I.seeds(g.n, s, seed_stream(args.workload, rank))
     stream = torch.cuda.current_stream()
     sptr = __import__("ctypes").c_void_p(stream.cuda_stream)
-    G = pg.Graph.from_inputs(g, stream=sptr)
+    host_csr = bool(spec.get("host_csr", False))
+    G = pg.Graph.from_inputs(g, stream=sptr, host_csr=host_csr)
     # schedule options: the library's autotuner picks them for this graph and
     # these seeds (untimed; counts are checked identical across candidates)
     tuned = None
@@ -340,7 +348,8 @@ def run_ours(args):
     for _ in range(max(1, min(args.steps, args.e2e_steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G2 = pg.Graph.from_csr(rp_pinned, col_pinned, g.n, directed=g.directed, stream=sptr)
+        G2 = pg.Graph.from_csr(rp_pinned, col_pinned, g.n, directed=g.directed, stream=sptr,
+                               host_csr=host_csr)
         r1 = pg.propagate_p(G2, seeds, opts=opts_run_p, stream=sptr)
         r2 = pg.propagate_s(G2, seeds, opts=opts_run_s, stream=sptr)
         pg.metrics(r1, g.n)

@@ -75,6 +75,13 @@ typedef struct pg_graph pg_graph;
                              nodes whose largest in-degree is at least 16
                              times the mean (skewed, power-law degrees) */
 #define PG_KEEP_ORDER 16u /* never relabel */
+#define PG_HOST_CSR 32u   /* keep the arc arrays (column indices, the out-edge
+                             transpose's, and the dense rounds' sliced-ELL
+                             copy) in pinned host memory, read by the kernels
+                             over the CPU-GPU link, so that a graph whose
+                             arcs exceed device memory can still run: only
+                             row pointers, signatures, bitmaps and lists
+                             stay on the device. Not with PG_BORROW */
 
 /*
  * Per-round, per-seed counts. Caller-owned host buffers.
@@ -119,8 +126,11 @@ typedef struct {
                                gained in the previous round (its delta, zero
                                if u did not change). 1: test u's changed bit
                                before reading its delta; 2: always read the
-                               delta; 0 (auto): test when the deltas exceed
-                               64 MiB (n x words per row x 8 bytes) */
+                               delta; 3: decide per round, testing while the
+                               previous round's frontier out-arcs are below
+                               half of all arcs; 0 (auto): 3 when the deltas
+                               exceed 64 MiB (n x words per row x 8 bytes),
+                               else 2 (a packed batch: 1 instead of 3) */
   int32_t planes_per_pass;  /* PROPAGATE-S: seeds per pass, 1..64; 0 = 64 */
   int32_t use_graphs;       /* 1: the round loop is one CUDA graph with a
                                device-driven while node (no host round trip
@@ -159,6 +169,15 @@ typedef struct {
                                bytes; copies of the graph (passes_together)
                                then serve only passes of fewer planes or an
                                explicit passes_together > 1 */
+  int32_t tma_gather;       /* dense rounds of rows of 4 or 8 words (s of 129
+                               to 512, or PROPAGATE-S passes as 4 or 8
+                               words): 2 = the neighbours' delta rows are
+                               copied into shared memory by the tensor memory
+                               accelerator (four rows per tile::gather4 copy,
+                               several steps in flight per warp) instead of
+                               loaded by each lane; 0 or 1 = per-lane loads
+                               (the default: they measured faster on a 2^26-
+                               node graph with 8-word rows) */
 } pg_options;
 
 #define PG_DIR_AUTO 0
@@ -236,7 +255,8 @@ typedef struct {
   int32_t pass_words;        /* PROPAGATE-S: passes run side by side as the
                                 words of one signature (the pull instantiation
                                 k_pull<words, lanes, 1>); 1 otherwise */
-  int32_t reserved;
+  int32_t dense_tma;         /* 1 if dense rounds gathered deltas by TMA
+                                (k_pull_tma<words, pass_words>) */
   uint64_t active_rows;      /* sum over rounds of |A_t|, the rows a round had
                                 to revisit (those m_active sums the in-degrees
                                 of); PROPAGATE-S: summed over passes */

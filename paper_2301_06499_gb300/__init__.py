@@ -73,7 +73,8 @@ class Graph:
 
     @classmethod
     def from_csr(cls, row_ptr, col, n: int | None = None, directed: bool = True,
-                 stream=None, reverse: bool = False, relabel: bool | None = None) -> "Graph":
+                 stream=None, reverse: bool = False, relabel: bool | None = None,
+                 host_csr: bool = False) -> "Graph":
         """row_ptr int64[n+1] and col int32[m] as numpy arrays (copied from the
         host) or CUDA torch tensors (used in place). reverse=True counts balls
         grown backward (nodes reaching each seed; PG_REVERSE). relabel: True =
@@ -81,11 +82,13 @@ class Graph:
         rev = _abi.PG_REVERSE if reverse else 0
         if relabel is not None:
             rev |= _abi.PG_RELABEL if relabel else _abi.PG_KEEP_ORDER
+        if host_csr:  # arc arrays in pinned host memory (PG_HOST_CSR)
+            rev |= _abi.PG_HOST_CSR
         L = _abi.lib()
         h = ctypes.c_void_p()
         st = stream if stream is not None else _current_stream()
         keep = None
-        if hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda:
+        if hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda and not host_csr:
             import torch
             rp = row_ptr.to(torch.int64).contiguous()
             cl = col.to(torch.int32).contiguous()
@@ -107,10 +110,10 @@ class Graph:
 
     @classmethod
     def from_inputs(cls, g, stream=None, reverse: bool = False,
-                    relabel: bool | None = None) -> "Graph":
+                    relabel: bool | None = None, host_csr: bool = False) -> "Graph":
         """From a generated graph (``inputs.Graph``) held in host memory."""
         return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream,
-                            reverse=reverse, relabel=relabel)
+                            reverse=reverse, relabel=relabel, host_csr=host_csr)
 
     @property
     def relabelled(self) -> bool:

@@ -6,6 +6,7 @@ library. Loading fails loudly if the library cannot be built or found.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 from . import build as _build
@@ -20,6 +21,7 @@ PG_BORROW = 2
 PG_REVERSE = 4
 PG_RELABEL = 8
 PG_KEEP_ORDER = 16
+PG_HOST_CSR = 32
 PG_DIR_AUTO, PG_DIR_DENSE, PG_DIR_SPARSE = 0, 1, 2
 PG_ALG_P, PG_ALG_S = 0, 1
 
@@ -31,7 +33,7 @@ class Options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("window_rows", ctypes.c_int32), ("words_per_thread", ctypes.c_int32),
                 ("wide_rows", ctypes.c_int32), ("passes_together", ctypes.c_int32),
-                ("pass_words", ctypes.c_int32)]
+                ("pass_words", ctypes.c_int32), ("tma_gather", ctypes.c_int32)]
 
 
 class Counts(ctypes.Structure):
@@ -59,7 +61,7 @@ class Stats(ctypes.Structure):
                 ("ms_init", ctypes.c_double), ("pull_launches", ctypes.c_int32),
                 ("post_launches", ctypes.c_int32), ("test_changed", ctypes.c_int32),
                 ("words_per_gather", ctypes.c_int32), ("seed_edge_traversals", ctypes.c_uint64),
-                ("pass_words", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pass_words", ctypes.c_int32), ("dense_tma", ctypes.c_int32),
                 ("active_rows", ctypes.c_uint64)]
 
 
@@ -160,11 +162,13 @@ _lib = None
 
 
 def lib():
-    """The loaded CUDA library (built in-tree on first use if missing)."""
+    """The loaded CUDA library (built in-tree on first use if missing). The
+    environment variable PG_LIBRARY_VARIANT=debug-bounds selects the build
+    whose gathers check their indices."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(variant=os.environ.get("PG_LIBRARY_VARIANT", ""))
             L = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(L, name)

@@ -19,6 +19,16 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpropagate.so")
+# variants: name -> (library file suffix, extra nvcc flags)
+VARIANTS = {"": ("", []),
+            # every gather checks its row and word index and records a bad one
+            # in the control block instead of faulting (the call returns
+            # PG_EDEVICE)
+            "debug-bounds": ("_debug_bounds", ["-DPG_DEBUG_BOUNDS"])}
+
+
+def lib_path(variant: str = "") -> str:
+    return os.path.join(OUT_DIR, f"libpropagate{VARIANTS[variant][0]}.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,22 +47,25 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(variant: str = "") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: list | None = None,
+          variant: str = "") -> str:
+    lib = lib_path(variant)
+    if not force and up_to_date(variant):
+        return lib
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    obj_dir = os.path.join(OUT_DIR, "obj" + VARIANTS[variant][0])
     os.makedirs(obj_dir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                     "-I", CSRC] + (extra or [])
+                     "-I", CSRC] + VARIANTS[variant][1] + (extra or [])
 
     def compile_one(src):
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
@@ -69,16 +82,17 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     verbose = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
-    print(build(force=True, verbose=verbose or bool(extra), extra=extra))
+    variant = "debug-bounds" if "--debug-bounds" in sys.argv else ""
+    print(build(force=True, verbose=verbose or bool(extra), extra=extra, variant=variant))

@@ -40,6 +40,8 @@ struct Ctrl {
   int32_t row_base;      // round held in row 0 of the device counts window
   int32_t iters;         // post launches of this pass (termination guard)
   int32_t ndense;        // packed batch: graphs swept whole in round t (in dlist)
+  int32_t test;          // round t tests changed bits before gathers (per-round mode)
+  int32_t bad_index;     // PG_DEBUG_BOUNDS builds: a gather's index was out of range
   unsigned long long nF_prev;  // |F_{t-1}|
 };
 
@@ -56,6 +58,12 @@ struct RoundStats {
 };
 
 // Everything the round kernels need, passed by value.
+// Per-round test of changed bits: a round tests them while the previous
+// round's frontier out-arcs are below this fraction of all arcs (a random
+// bitmap sector then costs less than gathering the zero deltas of the
+// in-neighbours that did not change).
+constexpr double kTestDensity = 0.5;
+
 struct Params {
   int64_t n, m;
   const int64_t *row_ptr;  // in-CSR
@@ -115,6 +123,8 @@ struct Params {
   float dense_threshold;
   int32_t row_cap;      // rows of the device counts window
   int32_t test_changed; // test C_{t-1} before gathering an in-neighbour's delta
+  int32_t test_adapt;   // decide test_changed per round (ctrl->test, set by the post kernel)
+  int32_t dense_tma;    // dense rounds are swept by k_pull_tma (launched before k_pull)
   int32_t use_cond;     // launched inside a conditional while-graph
   int32_t iter_guard;   // post launches after which a pass is abandoned
   unsigned long long cond;  // cudaGraphConditionalHandle of that graph

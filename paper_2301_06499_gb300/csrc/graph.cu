@@ -17,10 +17,16 @@ pg_status cuda_status(cudaError_t e) {
 
 pg_status ensure(DevBuf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  if (b.bytes >= bytes) return PG_OK;
-  if (b.p) cudaFree(b.p);
+  if (b.bytes >= bytes && !b.host) return PG_OK;
+  if (b.p) {
+    if (b.host)
+      cudaFreeHost(b.p);
+    else
+      cudaFree(b.p);
+  }
   b.p = nullptr;
   b.bytes = 0;
+  b.host = false;
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -31,10 +37,44 @@ pg_status ensure(DevBuf &b, size_t bytes) {
   return PG_OK;
 }
 
+pg_status ensure_host(DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes && b.host) return PG_OK;
+  release(b);
+  cudaError_t e = cudaMallocHost(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return cuda_status(e);
+  }
+  b.bytes = bytes;
+  b.host = true;
+  return PG_OK;
+}
+
 void release(DevBuf &b) {
-  if (b.p) cudaFree(b.p);
+  if (b.p) {
+    if (b.host)
+      cudaFreeHost(b.p);
+    else
+      cudaFree(b.p);
+  }
   b.p = nullptr;
   b.bytes = 0;
+  b.host = false;
+}
+
+// Arc arrays of a graph: device memory, or pinned host memory (PG_HOST_CSR).
+static cudaError_t alloc_arcs(void **p, size_t bytes, bool host) {
+  return host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+}
+
+static void free_arcs(void *p, bool host) {
+  if (!p) return;
+  if (host)
+    cudaFreeHost(p);
+  else
+    cudaFree(p);
 }
 
 int sm_count() {
@@ -455,7 +495,10 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
     rc = cuda_status(cudaMemcpyAsync(&slots, (int64_t *)sl.off.p + nchunks, sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, st));
   if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
-  if (rc == PG_OK) rc = ensure(sl.col, sizeof(int32_t) * (size_t)std::max<int64_t>(slots, 1));
+  if (rc == PG_OK) {
+    const size_t cb = sizeof(int32_t) * (size_t)std::max<int64_t>(slots, 1);
+    rc = g->host_csr ? ensure_host(sl.col, cb) : ensure(sl.col, cb);
+  }
   if (rc == PG_OK) {
     k_sell_fill<<<grid_for(nchunks * 32), kBlock, 0, st>>>(
         (const ulonglong2 *)sl.items.p, nchunks, (const int32_t *)sl.len.p,
@@ -480,7 +523,8 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
 static std::vector<DevBuf *> workspace_parts(Workspace &w) {
   return {&w.X,  &w.Y,  &w.D0,     &w.D1, &w.C0,   &w.C1,   &w.K0,    &w.K1,
           &w.Sat, &w.RB, &w.KW0,   &w.KW1, &w.F0,  &w.F1,   &w.E,     &w.A,
-          &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum, &w.gthr};
+          &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum, &w.gthr,
+          &w.dlist, &w.dpref};
 }
 
 pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, size_t>> &needs) {
@@ -684,7 +728,9 @@ static pg_status relabel_by_degree(pg_graph *g, cudaStream_t st) {
   if (!rc) rc = cuda_status(cudaMallocAsync((void **)&H, sizeof(int64_t) * (size_t)(tiles * kRelabelBuckets), st));
   if (!rc) rc = cuda_status(cudaMallocAsync((void **)&old_of, sizeof(int32_t) * (size_t)n, st));
   if (!rc) rc = cuda_status(cudaMalloc((void **)&nrp, sizeof(int64_t) * (size_t)(n + 1)));
-  if (!rc) rc = cuda_status(cudaMalloc((void **)&ncol, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1)));
+  if (!rc)
+    rc = cuda_status(alloc_arcs((void **)&ncol, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1),
+                                g->host_csr));
   if (!rc) {
     k_relabel_hist<<<(unsigned)tiles, kBlock, 0, st>>>(g->row_ptr, n, tiles, H);
     rc = cuda_status(cudaGetLastError());
@@ -707,16 +753,17 @@ static pg_status relabel_by_degree(pg_graph *g, cudaStream_t st) {
   if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
   if (rc) {
     if (nrp) cudaFree(nrp);
-    if (ncol) cudaFree(ncol);
+    free_arcs(ncol, g->host_csr);
     release(g->perm);
     return rc;
   }
   if (g->owns_in) {
     cudaFree(g->row_ptr);
-    cudaFree(g->col);
+    free_arcs(g->col, g->col_host);
   }
   g->row_ptr = nrp;
   g->col = ncol;
+  g->col_host = g->host_csr;
   g->owns_in = true;
   return PG_OK;
 }
@@ -834,11 +881,11 @@ const char *pg_strerror(pg_status st) {
 static void free_graph_arrays(pg_graph *g) {
   if (g->owns_in) {
     if (g->row_ptr) cudaFree(g->row_ptr);
-    if (g->col) cudaFree(g->col);
+    free_arcs(g->col, g->col_host);
   }
   if (g->owns_out && g->out_ptr != g->row_ptr) {
     if (g->out_ptr) cudaFree(g->out_ptr);
-    if (g->out_col) cudaFree(g->out_col);
+    free_arcs(g->out_col, g->out_col_host);
   }
   g->row_ptr = g->out_ptr = nullptr;
   g->col = g->out_col = nullptr;
@@ -883,11 +930,13 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
       (m > 0 && !col))
     return PG_EINVAL;
   if ((flags & PG_BORROW) && !(flags & PG_DEVICE_PTRS)) return PG_EINVAL;
+  if ((flags & PG_HOST_CSR) && (flags & PG_BORROW)) return PG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   pg_graph *g = new pg_graph();
   g->n = n;
   g->m = m;
   g->directed = directed ? 1 : 0;
+  g->host_csr = (flags & PG_HOST_CSR) != 0;
   cudaGetDevice(&g->device);
   pg_status rc = PG_OK;
   const bool dev = flags & PG_DEVICE_PTRS;
@@ -897,10 +946,15 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
     g->owns_in = false;
   } else {
     rc = cuda_status(cudaMalloc((void **)&g->row_ptr, sizeof(int64_t) * (n + 1)));
-    if (rc == PG_OK) rc = cuda_status(cudaMalloc((void **)&g->col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
-    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (rc == PG_OK)
-      rc = cuda_status(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, st));
+      rc = cuda_status(alloc_arcs((void **)&g->col, sizeof(int32_t) * std::max<int64_t>(m, 1),
+                                  g->host_csr));
+    g->col_host = g->host_csr;
+    cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (g->host_csr) kind = cudaMemcpyDefault;
+    if (rc == PG_OK)
+      rc = cuda_status(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1),
+                                       g->host_csr ? cudaMemcpyDefault : kind, st));
     if (rc == PG_OK && m > 0)
       rc = cuda_status(cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, kind, st));
   }
@@ -952,7 +1006,10 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
       g->owns_out = false;
     } else {
       rc = cuda_status(cudaMalloc((void **)&g->out_ptr, sizeof(int64_t) * (n + 1)));
-      if (rc == PG_OK) rc = cuda_status(cudaMalloc((void **)&g->out_col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+      if (rc == PG_OK)
+        rc = cuda_status(alloc_arcs((void **)&g->out_col,
+                                    sizeof(int32_t) * std::max<int64_t>(m, 1), g->host_csr));
+      g->out_col_host = g->host_csr;
       unsigned long long *cursor = nullptr;
       if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&cursor, sizeof(unsigned long long) * n, st));
       if (rc == PG_OK) {
@@ -981,6 +1038,7 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
     std::swap(g->row_ptr, g->out_ptr);
     std::swap(g->col, g->out_col);
     std::swap(g->owns_in, g->owns_out);
+    std::swap(g->col_host, g->out_col_host);
     release(g->pieces.list);  // built over the other side for the transpose
     g->pieces.L = 0;
     unsigned long long *mx2 = nullptr;

@@ -15,6 +15,7 @@ namespace pg {
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  bool host = false;  // pinned host memory the device reads over C2C (ensure_host)
 };
 
 // The buffers of a propagation, carved out of one device allocation (arena)
@@ -65,6 +66,10 @@ struct pg_graph {
   int32_t *out_col = nullptr;
   bool owns_in = true;
   bool owns_out = true;
+  // PG_HOST_CSR: the arc arrays (col, out_col and the sliced-ELL copy's
+  // columns) live in pinned host memory and are read over C2C
+  bool host_csr = false;
+  bool col_host = false, out_col_host = false;
   bool owns_sell = true;  // false in a view (make_view)
   // a packed batch: the graph of each node (device, borrowed) and how many
   const int32_t *seg_of = nullptr;
@@ -93,6 +98,8 @@ namespace pg {
 
 // Grow-only device buffer; contents are not preserved on growth.
 pg_status ensure(DevBuf &b, size_t bytes);
+// The same in pinned host memory, mapped into the device's address space.
+pg_status ensure_host(DevBuf &b, size_t bytes);
 void release(DevBuf &b);
 // Frees every buffer, event and pinned block of a workspace.
 void release_workspace(Workspace &w);

@@ -22,6 +22,29 @@
 
 namespace pg {
 
+// Whether round t tests an in-neighbour's changed bit before gathering its
+// delta: fixed for the call, or decided per round by the post kernel.
+__device__ __forceinline__ bool test_changed_now(const Params &p, const Ctrl *ctrl) {
+  return p.test_adapt ? ctrl->test != 0 : p.test_changed != 0;
+}
+
+// Bounds of a gathered row u and word w. A build with -DPG_DEBUG_BOUNDS
+// checks every gather (0 <= u < n, 0 <= w < Wp): an index out of range is
+// recorded in the control block (the call then returns PG_EDEVICE) and the
+// gather is skipped instead of faulting. Other builds check nothing.
+__device__ __forceinline__ bool gather_ok(const Params &p, int64_t u, int w) {
+#ifdef PG_DEBUG_BOUNDS
+  if (u >= 0 && u < p.n && w >= 0 && w < p.Wp) return true;
+  atomicExch(&p.ctrl->bad_index, 1);
+  return false;
+#else
+  (void)p;
+  (void)u;
+  (void)w;
+  return true;
+#endif
+}
+
 __device__ __forceinline__ bool test_bit(const uint32_t *bm, int64_t v) {
   return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
 }
@@ -317,6 +340,7 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
                                            uint32_t &my_items,
                                            uint32_t &my_rows) {
   constexpr int U = CW <= 2 ? PG_DENSE_UNROLL_NARROW : PG_DENSE_UNROLL_WIDE;
+  const bool tc = test_changed_now(p, ctrl);
   constexpr bool kPrefetch = CW <= 2;
   constexpr bool kPipe = CW <= 4;  // at 8 words the registers are not there
   const size_t Wp = (size_t)p.Wp;
@@ -408,7 +432,7 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
           for (int q = 0; q < U; ++q)
             un[q] = (act && k0 + U + q < len) ? __ldg(cc + 32LL * (k0 + U + q)) : -1;
         }
-        if (p.test_changed) {
+        if (tc) {
 #pragma unroll
           for (int q = 0; q < U; ++q)
             if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
@@ -416,7 +440,8 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
 #pragma unroll
         for (int q = 0; q < U; ++q)
           if (u[q] >= 0) {
-            or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
+            if (gather_ok(p, u[q], ch * CW + CW - 1))
+              or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + ch * CW);
             if (ch == 0) ++my_gath;
           }
         if (more) {
@@ -513,6 +538,7 @@ __device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const R
                                             uint32_t &my_items, uint32_t &my_rows) {
   constexpr int UNR = PullUnroll<CW>::value;
   constexpr int GPW = 32 / G;
+  const bool tc = test_changed_now(p, ctrl);
   const uint64_t *Dprev = rb.Dprev;
   const uint32_t *Cprev = rb.Cprev;
   int32_t *F = rb.F;
@@ -551,7 +577,7 @@ __device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const R
       const int j = gl + q * G;
       u[q] = (act && j < len) ? __ldg(p.col + b + j) : -1;
     }
-    if (p.test_changed) {
+    if (tc) {
 #pragma unroll
       for (int q = 0; q < UNR; ++q)
         if (u[q] >= 0 && !test_bit(Cprev, u[q])) u[q] = -1;
@@ -566,7 +592,8 @@ __device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const R
 #pragma unroll
       for (int q = 0; q < UNR; ++q)
         if (u[q] >= 0) {
-          or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
+          if (gather_ok(p, u[q], c * CW + CW - 1))
+            or_words<CW>(acc, Dprev + (size_t)u[q] * Wp + c * CW);
           if (c == 0) ++my_gath;
         }
 #pragma unroll
@@ -649,7 +676,7 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   unsigned long long my_work = 0;
   // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
   // of the graphs that chose a full sweep and take the others' work list
-  if (mode != kModeSparse)
+  if (mode != kModeSparse && !p.dense_tma)  // dense_tma: k_pull_tma swept them
     pull_dense<CW, PW>(p, ctrl, rb.Dprev, rb.Cprev, rb.F, rb.Ccur, rb.Kcur, rb.Kwcur, lane, warp,
                        nwarps, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
   if (mode != kModeDense)
@@ -659,6 +686,14 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
 }
 
 using PullFn = void (*)(Params);
+// Dense rounds with TMA-gathered deltas (pull_tma.cu), for rows of CW = 4 or
+// 8 words: the kernel, its dynamic shared memory, its launch, and the tensor
+// map (a CUtensorMap, 128 bytes) over a delta buffer of `rows` rows.
+const void *pull_tma_fn(int CW, bool pw);
+size_t pull_tma_smem(int CW);
+void launch_pull_tma(int CW, bool pw, const Params &p, const void *tm0, const void *tm1, int grid,
+                     cudaStream_t st);
+pg_status encode_delta_map(void *out, const uint64_t *D, int64_t rows, int Wp, int CW);
 PullFn pull_fn_cw1(int G, bool pw);
 PullFn pull_fn_cw2(int G, bool pw);
 PullFn pull_fn_cw4(int G, bool pw);

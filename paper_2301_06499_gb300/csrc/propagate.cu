@@ -2,6 +2,8 @@
 // seed i's bit set on its own node; Alg. 2's per-seed plane set-up), the post
 // kernel of every round (collision count, buffer sync, next work list,
 // fixpoint test) and the host round loop.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -43,6 +45,10 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     p.D0[words - 1] = 0ULL;
     p.D1[words - 1] = 0ULL;
   }
+  if (gtid < p.Wp) {  // the all-zero row past the last node
+    p.D0[words + gtid] = 0ULL;
+    p.D1[words + gtid] = 0ULL;
+  }
   for (int64_t i = gtid; i < p.nbm; i += nth) {
     p.C0[i] = 0u;
     p.C1[i] = 0u;
@@ -76,6 +82,8 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     c->row_base = 0;
     c->iters = 0;
     c->ndense = 0;
+    c->test = 1;
+    c->bad_index = 0;
     c->nF_prev = 0ULL;
   }
 }
@@ -538,6 +546,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
     } else {
       ctrl->t = t + 1;
       ctrl->mode = p.gfsum ? kModeMixed : next_dense ? kModeDense : kModeSparse;
+      ctrl->test = (double)fsum < kTestDensity * (double)p.m ? 1 : 0;
       if (next_dense) ctrl->dense_rounds += 1;
       ctrl->nA = *(volatile unsigned long long *)&ctrl->nA_next;
       ctrl->nA_next = 0ULL;
@@ -587,6 +596,10 @@ struct Plan {
   size_t post_smem = 0;
   bool smem_counts = true;
   bool post_wide = false;  // k_post's tiled part A (rows of 16+ words, one graph)
+  bool pw = false;         // PROPAGATE-S passes as words
+  bool tma = false;        // dense rounds by k_pull_tma (TMA-gathered deltas)
+  int grid_tma = 0;
+  CUtensorMap tm0, tm1;    // over D0 and D1 (n + 1 rows)
 };
 
 static PullFn pick_pull(int CW, int G, bool pw = false) {
@@ -690,9 +703,32 @@ static void launch_post(const Plan &pl, const Params &p, cudaStream_t st) {
   }
 }
 
-static void launch_round(const Plan &pl, const Params &p, cudaStream_t st) {
+// The pull of one round: k_pull_tma first when it sweeps the dense rounds
+// (it returns at once in the others), then k_pull.
+static void launch_pulls(const Plan &pl, const Params &p, cudaStream_t st) {
+  if (pl.tma) launch_pull_tma(pl.CW, pl.pw, p, &pl.tm0, &pl.tm1, pl.grid_tma, st);
   pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
+}
+
+static void launch_round(const Plan &pl, const Params &p, cudaStream_t st) {
+  launch_pulls(pl, p, st);
   launch_post(pl, p, st);
+}
+
+// Raises the dynamic shared memory limit of the TMA pull kernels (once per
+// device, before any launch).
+static void tma_smem_optin() {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && (done >> dev) & 1ULL) return;
+  for (int cw : {4, 8})
+    for (bool pw : {false, true})
+      cudaFuncSetAttribute(pull_tma_fn(cw, pw), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pull_tma_smem(cw));
+  if (dev < 64) done |= 1ULL << dev;
 }
 
 struct PassOut {
@@ -702,6 +738,7 @@ struct PassOut {
   int32_t launches = 0;
   double ms_pull = 0, ms_post = 0, ms_init = 0;
   int32_t pull_launches = 0, post_launches = 0;
+  bool tma = false;
 };
 
 struct Call {
@@ -775,6 +812,9 @@ struct GraphCache {
   size_t smem = 0;
   bool smem_counts = true;
   bool post_wide = false;
+  bool tma = false;
+  int grid_tma = 0;
+  unsigned char tm[2][sizeof(CUtensorMap)] = {};
   cudaStream_t cap = nullptr;
 };
 
@@ -797,7 +837,9 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   key.cond = c.p.cond;  // compare everything but the handle
   if (c.exec && c.pull == pl.pull && c.grid_pull == pl.grid_pull &&
       c.grid_post == pl.grid_post && c.smem == pl.post_smem && c.smem_counts == pl.smem_counts &&
-      c.post_wide == pl.post_wide &&
+      c.post_wide == pl.post_wide && c.tma == pl.tma && c.grid_tma == pl.grid_tma &&
+      (!pl.tma || (std::memcmp(c.tm[0], &pl.tm0, sizeof(CUtensorMap)) == 0 &&
+                   std::memcmp(c.tm[1], &pl.tm1, sizeof(CUtensorMap)) == 0)) &&
       std::memcmp(&c.p, &key, sizeof(Params)) == 0) {
     *out = c.exec;
     return PG_OK;
@@ -851,6 +893,10 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   c.smem = pl.post_smem;
   c.smem_counts = pl.smem_counts;
   c.post_wide = pl.post_wide;
+  c.tma = pl.tma;
+  c.grid_tma = pl.grid_tma;
+  std::memcpy(c.tm[0], &pl.tm0, sizeof(CUtensorMap));
+  std::memcpy(c.tm[1], &pl.tm1, sizeof(CUtensorMap));
   *out = c.exec;
   return PG_OK;
 }
@@ -895,6 +941,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     pl.pull = pl.wide ? pull_fn_wide(pl.Wp, true) : pick_pull(pl.CW, pl.G, true);
     if (!pl.pull) return PG_EINVAL;
   }
+  pl.pw = pw;
   if (bs) {  // a batch's columns: in shared memory when they fit
     pl.smem_counts = ncols <= kSmemCountMax;
     pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)ncols : 0;
@@ -910,8 +957,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   const size_t sig_bytes = sizeof(uint64_t) * (size_t)n * pl.Wp;
   const size_t bm_bytes = sizeof(uint32_t) * (size_t)nbm;
   pl.post_wide = !bs && pl.Wp >= kWidePostWords;
+  // the delta buffers keep one all-zero row past the last node (the row a
+  // TMA gather of an empty slot reads)
+  const size_t delta_bytes_alloc = sig_bytes + sizeof(uint64_t) * (size_t)pl.Wp;
   std::vector<std::pair<DevBuf *, size_t>> needs = {
-      {&w.X, sig_bytes}, {&w.Y, sig_bytes}, {&w.D0, sig_bytes}, {&w.D1, sig_bytes},
+      {&w.X, sig_bytes}, {&w.Y, sig_bytes}, {&w.D0, delta_bytes_alloc}, {&w.D1, delta_bytes_alloc},
       {&w.C0, bm_bytes}, {&w.C1, bm_bytes}, {&w.K0, bm_bytes}, {&w.K1, bm_bytes},
       {&w.Sat, bm_bytes},
       {&w.F0, sizeof(int32_t) * (size_t)n}, {&w.F1, sizeof(int32_t) * (size_t)n},
@@ -1006,10 +1056,34 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   // gather deltas unconditionally while they stay mostly in L2; beyond that,
   // test the (L2-resident) changed bitmap first
   const int64_t delta_bytes = n * (int64_t)pl.Wp * 8;
-  p.test_changed = cl.o.test_changed == 1 || (cl.o.test_changed == 0 && delta_bytes > (64LL << 20));
+  // 1: always test; 2: never; 3: per round; 0: per round once the deltas
+  // outgrow L2 (a packed batch: always, its frontiers are per graph)
+  const bool big = delta_bytes > (64LL << 20);
+  p.test_changed = cl.o.test_changed == 1 || cl.o.test_changed == 3 ||
+                   (cl.o.test_changed == 0 && big);
+  p.test_adapt = !p.gfsum && (cl.o.test_changed == 3 || (cl.o.test_changed == 0 && big));
   p.use_cond = 0;
   p.cond = 0ULL;
   p.iter_guard = cl.max_rounds + 2;
+  // TMA-gathered dense rounds: one graph (not a packed batch), rows of 4 or
+  // 8 words gathered whole, a sliced-ELL copy to sweep
+  const bool tma_ok = !bs && !pl.wide && pl.CW == pl.Wp && (pl.CW == 4 || pl.CW == 8) &&
+                      p.sell_chunks > 0;
+  // only on request: per-lane 256-bit loads measured faster on the
+  // relabelled scale-26 R-MAT (99.5 vs 171.7 ms of pull per PROPAGATE-P call)
+  pl.tma = tma_ok && cl.o.tma_gather == 2;
+  if (pl.tma) {
+    if ((rc = encode_delta_map(&pl.tm0, p.D0, n + 1, pl.Wp, pl.CW)) ||
+        (rc = encode_delta_map(&pl.tm1, p.D1, n + 1, pl.Wp, pl.CW)))
+      return rc;
+    tma_smem_optin();
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pull_tma_fn(pl.CW, pw), kBlock,
+                                                  pull_tma_smem(pl.CW));
+    if (per_sm < 1) return PG_ECUDA;
+    pl.grid_tma = sm_count() * per_sm;
+  }
+  p.dense_tma = pl.tma ? 1 : 0;
 
   const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
@@ -1101,7 +1175,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     }
     // every round of the loop is one pull and one post launch; iters counts
     // the post launches of the pass, post(0) included
-    po.launches = 2 + 2 * std::max(0, fin.iters) - 1;
+    po.launches = 3 + (pl.tma ? 3 : 2) * (std::max(0, fin.iters) - 1);
   } else {
     // Host-driven loop: batches of K rounds; the host reads the control
     // block of the batch before last while the last one runs. A first batch
@@ -1113,7 +1187,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
         if (timing) {
           int a = ntev++, b = ntev++, c = ntev++;
           cudaEventRecord(tev(a), st);
-          pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
+          launch_pulls(pl, p, st);
           cudaEventRecord(tev(b), st);
           launch_post(pl, p, st);
           cudaEventRecord(tev(c), st);
@@ -1123,7 +1197,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
           launch_round(pl, p, st);
         }
       }
-      po.launches += 2 * hint;
+      po.launches += (pl.tma ? 3 : 2) * hint;
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
       Ctrl cnow;
       if ((rc = cuda_status(cudaMemcpyAsync(&w.ctrl_h[0], p.ctrl, sizeof(Ctrl),
@@ -1147,7 +1221,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
         if (timing) {
           int a = ntev++, b = ntev++, c = ntev++;
           cudaEventRecord(tev(a), st);
-          pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
+          launch_pulls(pl, p, st);
           cudaEventRecord(tev(b), st);
           launch_post(pl, p, st);
           cudaEventRecord(tev(c), st);
@@ -1158,7 +1232,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
         }
       }
       enqueued += K;
-      po.launches += 2 * K;
+      po.launches += (pl.tma ? 3 : 2) * K;
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
       cudaMemcpyAsync(&w.ctrl_h[slot], p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
       cudaEventRecord(w.ev[slot], st);
@@ -1195,11 +1269,13 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       }
     }
   }
-  if (fin.status == PG_EDEVICE) return PG_EDEVICE;
+  if (fin.status == PG_EDEVICE || fin.status == PG_ETIMEOUT) return (pg_status)fin.status;
+  if (fin.bad_index) return PG_EDEVICE;  // a PG_DEBUG_BOUNDS build caught a bad gather
   const int32_t last = fin.status == PG_ERANGE ? cl.max_rounds : fin.last_round;
   const int32_t rows = last - row_base + 1;
   if ((rc = copy_window(cl, p, col0, row_base, rows, rows + 1))) return rc;
   po.rounds = fin.status == PG_ERANGE ? cl.max_rounds + 1 : fin.last_round;
+  po.tma = pl.tma;
   po.status = fin.status;
   po.dense_rounds = fin.dense_rounds;
   if (timing) {
@@ -1290,7 +1366,9 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   pg_default_options(&cl.o);
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
-  if (cl.o.pass_words < 0) return PG_EINVAL;
+  if (cl.o.pass_words < 0 || cl.o.test_changed < 0 || cl.o.test_changed > 3 ||
+      cl.o.tma_gather < 0 || cl.o.tma_gather > 2)
+    return PG_EINVAL;
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
   cl.counts_h = out->counts;
@@ -1419,6 +1497,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
     st.ms_init += po.ms_init;
     st.pull_launches += po.pull_launches;
     st.post_launches += po.post_launches;
+    st.dense_tma |= po.tma ? 1 : 0;
   }
   out->rounds = T;
   const int32_t last_stats = std::min(T + 1, out->max_rounds + 1);
@@ -1444,7 +1523,7 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   st.group_lanes = pl.G;
   st.pass_words = KW;
   st.words_per_gather = pl.wide ? 0 : pl.CW;
-  st.test_changed = cl.o.test_changed == 1 ||
+  st.test_changed = cl.o.test_changed == 1 || cl.o.test_changed == 3 ||
                     (cl.o.test_changed == 0 && g->n * (int64_t)pl.Wp * 8 > (64LL << 20));
   g->last = st;
   return status == PG_ERANGE ? PG_ERANGE : PG_OK;
@@ -1523,7 +1602,7 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
       st.words_per_gather = pl.wide ? 0 : pl.CW;
     }
   }
-  st.test_changed = cl.o.test_changed == 1 ||
+  st.test_changed = cl.o.test_changed == 1 || cl.o.test_changed == 3 ||
                     (cl.o.test_changed == 0 && g->n * (int64_t)st.words_per_row * 8 > (64LL << 20));
   g->last = st;
   if (st_out) *st_out = st;
@@ -1587,6 +1666,7 @@ void pg_default_options(pg_options *o) {
   o->wide_rows = 0;
   o->passes_together = 0;
   o->pass_words = 0;
+  o->tma_gather = 0;
 }
 
 pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
   const int64_t nwarps = nthreads >> 5;
   const int Wp = p.Wp;
   const int passes = NW > 0 ? 1 : (Wp + 32 * R - 1) / (32 * R);
+  const bool tc = test_changed_now(p, ctrl);
   unsigned long long my_mact = 0, my_work = 0, my_scan = 0, my_gath = 0, my_items = 0,
                      my_rows = 0;
   // dense: every row's pieces; sparse: the claimed pieces; mixed (a packed
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
       for (int r = 0; r < R; ++r) acc[r] = 0ULL;
       for (int a0 = 0; a0 < len; a0 += 32) {
         int32_t u = a0 + lane < len ? __ldg(p.col + b + a0 + lane) : -1;
-        if (u >= 0 && p.test_changed && !test_bit(Cprev, u)) u = -1;
+        if (u >= 0 && tc && !test_bit(Cprev, u)) u = -1;
         unsigned m = __ballot_sync(kFullMask, u >= 0);
         if (pass == 0 && lane == 0) my_gath += (unsigned long long)__popc(m);
         while (m) {  // four neighbours at a time: their loads are independent
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
 #pragma unroll
               for (int r = 0; r < R; ++r) {
                 const int w = w0 + 32 * r;
-                if (w < Wp) acc[r] |= __ldg(reinterpret_cast<const unsigned long long *>(dr) + w);
+                if (w < Wp && gather_ok(p, uu[q], w))
+                  acc[r] |= __ldg(reinterpret_cast<const unsigned long long *>(dr) + w);
               }
             }
         }

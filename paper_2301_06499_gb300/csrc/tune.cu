@@ -93,7 +93,7 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
     if (c <= cw_class && cw_class > 1) wpt.push_back(c);
   const int lanes[] = {0, 1, 2, 4, 8, 16, 32};
   const float dens[] = {0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.5f};
-  const int tests[] = {0, 1, 2};
+  const int tests[] = {0, 1, 2, 3};
   if (W > 8) {  // a warp per row piece, or lanes over 8-word chunks
     pg_options o = cur;
     o.wide_rows = cur.wide_rows == 2 ? 0 : 2;

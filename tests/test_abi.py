@@ -146,3 +146,16 @@ def test_argument_checks_before_any_device_work():
         rc = L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, 2, 2, 1, 0, None,
                                  ctypes.byref(out))
         assert rc == _abi.PG_ECUDA
+
+
+def test_debug_bounds_variant_builds_and_exports_every_symbol():
+    """The PG_DEBUG_BOUNDS build (every gather checks its indices and records
+    a bad one instead of faulting) compiles for sm_103a and exports the same
+    C ABI."""
+    import ctypes as C
+    from paper_2301_06499_gb300 import build
+    path = build.build(variant="debug-bounds")
+    assert path != build.lib_path("") and path.endswith("libpropagate_debug_bounds.so")
+    lib = C.CDLL(path)
+    for name in _declared("propagate.h"):
+        assert hasattr(lib, name), name

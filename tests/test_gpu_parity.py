@@ -430,3 +430,101 @@ def test_active_rows_match_distances(which):
     for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
         pg.propagate_p(G, seeds, opts=pg.options(direction=direction))
         assert G.last_stats()["active_rows"] == want, direction
+
+
+# --------------------------------------------------- TMA-gathered dense rounds
+@pytest.mark.parametrize("s", [512, 256, 130])
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE])
+def test_tma_gather_dense_rounds_match_the_oracle(s, direction):
+    """tma_gather = 2: the dense rounds copy the neighbours' delta rows into
+    shared memory with tile::gather4 (rows of 8 or 4 words); counts, m_active
+    and active rows equal the oracle's, for PROPAGATE-P and for PROPAGATE-S
+    with its passes as words, over rows cut into pieces (R-MAT hubs), with the
+    captured round loop and with plain event-timed launches."""
+    g = I.rmat(13, 16, 191, directed=False)
+    seeds = I.seeds(g.n, s, 192)
+    want = _oracle_p(g, seeds)
+    G = pg.Graph.from_inputs(g)
+    base = dict(direction=direction, tma_gather=2)
+    for extra in (dict(), dict(timing=1), dict(test_changed=2), dict(test_changed=1)):
+        res = pg.propagate_p(G, seeds, opts=pg.options(**base, **extra))
+        assert G.last_stats()["dense_tma"] == 1
+        _assert_same(res, want)
+    if direction == pg.PG_DIR_DENSE:
+        assert G.last_stats()["dense_tma"] == 1
+        assert G.last_stats()["active_rows"] == int(_active_rows_from_distances(g, seeds).sum())
+    res_s = pg.propagate_s(G, seeds, opts=pg.options(**base))
+    assert res_s.rounds == want["rounds"] and np.array_equal(res_s.counts, want["counts"])
+    assert np.array_equal(res_s.m_active,
+                          _oracle_s_mactive(g, seeds, 64, want["rounds"])[:res_s.m_active.size])
+
+
+def test_tma_gather_directed_and_reverse():
+    """TMA-gathered dense rounds on a directed graph, forward and with
+    PG_REVERSE (the pull over the out-edge transpose)."""
+    g = I.rmat(12, 16, 193, directed=True)
+    seeds = I.seeds(g.n, 300, 194)
+    o = pg.options(direction=pg.PG_DIR_DENSE, tma_gather=2)
+    _assert_same(pg.propagate_p(pg.Graph.from_inputs(g), seeds, opts=o), _oracle_p(g, seeds))
+    want = oracle.run(_transpose(g), seeds)
+    res = pg.propagate_p(pg.Graph.from_inputs(g, reverse=True), seeds, opts=o)
+    assert res.rounds == want["rounds"] and np.array_equal(res.counts, want["counts"])
+
+
+# ------------------------------------------------ arc arrays in host memory
+@pytest.mark.parametrize("which", ["rmat_directed", "rmat_undirected", "grid"])
+def test_host_csr_counts_match_the_oracle(which):
+    """PG_HOST_CSR keeps the arc arrays (columns, transpose, sliced-ELL copy)
+    in pinned host memory, read by the kernels over the CPU-GPU link: the
+    counts, m_active and metrics are the oracle's, in every direction, for
+    P and S, relabelled or not, and over the transpose (PG_REVERSE)."""
+    if which == "rmat_directed":
+        g, s = I.rmat(12, 16, 201, directed=True), 200
+    elif which == "rmat_undirected":
+        g, s = I.rmat(13, 16, 202, directed=False), 512
+    else:
+        g, s = I.grid(80, 90, 0.05, 203), 128
+    seeds = I.seeds(g.n, s, 204)
+    want = _oracle_p(g, seeds)
+    for relabel in (False, True):
+        G = pg.Graph.from_inputs(g, host_csr=True, relabel=relabel)
+        for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE):
+            _assert_same(pg.propagate_p(G, seeds, opts=pg.options(direction=direction)), want)
+        res_s = pg.propagate_s(G, seeds)
+        assert res_s.rounds == want["rounds"] and np.array_equal(res_s.counts, want["counts"])
+        G.close()
+    if g.directed:
+        wr = oracle.run(_transpose(g), seeds)
+        r = pg.propagate_p(pg.Graph.from_inputs(g, host_csr=True, reverse=True), seeds)
+        assert r.rounds == wr["rounds"] and np.array_equal(r.counts, wr["counts"])
+
+
+def test_debug_bounds_build_gives_the_oracles_counts():
+    """The PG_DEBUG_BOUNDS build, in a process of its own
+    (PG_LIBRARY_VARIANT=debug-bounds): no gather is out of range on valid
+    inputs (a bad index would make the call return PG_EDEVICE), and the
+    counts equal the oracle's, for the per-lane, wide-row and TMA pulls."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, oracle, paper_2301_06499_gb300 as pg\n"
+        "from paper_2301_06499_gb300 import inputs as I, _abi\n"
+        "assert 'debug_bounds' in _abi.lib()._name\n"
+        "cases = [(I.rmat(12, 16, 211, directed=True), 200, {}),\n"
+        "         (I.rmat(13, 16, 212, directed=False), 512, {'tma_gather': 2}),\n"
+        "         (I.grid(60, 70, 0.05, 213), 64, {}), (I.er(2000, 6, 214), 700, {})]\n"
+        "for g, s, o in cases:\n"
+        "    seeds = I.seeds(g.n, s, 215)\n"
+        "    want = oracle.run(g, seeds)\n"
+        "    G = pg.Graph.from_inputs(g)\n"
+        "    for fn in (pg.propagate_p, pg.propagate_s):\n"
+        "        r = fn(G, seeds, opts=pg.options(**o))\n"
+        "        assert r.rounds == want['rounds'] and np.array_equal(r.counts, want['counts'])\n"
+        "print('debug-bounds ok')\n")
+    env = dict(os.environ, PG_LIBRARY_VARIANT="debug-bounds")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                         text=True, timeout=1200)
+    assert out.returncode == 0, out.stderr[-3000:]
+    assert "debug-bounds ok" in out.stdout
