@@ -420,6 +420,23 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    # the same graph drawn and built on the device (pg_graph_generate),
+    # outside every timing: its time beside the host generator's
+    dev_gen = None
+    if spec["kind"] in ("rmat", "er", "grid") and not host_csr:
+        kw = ({"scale": spec["scale"], "edge_factor": spec["ef"], "directed": spec["directed"]}
+              if spec["kind"] == "rmat" else
+              {"n": spec["n"], "avg_degree": spec["d"]} if spec["kind"] == "er" else
+              {"rows": spec["rows"], "cols": spec["cols"], "p_delete": spec["p"]})
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gd = pg.Graph.generate(spec["kind"], spec["seed"], stream=sptr, **kw)
+        torch.cuda.synchronize()
+        dev_gen = {"seconds": round(time.perf_counter() - t0, 3),
+                   "same_size": (Gd.n, Gd.m) == (g.n, g.m)}
+        Gd.close()
+        torch.cuda.empty_cache()
+    out["config"]["device_generation"] = dev_gen
     if args.batched and args.workload == DEFAULT_WORKLOAD:
         # the metric's own comparison, batched vs plain, on the mixed workload
         # of 512 graphs (library default schedules, fewer steps than the
@@ -733,7 +750,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
 
-    srv = pg.Server(slots=args.slots)
+    srv = pg.Server(slots=args.slots, cross_graph=bool(args.cross_graph))
     gids = [srv.add_inputs(g) for g in graphs]  # the uploads join while serving
     upload_s = []
 
@@ -779,16 +796,17 @@ def run_serve(args):
                 r, w = run_alone(key)
                 alone[key] = (r.counts, r.rounds, w)
 
-    def open_loop_run(rate, uploads_at=()):
-        count = min(int(rate * W["duration"]), W["max_requests"])
-        rng = np.random.default_rng(W["seed"] + int(rate))
+    def open_loop_run(rate, uploads_at=(), count=None):
+        count = count or min(int(rate * W["duration"]), W["max_requests"])
+        rng = np.random.default_rng(W["seed"] + int(rate * 1000))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
         first = len(graphs)
 
         def avail(k):  # graphs registered by the time request k is submitted
             return first + sum(1 for at in uploads_at if at <= k) if uploads_at else len(allg)
 
-        reqs = _serve_requests(count, len(allg), W["seed"] + int(rate), V, upload_at=avail)
+        reqs = _serve_requests(count, len(allg), W["seed"] + int(rate * 1000), V,
+                               upload_at=avail)
         ensure_alone(reqs)
         lat, bad, wall = served(reqs, arrivals, uploads_at)
         assert bad == 0, f"{bad} served answers differ from the request alone"
@@ -802,18 +820,27 @@ def run_serve(args):
     warm = [k for k in burst if k[0] < len(graphs)][:16]
     served(warm)  # warm-up: views, workspaces, captured loops
     open_loop = []
-    n0 = min(int(W["rates"][0] * W["duration"]), W["max_requests"])
-    open_loop.append(open_loop_run(W["rates"][0], uploads_at=(n0 // 3, 2 * n0 // 3)))
-    st0 = srv.stats()
-    lat_b, bad_b, served_s = served(burst)
-    st1 = srv.stats()
-    assert bad_b == 0, f"{bad_b} served answers differ from the request alone"
-    work = sum(alone[k][2] for k in burst)
-    assert work == plain_work
-    value = work / served_s
-    plain_value = work / plain_s
-    for rate in W["rates"][1:]:
-        open_loop.append(open_loop_run(rate))
+    with Clocks(torch.cuda.current_device()) as clk:
+        n0 = min(int(W["rates"][0] * W["duration"]), W["max_requests"])
+        open_loop.append(open_loop_run(W["rates"][0], uploads_at=(n0 // 3, 2 * n0 // 3)))
+        st0 = srv.stats()
+        lat_b, bad_b, served_s = served(burst)
+        st1 = srv.stats()
+        assert bad_b == 0, f"{bad_b} served answers differ from the request alone"
+        work = sum(alone[k][2] for k in burst)
+        assert work == plain_work
+        value = work / served_s
+        plain_value = work / plain_s
+        # capacity: the burst's completion rate; latency below and at it, so
+        # that p50/p99 are not queueing alone
+        capacity = len(burst) / served_s
+        for frac in (0.5, 0.9):
+            rate = frac * capacity
+            r = open_loop_run(rate, count=int(max(60, min(300, rate * 20))))
+            r["fraction_of_capacity"] = frac
+            open_loop.append(r)
+        for rate in W["rates"][1:]:
+            open_loop.append(open_loop_run(rate))
     stats = srv.stats()
     srv.close()
 
@@ -828,11 +855,13 @@ def run_serve(args):
                                   f"[{W['n_lo']:g}, {W['n_hi']:g}]) + uploaded ER "
                                   f"{[u[0] for u in W['uploads']]}; eps in {{0.05, 0.1, 0.2}}",
                    "burst_requests": len(burst), "slots": args.slots,
+                   "cross_graph": bool(args.cross_graph),
                    "distinct_requests": len(alone), "generate_s": gen_s,
                    "timing": "wall clock between device synchronisations",
                    "parallelism": f"replicas x{world}"},
         "plain": {"value": plain_value, "ms_per_step": plain_s * 1e3},
         "served_over_plain": value / plain_value,
+        "capacity_req_per_s": capacity,
         "burst_latency_ms": {"p50": float(np.percentile(lat_b, 50)),
                              "p99": float(np.percentile(lat_b, 99))},
         "burst_propagations": st1["propagations"] - st0["propagations"],
@@ -844,6 +873,7 @@ def run_serve(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": served_s * 1e3},
         "gpu_launches": int(st1["gpu_launches"] - st0["gpu_launches"]),
+        "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -1060,6 +1090,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) +
                     sorted(SERVE_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--slots", type=int, default=4, help="server slots (serving workload)")
+    ap.add_argument("--cross-graph", type=int, default=1,
+                    help="server: 1 = merge requests across graphs of one width as a union")
     ap.add_argument("--tune", type=int, default=1,
                     help="1 = let the autotuner pick the schedule options before timing")
     ap.add_argument("--tune-trials", type=int, default=16)

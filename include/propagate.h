@@ -178,6 +178,16 @@ typedef struct {
                                loaded by each lane; 0 or 1 = per-lane loads
                                (the default: they measured faster on a 2^26-
                                node graph with 8-word rows) */
+  int32_t sparse_push;      /* sparse rounds: 2 = push, each row that changed
+                               in the previous round ORs its delta into its
+                               out-neighbours with atomics (their claims for
+                               m_active made on the way); 1 = pull, the post
+                               kernel claims the frontier's out-neighbours
+                               and the pull gathers their in-arcs; 0 = push
+                               where it applies: one graph with rows of up
+                               to 4 words (s <= 256) gathered whole,
+                               PROPAGATE-P or PROPAGATE-S one pass at a
+                               time; pull elsewhere */
 } pg_options;
 
 #define PG_DIR_AUTO 0
@@ -293,7 +303,54 @@ void pg_graph_free(pg_graph *g);
  * (PG_RELABEL, or by default on a skewed graph), else 0. */
 pg_status pg_graph_is_relabelled(const pg_graph *g, int32_t *relabelled);
 
-/* n and m of a graph. */
+/*
+ * Graph generators on the device. The paper measures on real graphs
+ * (Table 1); these are the seeded synthetic stand-ins of the same classes,
+ * drawn on the GPU from one counter-based SplitMix64 stream (draw i of stream
+ * k under a seed), so that they equal, arc for arc, what any implementation
+ * of the same definitions produces (the tests compare with the host
+ * generators):
+ *  PG_GEN_ER    undirected G(n, M), M = round(n avg_degree / 2) uniform
+ *               pairs with replacement (draws 2i, 2i+1 of stream 0)
+ *  PG_GEN_RMAT  2^scale nodes, round(edge_factor 2^scale) edges, each by
+ *               `scale` quadrant choices with probabilities (a, b, c, 1-a-b-c)
+ *               quantised to 16 bits, four levels per draw of stream 1; no
+ *               noise, no permutation; directed keeps src -> dst, else
+ *               symmetrised
+ *  PG_GEN_GRID  rows x cols 4-neighbour lattice, node (r, c) = r cols + c,
+ *               edge i deleted when draw i of stream 2 < p_delete 2^64
+ * Self-loops are dropped and duplicates removed. The CSR over in-edges is
+ * built on the device (a radix sort of the arc keys, a scan for the unique
+ * ones) and becomes the graph as pg_graph_from_csr would make it (flags as
+ * there, except PG_DEVICE_PTRS, PG_BORROW and PG_HOST_CSR). Errors: PG_EINVAL
+ * (sizes, probabilities), PG_ENOMEM, PG_ECUDA.
+ */
+#define PG_GEN_ER 0
+#define PG_GEN_RMAT 1
+#define PG_GEN_GRID 2
+typedef struct {
+  int32_t kind;        /* PG_GEN_ER, PG_GEN_RMAT or PG_GEN_GRID */
+  int32_t directed;    /* PG_GEN_RMAT only: 1 = arcs src -> dst, 0 = symmetrised */
+  uint64_t seed;
+  int64_t n;           /* PG_GEN_ER: nodes */
+  double avg_degree;   /* PG_GEN_ER */
+  int32_t scale;       /* PG_GEN_RMAT: 2^scale nodes (1..30) */
+  int32_t reserved;
+  double edge_factor;  /* PG_GEN_RMAT */
+  double a, b, c;      /* PG_GEN_RMAT quadrant probabilities */
+  int64_t rows, cols;  /* PG_GEN_GRID */
+  double p_delete;     /* PG_GEN_GRID */
+} pg_generator;
+pg_status pg_graph_generate(const pg_generator *gen, unsigned flags, void *stream,
+                            pg_graph **out);
+
+/* Copies g's CSR over in-edges, as the kernels read it (the library's
+ * internal node ids: the caller's unless the graph was relabelled), into
+ * row_ptr[n+1] and col[m] (host or device; the call returns when they are
+ * written). Errors: PG_EINVAL, PG_ECUDA. */
+pg_status pg_graph_copy_csr(const pg_graph *g, int64_t *row_ptr, int32_t *col, void *stream);
+
+/* n and m of a graph. *//* n and m of a graph. */
 pg_status pg_graph_info(const pg_graph *g, int64_t *n, int64_t *m);
 
 /* A safe max_rounds: every eccentricity is at most n - 1. */
@@ -496,7 +553,10 @@ pg_status pg_batch_get_options(pg_batch *b, int32_t group, pg_options *out, int3
  * takes the oldest request that fits the memory budget and merges into the
  * same propagation the other queued requests on that graph (up to merge_max
  * requests and merge_max_seeds seeds; seeds of different requests are
- * independent bit columns and may coincide). Propagations on different
+ * independent bit columns and may coincide) and, with cross_graph, queued
+ * requests on other graphs of the same signature width: those graphs run
+ * as one disjoint union, as a batch does (pg_batch_*), built on the device
+ * from the resident copies for that propagation. Propagations on different
  * slots run concurrently on the device.
  *
  * Memory admission: resident graphs (CSR, out-CSR, sliced-ELL copy) plus
@@ -517,7 +577,12 @@ typedef struct {
   int32_t slots;            /* concurrent propagations (1..64; default 4) */
   int32_t merge_max;        /* most requests merged into one propagation (16) */
   int32_t merge_max_seeds;  /* most seeds of a merged propagation (8192) */
-  int32_t reserved;
+  int32_t cross_graph;      /* 1 (default): a propagation may also merge
+                               queued requests on other graphs of the same
+                               signature width (1, 2, 4 or a multiple of 8
+                               words), run as one packed union of those
+                               graphs (up to 2^22 nodes, each graph its own
+                               kind of round); 0: requests on one graph only */
   int64_t hbm_budget;       /* device bytes for graphs + workspaces; 0 = 90% of
                                the memory free at creation */
   pg_options opt;           /* options of every propagation (timing ignored;

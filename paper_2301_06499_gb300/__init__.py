@@ -115,6 +115,47 @@ class Graph:
         return cls.from_csr(g.row_ptr, g.col, g.n, directed=g.directed, stream=stream,
                             reverse=reverse, relabel=relabel, host_csr=host_csr)
 
+    @classmethod
+    def generate(cls, kind: str, seed: int, stream=None, reverse: bool = False,
+                 relabel: bool | None = None, **kw) -> "Graph":
+        """pg_graph_generate: a seeded synthetic graph drawn and built on the
+        device. kind "er" (n, avg_degree), "rmat" (scale, edge_factor,
+        directed, a=.57, b=.19, c=.19) or "grid" (rows, cols, p_delete)."""
+        gen = _abi.Generator()
+        gen.seed = int(seed)
+        if kind == "er":
+            gen.kind, gen.n, gen.avg_degree = _abi.PG_GEN_ER, int(kw["n"]), float(kw["avg_degree"])
+        elif kind == "rmat":
+            gen.kind, gen.scale = _abi.PG_GEN_RMAT, int(kw["scale"])
+            gen.edge_factor, gen.directed = float(kw["edge_factor"]), int(bool(kw["directed"]))
+            gen.a, gen.b, gen.c = (float(kw.get("a", 0.57)), float(kw.get("b", 0.19)),
+                                   float(kw.get("c", 0.19)))
+        elif kind == "grid":
+            gen.kind, gen.rows, gen.cols = _abi.PG_GEN_GRID, int(kw["rows"]), int(kw["cols"])
+            gen.p_delete = float(kw["p_delete"])
+        else:
+            raise ValueError(f"unknown generator {kind!r}")
+        flags = _abi.PG_REVERSE if reverse else 0
+        if relabel is not None:
+            flags |= _abi.PG_RELABEL if relabel else _abi.PG_KEEP_ORDER
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _abi.check(_abi.lib().pg_graph_generate(ctypes.byref(gen), flags, st, ctypes.byref(h)),
+                   "pg_graph_generate")
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        _abi.check(_abi.lib().pg_graph_info(h, ctypes.byref(n), ctypes.byref(m)), "pg_graph_info")
+        return cls(h, int(n.value), int(m.value))
+
+    def csr(self, stream=None):
+        """pg_graph_copy_csr: (row_ptr, col) as the kernels read them (the
+        internal ids of a relabelled graph)."""
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(max(self.m, 1), dtype=np.int32)
+        st = stream if stream is not None else _current_stream()
+        _abi.check(_abi.lib().pg_graph_copy_csr(self._h, rp.ctypes.data, col.ctypes.data, st),
+                   "pg_graph_copy_csr")
+        return rp, col[:self.m]
+
     @property
     def relabelled(self) -> bool:
         r = ctypes.c_int32()
@@ -337,16 +378,18 @@ class Batch:
 
 class Server:
     """pg_server: resident graphs and asynchronous PROPAGATE-P requests with
-    continuous batching (merging of queued requests on one graph, concurrent
-    slots, admission by device-memory budget). Results are the counts
+    continuous batching (merging of queued requests on one graph, and with
+    cross_graph on graphs of one signature width as a packed union;
+    concurrent slots; admission by device-memory budget). Results are the counts
     pg_propagate_p gives for each request alone."""
 
     def __init__(self, slots: int = 4, merge_max: int = 16, merge_max_seeds: int = 8192,
-                 hbm_budget: int = 0, opts=None):
+                 hbm_budget: int = 0, opts=None, cross_graph: bool = True):
         c = _abi.ServerConfig()
         _abi.lib().pg_server_default_config(ctypes.byref(c))
         c.slots, c.merge_max, c.merge_max_seeds, c.hbm_budget = (
             int(slots), int(merge_max), int(merge_max_seeds), int(hbm_budget))
+        c.cross_graph = int(bool(cross_graph))
         if opts is not None:
             c.opt = opts
         h = ctypes.c_void_p()

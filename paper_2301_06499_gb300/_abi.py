@@ -33,7 +33,21 @@ class Options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("window_rows", ctypes.c_int32), ("words_per_thread", ctypes.c_int32),
                 ("wide_rows", ctypes.c_int32), ("passes_together", ctypes.c_int32),
-                ("pass_words", ctypes.c_int32), ("tma_gather", ctypes.c_int32)]
+                ("pass_words", ctypes.c_int32), ("tma_gather", ctypes.c_int32),
+                ("sparse_push", ctypes.c_int32)]
+
+
+class Generator(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("directed", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("n", ctypes.c_int64),
+                ("avg_degree", ctypes.c_double), ("scale", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("edge_factor", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("p_delete", ctypes.c_double)]
+
+
+PG_GEN_ER, PG_GEN_RMAT, PG_GEN_GRID = 0, 1, 2
 
 
 class Counts(ctypes.Structure):
@@ -78,7 +92,7 @@ class BatchStats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("merge_max", ctypes.c_int32),
-                ("merge_max_seeds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("merge_max_seeds", ctypes.c_int32), ("cross_graph", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("opt", Options)]
 
 
@@ -115,6 +129,9 @@ SIGNATURES = {
     "pg_graph_free": (None, [_vp]),
     "pg_graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "pg_graph_is_relabelled": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    "pg_graph_generate": (ctypes.c_int, [ctypes.POINTER(Generator), ctypes.c_uint, _vp,
+                                         ctypes.POINTER(_vp)]),
+    "pg_graph_copy_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "pg_query_rounds_bound": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "pg_propagate_p": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(Counts),
                                       ctypes.POINTER(Options), _vp]),

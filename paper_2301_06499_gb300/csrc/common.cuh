@@ -22,7 +22,9 @@ constexpr unsigned long long kFsumMask = (1ULL << kFsumBits) - 1ULL;
 
 // kModeMixed (packed batches): each graph of the union picks its own kind
 // of round from its own frontier (see Params::gfsum).
-enum : int32_t { kModeDense = 0, kModeSparse = 1, kModeMixed = 2 };
+// kModePush: a sparse round pushed from the frontier of round t-1 along its
+// out-arcs (atomic OR of each changed row's delta into its out-neighbours).
+enum : int32_t { kModeDense = 0, kModeSparse = 1, kModeMixed = 2, kModePush = 3 };
 
 // Device-side control block of one propagation (one pass).
 struct Ctrl {
@@ -43,6 +45,7 @@ struct Ctrl {
   int32_t test;          // round t tests changed bits before gathers (per-round mode)
   int32_t bad_index;     // PG_DEBUG_BOUNDS builds: a gather's index was out of range
   unsigned long long nF_prev;  // |F_{t-1}|
+  unsigned long long nE_prev;  // out-arc pieces of F_{t-1} (read by a push round)
 };
 
 // Per-round work counters (device), indexed by round.
@@ -86,6 +89,7 @@ struct Params {
   int64_t nbm;         // 32-bit words per bitmap
   int32_t *F0, *F1;    // rows changed in round t, by round parity
   unsigned long long *E;  // out-arc pieces of F rows: (row << 32) | piece of LE arcs
+  unsigned long long *E1; // with push rounds: the pieces of odd rounds (E: even), else null
   ulonglong2 *A;        // sparse work list: in-arc pieces of the claimed rows
   const ulonglong2 *Pall;  // every in-arc piece of every row (unused by dense rounds)
   const ulonglong2 *sell_items;  // dense rounds: sliced-ELL copy (see SellList)
@@ -125,6 +129,7 @@ struct Params {
   int32_t test_changed; // test C_{t-1} before gathering an in-neighbour's delta
   int32_t test_adapt;   // decide test_changed per round (ctrl->test, set by the post kernel)
   int32_t dense_tma;    // dense rounds are swept by k_pull_tma (launched before k_pull)
+  int32_t push;         // sparse rounds push from the previous frontier (kModePush)
   int32_t use_cond;     // launched inside a conditional while-graph
   int32_t iter_guard;   // post launches after which a pass is abandoned
   unsigned long long cond;  // cudaGraphConditionalHandle of that graph

@@ -23,7 +23,7 @@ struct DevBuf {
 struct Workspace {
   DevBuf arena;
   DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, KW0, KW1, F0, F1, E, A, counts, rs, ctrl, seeds,
-      seed_bits, gfsum, gthr, dlist, dpref;
+      seed_bits, gfsum, gthr, dlist, dpref, E1;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -154,5 +154,8 @@ void drop_replicas(pg_graph *g);
 // Device bytes a propagation of s seeds on g will hold in its workspace
 // (window_rows as pg_options.window_rows).
 int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows);
+// The same for a graph of n nodes and m arcs.
+int64_t workspace_bytes_nm(int64_t n, int64_t m, int32_t s, int32_t max_rounds,
+                           int32_t window_rows);
 
 }  // namespace pg

@@ -130,6 +130,12 @@ __device__ __forceinline__ void block_add(const unsigned long long (&v)[N],
   }
 }
 
+// Out-arc pieces of the frontier of round t: one list, or (with push rounds,
+// which read round t-1's while appending round t's) two by round parity.
+__device__ __forceinline__ unsigned long long *E_of(const Params &p, int t) {
+  return ((t & 1) && p.E1) ? p.E1 : p.E;
+}
+
 // Seeds of the graph node v belongs to (a batch of disjoint graphs), else s.
 __device__ __forceinline__ int seeds_of(const Params &p, int32_t v) {
   return p.node_graph ? __ldg(p.graph_s + __ldg(p.node_graph + v)) : p.s;
@@ -206,6 +212,53 @@ __device__ __forceinline__ void warp_append_items(ulonglong2 *list, unsigned lon
   }
 }
 
+// warp_append_items for N rows per lane at once (cnt[q] pieces of row[q],
+// its arcs read from row_ptr again): one scan and one atomicAdd on *counter
+// for all of them (the post kernel's claims of one step).
+template <int N>
+__device__ __forceinline__ void warp_append_items_n(ulonglong2 *list, unsigned long long *counter,
+                                                    const int64_t *row_ptr,
+                                                    const int32_t (&row)[N], int L,
+                                                    const uint32_t (&cnt)[N], int lane) {
+  unsigned long long mine = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q) mine += cnt[q];
+  unsigned long long total;
+  const unsigned long long ex = warp_excl_scan64(mine, lane, &total);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(kFullMask, base, 0);
+  unsigned long long at = base + ex;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const uint32_t c = cnt[q];
+    int64_t rb = 0, indeg = 0;
+    if (c) {
+      rb = __ldg(row_ptr + row[q]);
+      indeg = __ldg(row_ptr + row[q] + 1) - rb;
+    }
+    const bool whole = c == 1;
+    const uint32_t head = c < 4 ? c : 4;
+    for (uint32_t k = 0; k < head; ++k)
+      list[at + k] = make_item(row[q], rb + (int64_t)k * L, min((int64_t)L, indeg - (int64_t)k * L),
+                               whole);
+    unsigned big = __ballot_sync(kFullMask, c > 4);
+    while (big) {  // long rows are written by the whole warp
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t cc = __shfl_sync(kFullMask, c, src);
+      const unsigned long long a = __shfl_sync(kFullMask, at, src);
+      const int32_t r = __shfl_sync(kFullMask, row[q], src);
+      const int64_t b0 = __shfl_sync(kFullMask, rb, src);
+      const int64_t d0 = __shfl_sync(kFullMask, indeg, src);
+      for (uint32_t k = 4 + lane; k < cc; k += 32)
+        list[a + k] = make_item(r, b0 + (int64_t)k * L, min((int64_t)L, d0 - (int64_t)k * L), false);
+    }
+    at += c;
+  }
+}
+
 // Frontier append of the rows whose lane has app set: F_t (rows; the packed
 // counter also sums their out-degrees) and E (their out-arcs in pieces of LE).
 __device__ __forceinline__ void frontier_append(const Params &p, Ctrl *ctrl, int32_t *F, int32_t v,
@@ -235,8 +288,70 @@ __device__ __forceinline__ void frontier_append(const Params &p, Ctrl *ctrl, int
     F[(int64_t)(basep >> kFsumBits) + rank] = v;
   }
   const unsigned long long ne = app ? (od + p.LE - 1) / p.LE : 0ULL;
-  warp_append_pieces(p.E, &ctrl->nE, v, ne, lane);
+  warp_append_pieces(E_of(p, ctrl->t), &ctrl->nE, v, ne, lane);
 }
+
+// frontier_append for up to N rows per lane (app[q] marks row v[q]): one
+// reservation in F_t (with the rows' out-degree sum) and one in E_t per warp.
+template <int N>
+__device__ __forceinline__ void frontier_append_n(const Params &p, Ctrl *ctrl, int32_t *F,
+                                                  const int32_t (&v)[N], const bool (&app)[N],
+                                                  int lane) {
+  uint32_t cnt = 0;
+  unsigned long long odsum = 0, nesum = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (app[q]) {
+      const unsigned long long od =
+          (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
+      ++cnt;
+      odsum += od;
+      nesum += (od + p.LE - 1) / p.LE;
+    }
+  if (!__any_sync(kFullMask, cnt != 0)) return;
+  unsigned long long tot;
+  const unsigned long long ex =
+      warp_excl_scan64(((unsigned long long)cnt << kFsumBits) + odsum, lane, &tot);
+  unsigned long long basep = 0;
+  if (lane == 0) basep = atomicAdd(&ctrl->fpack, tot);
+  basep = __shfl_sync(kFullMask, basep, 0);
+  unsigned long long at = (basep >> kFsumBits) + (ex >> kFsumBits);
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (app[q]) F[at++] = v[q];
+  unsigned long long tote;
+  const unsigned long long exe = warp_excl_scan64(nesum, lane, &tote);
+  if (tote == 0) return;
+  unsigned long long basee = 0;
+  if (lane == 0) basee = atomicAdd(&ctrl->nE, tote);
+  basee = __shfl_sync(kFullMask, basee, 0);
+  unsigned long long *E = E_of(p, ctrl->t);
+  unsigned long long ate = basee + exe;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    unsigned long long ne = 0;
+    if (app[q]) {
+      const unsigned long long od =
+          (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
+      ne = (od + p.LE - 1) / p.LE;
+    }
+    const unsigned long long head = ne < 4 ? ne : 4;
+    for (unsigned long long k = 0; k < head; ++k)
+      E[ate + k] = ((unsigned long long)(uint32_t)v[q] << 32) | k;
+    unsigned big = __ballot_sync(kFullMask, ne > 4);
+    while (big) {  // long lists are written by the whole warp
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const unsigned long long c = __shfl_sync(kFullMask, ne, src);
+      const unsigned long long a = __shfl_sync(kFullMask, ate, src);
+      const int32_t r = __shfl_sync(kFullMask, v[q], src);
+      for (unsigned long long k = 4 + lane; k < c; k += 32)
+        E[a + k] = ((unsigned long long)(uint32_t)r << 32) | k;
+    }
+    ate += ne;
+  }
+}
+
 
 // Finishes one row piece after its deltas are ORed into acc (words
 // [c*CW, c*CW+CW) of the row): a row of one piece compares with X[v] and
@@ -625,6 +740,77 @@ __device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const R
   }
 }
 
+// Push round t (sparse rounds with p.push): every changed row u of round t-1
+// ORs its delta D_{t-1}[u] into Y[v] of each unsaturated out-neighbour v
+// with 64-bit atomics, over the out-arc pieces of F_{t-1} (E of round t-1).
+// The result equals the pull's: Sig_t(v) = Sig_{t-1}(v) | OR of the deltas
+// of v's changed in-neighbours. The pusher whose OR added a bit to v first
+// puts v in the frontier. Activity for m_active is the same claim as the
+// post kernel's for a pull round: the first pusher to reach an unsaturated v
+// claims it and counts its in-degree.
+template <int CW>
+__device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const RoundBufs &rb, int t,
+                                          int lane, int64_t warp, int64_t nwarps,
+                                          uint32_t &my_mact, unsigned long long &my_work,
+                                          uint32_t &my_scan, uint32_t &my_gath,
+                                          uint32_t &my_items, uint32_t &my_rows) {
+  constexpr int UNR = 4;
+  const unsigned long long *Ep = E_of(p, t - 1);
+  const int64_t nEp = (int64_t)ctrl->nE_prev;
+  const size_t Wp = (size_t)p.Wp;
+  for (int64_t base = warp * 32; base < nEp; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    int64_t ob = 0, oe = 0;
+    uint64_t d[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) d[k] = 0ULL;
+    if (i < nEp) {
+      const unsigned long long it = Ep[i];
+      const int32_t u = (int32_t)(it >> 32);
+      const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
+      const int64_t o1 = __ldg(p.out_ptr + u + 1);
+      ob = __ldg(p.out_ptr + u) + k * p.LE;
+      oe = min(o1, ob + (int64_t)p.LE);
+      if (gather_ok(p, u, CW - 1)) load_words<CW>(d, rb.Dprev + (size_t)u * Wp);
+      ++my_items;
+      ++my_gath;
+      my_scan += (uint32_t)(oe - ob);
+    }
+    for (int h = 0; h < p.LE; h += UNR) {
+      int32_t v[UNR];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) {
+        const int64_t j = ob + h + q;
+        v[q] = j < oe ? __ldg(p.out_col + j) : -1;
+        if (v[q] >= 0 && (!gather_ok(p, v[q], CW - 1) || test_bit(p.Sat, v[q]))) v[q] = -1;
+      }
+      bool app[UNR];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) {
+        app[q] = false;
+        if (v[q] < 0) continue;
+        if (!test_bit_live(rb.Kcur, v[q]) && !set_bit(rb.Kcur, v[q])) {
+          const uint32_t indeg = (uint32_t)(__ldg(p.row_ptr + v[q] + 1) - __ldg(p.row_ptr + v[q]));
+          my_mact += indeg;
+          my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, v[q]);
+          ++my_rows;
+        }
+        bool changed = false;
+#pragma unroll
+        for (int k = 0; k < CW; ++k)
+          if (d[k]) {
+            const unsigned long long old = atomicOr(
+                reinterpret_cast<unsigned long long *>(p.Y + (size_t)v[q] * Wp + k),
+                (unsigned long long)d[k]);
+            changed |= (old | d[k]) != old;
+          }
+        app[q] = changed && !set_bit(rb.Ccur, v[q]);
+      }
+      frontier_append_n<UNR>(p, ctrl, rb.F, v, app, lane);
+    }
+  }
+}
+
 // Per-block sums of a pull launch's work counters into round t's slot.
 __device__ __forceinline__ void pull_end(const Params &p, Ctrl *ctrl, int t, uint32_t my_mact,
                                          unsigned long long my_work, uint32_t my_scan,
@@ -676,12 +862,18 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   unsigned long long my_work = 0;
   // dense rounds sweep every row; mixed rounds (a packed batch) sweep the rows
   // of the graphs that chose a full sweep and take the others' work list
-  if (mode != kModeSparse && !p.dense_tma)  // dense_tma: k_pull_tma swept them
+  if ((mode == kModeDense && !p.dense_tma) || mode == kModeMixed)  // dense_tma: k_pull_tma
     pull_dense<CW, PW>(p, ctrl, rb.Dprev, rb.Cprev, rb.F, rb.Ccur, rb.Kcur, rb.Kwcur, lane, warp,
                        nwarps, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
-  if (mode != kModeDense)
+  if (mode == kModeSparse || mode == kModeMixed)
     pull_sparse<CW, G, PW>(p, ctrl, rb, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
                            my_items, my_rows);
+  // push rounds for rows of up to 4 words (the 8-word kernel keeps its
+  // registers for the dense sweep)
+  if constexpr (!PW && CW <= 4)
+    if (mode == kModePush)
+      pull_push<CW>(p, ctrl, rb, t, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
+                    my_items, my_rows);
   pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
     c->test = 1;
     c->bad_index = 0;
     c->nF_prev = 0ULL;
+    c->nE_prev = 0ULL;
   }
 }
 
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(1024) k_seed(Params p, const int32_t *seeds,
       }
     }
     const unsigned long long ne = first ? (od + p.LE - 1) / p.LE : 0ULL;
-    warp_append_pieces(p.E, &p.ctrl->nE, x, ne, lane);
+    warp_append_pieces(E_of(p, 0), &p.ctrl->nE, x, ne, lane);
   }
   __syncthreads();
   if (threadIdx.x == 0) p.ctrl->fpack = ((unsigned long long)nf << kFsumBits) | tot;
@@ -399,7 +400,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       !p.gfsum && (p.direction == PG_DIR_DENSE ||
                    (p.direction == PG_DIR_AUTO &&
                     (double)fsum > (double)p.dense_threshold * (double)p.m));
-  const bool expand = !next_dense && nF > 0 && t + 1 <= p.max_rounds + 1;
+  // a push round reads this frontier's out-arcs itself: nothing to claim here
+  const bool next_push = !next_dense && p.push && !p.gfsum;
+  const bool expand = !next_dense && !next_push && nF > 0 && t + 1 <= p.max_rounds + 1;
   // a packed batch decides per graph: a graph whose frontier out-arcs exceed
   // its own threshold is swept whole in round t+1 and not expanded here
   const unsigned long long *gf_cur = p.gfsum ? p.gfsum + (size_t)(t & 1) * (size_t)p.nseg : nullptr;
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       const int64_t i = base + lane;
       int64_t ob = 0, oe = 0;
       if (i < nE) {
-        const unsigned long long it = p.E[i];
+        const unsigned long long it = E_of(p, t)[i];
         const int32_t u = (int32_t)(it >> 32);
         const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
         const int gu = gf_cur ? __ldg(p.node_graph + u) : 0;
@@ -443,22 +446,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
 #pragma unroll
         for (int q = 0; q < UNR; ++q)  // a bit already seen set needs no atomic
           claim[q] = cand[q] && !test_bit_live(Knext, x[q]) && !set_bit(Knext, x[q]);
+        uint32_t np[UNR];
 #pragma unroll
         for (int q = 0; q < UNR; ++q) {
-          unsigned long long np = 0;
-          int64_t rb = 0, indeg = 0;
+          np[q] = 0;
           if (claim[q]) {
-            rb = __ldg(p.row_ptr + x[q]);
-            indeg = __ldg(p.row_ptr + x[q] + 1) - rb;
+            const int64_t indeg = __ldg(p.row_ptr + x[q] + 1) - __ldg(p.row_ptr + x[q]);
             if (!p.pass_words) {  // passes as words: the pull counts each pass
               my_mact += (unsigned long long)indeg;
               my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
               ++my_rows;
             }
-            np = (unsigned long long)((indeg + p.L - 1) / p.L);
+            np[q] = (uint32_t)((indeg + p.L - 1) / p.L);
           }
-          warp_append_items(p.A, &ctrl->nA_next, x[q], rb, indeg, p.L, np, lane);
         }
+        // the step's claims of all lanes: one reservation in the work list
+        warp_append_items_n<UNR>(p.A, &ctrl->nA_next, p.row_ptr, x, p.L, np, lane);
       }
     }
   }
@@ -545,12 +548,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       ctrl->done = 1;
     } else {
       ctrl->t = t + 1;
-      ctrl->mode = p.gfsum ? kModeMixed : next_dense ? kModeDense : kModeSparse;
+      ctrl->mode = p.gfsum      ? kModeMixed
+                   : next_dense ? kModeDense
+                   : next_push  ? kModePush
+                                : kModeSparse;
       ctrl->test = (double)fsum < kTestDensity * (double)p.m ? 1 : 0;
       if (next_dense) ctrl->dense_rounds += 1;
       ctrl->nA = *(volatile unsigned long long *)&ctrl->nA_next;
       ctrl->nA_next = 0ULL;
       ctrl->fpack = 0ULL;
+      ctrl->nE_prev = ctrl->nE;
       ctrl->nE = 0ULL;
       if (t + 1 - ctrl->row_base >= p.row_cap) {
         ctrl->status = kStatusWindow;
@@ -976,6 +983,13 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     needs.push_back({&w.KW1, bm_bytes * (size_t)pl.Wp});
   }
   if (bs) needs.push_back({&w.seed_bits, sizeof(int32_t) * (size_t)sp});
+  // push rounds (one graph, rows gathered whole, PROPAGATE-P or one pass at
+  // a time): the frontier's out-arc pieces by round parity
+  // (the default for them: measured faster on the 4096^2 grid by 19%, on
+  // R-MAT 22 with s = 256 by 13% and on ER 10^6 with s = 128 by 11%)
+  const bool push = !bs && !pl.wide && !pw && pl.CW == pl.Wp && pl.CW <= 4 &&
+                    (cl.o.sparse_push == 2 || cl.o.sparse_push == 0);
+  if (push) needs.push_back({&w.E1, sizeof(unsigned long long) * (size_t)e_cap});
   if (bs && g->nseg > 0) {
     needs.push_back({&w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg});
     needs.push_back({&w.gthr, sizeof(unsigned long long) * (size_t)g->nseg});
@@ -1017,6 +1031,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.F0 = (int32_t *)w.F0.p;
   p.F1 = (int32_t *)w.F1.p;
   p.E = (unsigned long long *)w.E.p;
+  p.E1 = push ? (unsigned long long *)w.E1.p : nullptr;
+  p.push = push ? 1 : 0;
   p.A = (ulonglong2 *)w.A.p;
   p.Pall = (const ulonglong2 *)g->pieces.list.p;
   p.nPall = g->pieces.count;
@@ -1367,7 +1383,8 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
   if (opt) cl.o = *opt;
   if (cl.o.direction < 0 || cl.o.direction > 2) return PG_EINVAL;
   if (cl.o.pass_words < 0 || cl.o.test_changed < 0 || cl.o.test_changed > 3 ||
-      cl.o.tma_gather < 0 || cl.o.tma_gather > 2)
+      cl.o.tma_gather < 0 || cl.o.tma_gather > 2 || cl.o.sparse_push < 0 ||
+      cl.o.sparse_push > 2)
     return PG_EINVAL;
   cl.s_total = s;
   cl.max_rounds = out->max_rounds;
@@ -1623,8 +1640,12 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
 }
 
 int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows) {
+  return workspace_bytes_nm(g->n, g->m, s, max_rounds, window_rows);
+}
+
+int64_t workspace_bytes_nm(int64_t n, int64_t m, int32_t s, int32_t max_rounds,
+                           int32_t window_rows) {
   // the buffers run_pass ensures, sized for the widest plan of s seeds
-  const int64_t n = g->n, m = g->m;
   const int W = (s + 63) / 64;
   const int CW = W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : 8;
   const int64_t Wp = (W + CW - 1) / CW * CW;
@@ -1667,6 +1688,7 @@ void pg_default_options(pg_options *o) {
   o->passes_together = 0;
   o->pass_words = 0;
   o->tma_gather = 0;
+  o->sparse_push = 0;
 }
 
 pg_status pg_propagate_p(pg_graph *g, const int32_t *seeds, int32_t s, pg_counts *out,

@@ -132,8 +132,26 @@ void trim(Slot &sl) {
 struct Job {
   std::vector<Request *> reqs;
   int32_t graph = -1;
-  int64_t need = 0;  // slot bytes after the job
+  std::vector<int32_t> graphs;  // distinct graphs, first-taken first (several: a union)
+  int64_t need = 0;             // slot bytes after the job
 };
+
+// Largest packed union a cross-graph propagation builds.
+constexpr int64_t kUnionMaxNodes = 1LL << 22;
+constexpr int64_t kUnionMaxArcs = 1LL << 27;
+
+int width_class(int64_t s) {
+  const int64_t W = (s + 63) / 64;
+  return W <= 1 ? 1 : W <= 2 ? 2 : W <= 4 ? 4 : (int)((W + 7) / 8 * 8);
+}
+
+// Device bytes of the arrays of a union of n nodes and m arcs (directed:
+// with its out-CSR): its CSR copies, node map and relabelling map, and its
+// sliced-ELL copy and piece lists (the propagation's workspace is the slot's).
+int64_t union_array_bytes(int64_t n, int64_t m, bool directed) {
+  const int64_t csr = (n + 1) * 8 + m * 4;
+  return csr * (directed ? 2 : 1) + n * 8 + (n + m / 2 + 1) * 16 * 2 + m * 4;
+}
 
 // Bytes the slot will hold after running s seeds on graph gid.
 int64_t slot_need(const pg_server *srv, const Slot &sl, int32_t gid, int32_t s) {
@@ -155,6 +173,10 @@ bool pick(pg_server *srv, int k, Job &job) {
     Request *head = srv->reqs.at(srv->queue[qi]).get();
     std::vector<size_t> take{qi};
     int64_t s_total = (int64_t)head->seeds.size();
+    // same graph first (as without unions), then, with cross_graph, queued
+    // requests on other graphs whose seeds keep each graph within the
+    // signature width the head's graph reached (those graphs run as one
+    // union; a narrower graph only leaves words of its rows unused)
     for (size_t qj = qi + 1; qj < srv->queue.size(); ++qj) {
       if ((int32_t)take.size() >= srv->cfg.merge_max) break;
       Request *r = srv->reqs.at(srv->queue[qj]).get();
@@ -163,7 +185,50 @@ bool pick(pg_server *srv, int k, Job &job) {
       take.push_back(qj);
       s_total += (int64_t)r->seeds.size();
     }
-    int64_t need = slot_need(srv, me, head->graph, (int32_t)s_total);
+    std::vector<std::pair<int32_t, int64_t>> per{{head->graph, s_total}};
+    const pg_graph *hg = srv->graphs.at(head->graph).g;
+    const int cls = width_class(s_total);
+    int64_t un = hg->n, um = hg->m;
+    bool udir = hg->directed != 0;
+    int32_t umaxr = (int32_t)std::min<int64_t>(hg->n - 1, 0x3FFFFFFF);
+    const bool cross = srv->cfg.cross_graph && cls <= 8 && hg->n <= kUnionMaxNodes / 2;
+    for (size_t qj = qi + 1; cross && qj < srv->queue.size(); ++qj) {
+      if ((int32_t)take.size() >= srv->cfg.merge_max) break;
+      Request *r = srv->reqs.at(srv->queue[qj]).get();
+      if (r->graph == head->graph) continue;
+      const int64_t rs = (int64_t)r->seeds.size();
+      if (s_total + rs > srv->cfg.merge_max_seeds) continue;
+      auto it = std::find_if(per.begin(), per.end(),
+                             [&](const std::pair<int32_t, int64_t> &x) { return x.first == r->graph; });
+      if (it != per.end()) {
+        if (width_class(it->second + rs) > cls) continue;
+        it->second += rs;
+      } else {
+        if (width_class(rs) > cls) continue;
+        const pg_graph *g = srv->graphs.at(r->graph).g;
+        if (un + g->n > kUnionMaxNodes || um + g->m > kUnionMaxArcs) continue;
+        per.push_back({r->graph, rs});
+        un += g->n;
+        um += g->m;
+        udir = udir || g->directed;
+        umaxr = std::max<int32_t>(umaxr, (int32_t)std::min<int64_t>(g->n - 1, 0x3FFFFFFF));
+      }
+      take.push_back(qj);
+      s_total += rs;
+    }
+    int64_t smax = 0;
+    for (auto &x : per) smax = std::max(smax, x.second);
+    const bool uni = per.size() > 1;
+    auto need_now = [&]() {
+      if (!uni) return slot_need(srv, me, head->graph, (int32_t)s_total);
+      int64_t views = 0;
+      for (const auto &kv : me.views) views += view_bytes(kv.second);
+      return std::max(workspace_held(me.ws),
+                      workspace_bytes_nm(un, um, (int32_t)smax, umaxr,
+                                         srv->cfg.opt.window_rows)) +
+             views + union_array_bytes(un, um, udir);
+    };
+    int64_t need = need_now();
     const int64_t fixed = resident_total(srv);
     int64_t others = slots_total(srv) - me.held;
     auto fits = [&](int64_t nd) { return fixed + others + nd <= srv->budget; };
@@ -181,11 +246,13 @@ bool pick(pg_server *srv, int k, Job &job) {
     }
     if (!fits(need) && me.held > 0) {  // this slot's own cache may be in the way
       trim(me);
-      need = slot_need(srv, me, head->graph, (int32_t)s_total);
+      need = need_now();
     }
     if (!fits(need)) continue;  // a younger, smaller request may fit
+    std::sort(take.begin(), take.end());  // queue positions, erased from the back
     job.need = need;
     job.graph = head->graph;
+    for (auto &x : per) job.graphs.push_back(x.first);
     for (size_t t : take) job.reqs.push_back(srv->reqs.at(srv->queue[t]).get());
     for (auto it = take.rbegin(); it != take.rend(); ++it)
       srv->queue.erase(srv->queue.begin() + (std::ptrdiff_t)*it);
@@ -221,6 +288,118 @@ void split_window(void *vctx, int32_t row_base, int32_t rows, const uint32_t *da
   }
 }
 
+// Union builder: graph k's rows at node offset v0 and arc offset a0.
+__global__ void k_union_rows(const int64_t *rp, int64_t n, int64_t v0, int64_t a0, int64_t *rp_u,
+                             int32_t *node_graph, int32_t k, const int32_t *perm,
+                             int32_t *perm_u) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    rp_u[v0 + v] = rp[v] + a0;
+    node_graph[v0 + v] = k;
+    // a relabelled graph: the caller's id v0 + x maps to v0 + its internal id
+    if (perm_u) perm_u[v0 + v] = (int32_t)(v0 + (perm ? perm[v] : v));
+  }
+}
+
+__global__ void k_union_cols(const int32_t *col, int64_t m, int32_t v0, int64_t a0,
+                             int32_t *col_u) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x)
+    col_u[a0 + j] = col[j] + v0;
+}
+
+struct Union {
+  pg_graph *g = nullptr;
+  DevBuf node_graph, graph_s, graph_col0;
+  std::vector<int64_t> v0, graph_m;
+  int64_t last = 0;  // the last row pointer, the source of its copy
+  ~Union() {
+    if (g) pg_graph_free(g);
+    release(node_graph);
+    release(graph_s);
+    release(graph_col0);
+  }
+};
+
+// Packs the resident graphs `parts` into one disjoint union on the device (a
+// packed batch, as build_groups does from host CSRs), with each part's seed
+// count s[k] and first count column col0[k].
+pg_status build_union(const std::vector<const pg_graph *> &parts, const std::vector<int32_t> &s,
+                      const std::vector<int32_t> &col0, cudaStream_t st, Union &u) {
+  const int K = (int)parts.size();
+  int64_t n = 0, m = 0;
+  bool directed = false, perm = false;
+  int64_t maxdeg = 0;
+  for (const pg_graph *g : parts) {
+    u.v0.push_back(n);
+    u.graph_m.push_back(g->m);
+    n += g->n;
+    m += g->m;
+    directed = directed || g->directed;
+    perm = perm || g->perm_ptr;
+    maxdeg = std::max(maxdeg, g->max_degree);
+  }
+  pg_graph *ug = new pg_graph();
+  u.g = ug;
+  ug->n = n;
+  ug->m = m;
+  ug->directed = directed ? 1 : 0;
+  cudaGetDevice(&ug->device);
+  ug->max_degree = maxdeg;
+  ug->mean_degree = (double)m / (double)std::max<int64_t>(n, 1);
+  pg_status rc = cuda_status(cudaMalloc((void **)&ug->row_ptr, sizeof(int64_t) * (n + 1)));
+  if (!rc) rc = cuda_status(cudaMalloc((void **)&ug->col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+  if (!rc && directed) {
+    rc = cuda_status(cudaMalloc((void **)&ug->out_ptr, sizeof(int64_t) * (n + 1)));
+    if (!rc) rc = cuda_status(cudaMalloc((void **)&ug->out_col, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+  } else if (!rc) {
+    ug->out_ptr = ug->row_ptr;
+    ug->out_col = ug->col;
+    ug->owns_out = false;
+  }
+  if (!rc) rc = ensure(u.node_graph, sizeof(int32_t) * (size_t)n);
+  if (!rc && perm) rc = ensure(ug->perm, sizeof(int32_t) * (size_t)n);
+  if (!rc) rc = ensure(u.graph_s, sizeof(int32_t) * (size_t)K);
+  if (!rc) rc = ensure(u.graph_col0, sizeof(int32_t) * (size_t)K);
+  int64_t a0 = 0;
+  for (int k = 0; k < K && !rc; ++k) {
+    const pg_graph *g = parts[k];
+    const int blocks = (int)std::min<int64_t>(4096, (std::max(g->n, g->m) + kBlock - 1) / kBlock);
+    k_union_rows<<<blocks, kBlock, 0, st>>>(g->row_ptr, g->n, u.v0[k], a0, ug->row_ptr,
+                                            (int32_t *)u.node_graph.p, k, g->perm_ptr,
+                                            perm ? (int32_t *)ug->perm.p : nullptr);
+    k_union_cols<<<blocks, kBlock, 0, st>>>(g->col, g->m, (int32_t)u.v0[k], a0, ug->col);
+    if (directed) {
+      k_union_rows<<<blocks, kBlock, 0, st>>>(g->out_ptr, g->n, u.v0[k], a0, ug->out_ptr,
+                                              (int32_t *)u.node_graph.p, k, nullptr, nullptr);
+      k_union_cols<<<blocks, kBlock, 0, st>>>(g->out_col, g->m, (int32_t)u.v0[k], a0,
+                                              ug->out_col);
+    }
+    rc = cuda_status(cudaGetLastError());
+    a0 += g->m;
+  }
+  if (!rc) {  // the last row pointer, m (its source outlives the synchronisation below)
+    u.last = m;
+    rc = cuda_status(cudaMemcpyAsync(ug->row_ptr + n, &u.last, sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    if (!rc && directed)
+      rc = cuda_status(cudaMemcpyAsync(ug->out_ptr + n, &u.last, sizeof(int64_t),
+                                       cudaMemcpyHostToDevice, st));
+    if (!rc)
+      rc = cuda_status(cudaMemcpyAsync(u.graph_s.p, s.data(), sizeof(int32_t) * K,
+                                       cudaMemcpyHostToDevice, st));
+    if (!rc)
+      rc = cuda_status(cudaMemcpyAsync(u.graph_col0.p, col0.data(), sizeof(int32_t) * K,
+                                       cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+  }
+  if (rc) return rc;
+  ug->seg_of = (const int32_t *)u.node_graph.p;
+  ug->nseg = K;
+  if (perm) ug->perm_ptr = (const int32_t *)ug->perm.p;
+  return PG_OK;
+}
+
 void worker(pg_server *srv, int k) {
   cudaSetDevice(srv->device);
   Slot &me = *srv->slots[k];
@@ -248,32 +427,76 @@ void worker(pg_server *srv, int k) {
     }
     // outside the lock: the propagation
     pg_status rc = PG_OK;
-    pg_graph *view = nullptr;
-    auto it = me.views.find(job.graph);
-    if (it != me.views.end()) {
-      view = it->second;
-    } else {
-      rc = make_view(master, me.stream, &view);
-      if (rc == PG_OK) {
-        view->ext_ws = &me.ws;
-        me.views[job.graph] = view;
-      }
-    }
     Split sp;
-    std::vector<int32_t> seeds;
-    for (Request *r : job.reqs) {
-      sp.reqs.push_back(r);
-      sp.col0.push_back((int32_t)seeds.size());
-      seeds.insert(seeds.end(), r->seeds.begin(), r->seeds.end());
-      r->counts.clear();
-      r->open = true;
-    }
     pg_stats pst{};
     int32_t T = 0;
-    if (rc == PG_OK) {
-      const int32_t maxr = (int32_t)std::min<int64_t>(master->n - 1, 0x3FFFFFFF);
-      rc = propagate_columns(view, seeds.data(), (int32_t)seeds.size(), maxr, &split_window, &sp,
-                             &T, &srv->cfg.opt, me.stream, &pst);
+    if (job.graphs.size() <= 1) {
+      pg_graph *view = nullptr;
+      auto it = me.views.find(job.graph);
+      if (it != me.views.end()) {
+        view = it->second;
+      } else {
+        rc = make_view(master, me.stream, &view);
+        if (rc == PG_OK) {
+          view->ext_ws = &me.ws;
+          me.views[job.graph] = view;
+        }
+      }
+      std::vector<int32_t> seeds;
+      for (Request *r : job.reqs) {
+        sp.reqs.push_back(r);
+        sp.col0.push_back((int32_t)seeds.size());
+        seeds.insert(seeds.end(), r->seeds.begin(), r->seeds.end());
+        r->counts.clear();
+        r->open = true;
+      }
+      if (rc == PG_OK) {
+        const int32_t maxr = (int32_t)std::min<int64_t>(master->n - 1, 0x3FFFFFFF);
+        rc = propagate_columns(view, seeds.data(), (int32_t)seeds.size(), maxr, &split_window,
+                               &sp, &T, &srv->cfg.opt, me.stream, &pst);
+      }
+    } else {
+      // several graphs: their requests' seeds as one packed union, each
+      // graph's columns together (its requests in queue order)
+      std::vector<const pg_graph *> parts;
+      std::vector<int32_t> gs, gc0, seeds, bits;
+      {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (int32_t gid : job.graphs) parts.push_back(srv->graphs.at(gid).g);
+      }
+      Union u;
+      int32_t maxr = 0;
+      for (size_t gk = 0; gk < job.graphs.size(); ++gk) {
+        int32_t sk = 0;
+        gc0.push_back((int32_t)seeds.size());
+        maxr = std::max<int32_t>(maxr, (int32_t)std::min<int64_t>(parts[gk]->n - 1, 0x3FFFFFFF));
+        for (Request *r : job.reqs) {
+          if (r->graph != job.graphs[gk]) continue;
+          sp.reqs.push_back(r);
+          sp.col0.push_back((int32_t)seeds.size());
+          for (int32_t x : r->seeds) {
+            seeds.push_back(x);  // the caller's id; the union's offset is added below
+            bits.push_back(sk++);
+          }
+          r->counts.clear();
+          r->open = true;
+        }
+        gs.push_back(sk);
+      }
+      rc = build_union(parts, gs, gc0, me.stream, u);
+      if (rc == PG_OK) {
+        for (size_t gk = 0, i = 0; gk < job.graphs.size(); ++gk)
+          for (int32_t b = 0; b < gs[gk]; ++b, ++i) seeds[i] += (int32_t)u.v0[gk];
+        u.g->ext_ws = &me.ws;
+        int32_t smax = 0;
+        for (int32_t x : gs) smax = std::max(smax, x);
+        rc = propagate_batch_group(u.g, seeds.data(), bits.data(), (int32_t)seeds.size(),
+                                   (const int32_t *)u.node_graph.p,
+                                   (const int32_t *)u.graph_s.p, (const int32_t *)u.graph_col0.p,
+                                   u.graph_m.data(), (int32_t)seeds.size(), smax, maxr,
+                                   &split_window, &sp, &T, &srv->cfg.opt, me.stream, &pst);
+      }
+      cudaStreamSynchronize(me.stream);  // the union's arrays are freed next
     }
     {
       std::lock_guard<std::mutex> lk(srv->mu);
@@ -340,6 +563,7 @@ void pg_server_default_config(pg_server_config *cfg) {
   cfg->slots = 4;
   cfg->merge_max = 16;
   cfg->merge_max_seeds = 8192;
+  cfg->cross_graph = 1;
   cfg->hbm_budget = 0;
   pg_default_options(&cfg->opt);
 }

@@ -1,6 +1,7 @@
 // Autotuner (pg_autotune, pg_batch_tune): coordinate descent over the
-// schedule options that leave the counts unchanged — words a lane gathers per
-// arc, lanes per work piece, the dense-round threshold, the changed-bit test.
+// schedule options that leave the counts unchanged — PROPAGATE-S's pass
+// schedule, push or pull sparse rounds, words a lane gathers per arc, lanes
+// per work piece, the dense-round threshold, the changed-bit test.
 // Every candidate runs the real propagation twice (the faster run is kept, so
 // one-time costs such as a new piece list or a graph capture do not count);
 // its counts must hash to the same value as the first run's.
@@ -97,6 +98,11 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
   if (W > 8) {  // a warp per row piece, or lanes over 8-word chunks
     pg_options o = cur;
     o.wide_rows = cur.wide_rows == 2 ? 0 : 2;
+    if ((rc = try_value(o))) return rc;
+  }
+  if (W <= 4) {  // sparse rounds pushed from the frontier instead of pulled
+    pg_options o = cur;
+    o.sparse_push = cur.sparse_push == 1 ? 0 : 1;
     if ((rc = try_value(o))) return rc;
   }
   const bool wide = W > 8 && cur.wide_rows != 2;  // lanes and chunk width then fixed

@@ -98,7 +98,7 @@ def test_struct_layouts_match_the_header(tmp_path):
              "pg_metrics_out": _abi.MetricsOut, "pg_stats": _abi.Stats,
              "pg_tune_report": _abi.TuneReport, "pg_batch_stats": _abi.BatchStats,
              "pg_server_config": _abi.ServerConfig, "pg_request_info": _abi.RequestInfo,
-             "pg_server_stats": _abi.ServerStats}
+             "pg_server_stats": _abi.ServerStats, "pg_generator": _abi.Generator}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "propagate.h"',
              "int main(void) {"]
     for cname, cls in pairs.items():

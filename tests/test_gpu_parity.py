@@ -70,10 +70,12 @@ def test_cfg1_er_propagate_p_default():
 @pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("test_changed", [1, 2])
-def test_cfg1_every_schedule_identical(direction, lanes, test_changed):
+@pytest.mark.parametrize("sparse_push", [1, 2])
+def test_cfg1_every_schedule_identical(direction, lanes, test_changed, sparse_push):
     g, seeds, want = _cfg1()
     G = pg.Graph.from_inputs(g)
-    o = pg.options(direction=direction, group_lanes=lanes, test_changed=test_changed)
+    o = pg.options(direction=direction, group_lanes=lanes, test_changed=test_changed,
+                   sparse_push=sparse_push)
     _assert_same(pg.propagate_p(G, seeds, opts=o), want)
 
 
@@ -528,3 +530,51 @@ def test_debug_bounds_build_gives_the_oracles_counts():
                          text=True, timeout=1200)
     assert out.returncode == 0, out.stderr[-3000:]
     assert "debug-bounds ok" in out.stdout
+
+
+# ------------------------------------------------------------ push rounds
+@pytest.mark.parametrize("case", ["er", "grid", "rmat_directed", "star", "path"])
+def test_push_rounds_match_the_oracle(case):
+    """sparse_push = 2: sparse rounds OR each changed row's delta into its
+    out-neighbours with atomics (claims counted on the way); counts, m_active
+    and active rows equal the oracle's in every direction, for PROPAGATE-P
+    and PROPAGATE-S one pass at a time, with captured and plain launches."""
+    if case == "er":
+        g, seeds = _cfg1()[0], _cfg1()[1]
+    elif case == "grid":
+        g = I.grid(90, 70, 0.05, 221)
+        seeds = I.seeds(g.n, 128, 222)
+    elif case == "rmat_directed":
+        g = I.rmat(12, 16, 223, directed=True)
+        seeds = I.seeds(g.n, 256, 224)
+    elif case == "star":
+        g = I.star(5000)
+        seeds = I.seeds(g.n, 65, 225)
+    else:
+        g = I.path(1500)
+        seeds = np.array([0, 700, 1499], np.int32)
+    want = _oracle_p(g, seeds)
+    rows = int(_active_rows_from_distances(g, seeds).sum())
+    G = pg.Graph.from_inputs(g)
+    for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_SPARSE):
+        for extra in (dict(), dict(timing=1), dict(test_changed=1), dict(group_lanes=4)):
+            res = pg.propagate_p(G, seeds, opts=pg.options(direction=direction, sparse_push=2,
+                                                           **extra))
+            _assert_same(res, want)
+            assert G.last_stats()["active_rows"] == rows
+    one = pg.options(sparse_push=2, pass_words=1, passes_together=1, direction=pg.PG_DIR_SPARSE)
+    res_s = pg.propagate_s(G, seeds, opts=one)
+    assert res_s.rounds == want["rounds"] and np.array_equal(res_s.counts, want["counts"])
+    assert np.array_equal(res_s.m_active,
+                          _oracle_s_mactive(g, seeds, 64, want["rounds"])[:res_s.m_active.size])
+
+
+def test_push_rounds_reverse_and_relabelled():
+    """Push rounds over the transpose (PG_REVERSE) of a relabelled digraph."""
+    g = I.rmat(12, 8, 226, directed=True)
+    seeds = I.seeds(g.n, 100, 227)
+    want = oracle.run(_transpose(g), seeds)
+    G = pg.Graph.from_inputs(g, reverse=True, relabel=True)
+    res = pg.propagate_p(G, seeds, opts=pg.options(sparse_push=2, direction=pg.PG_DIR_SPARSE))
+    assert res.rounds == want["rounds"] and np.array_equal(res.counts, want["counts"])
+    assert np.array_equal(res.m_active, want["m_active"])

@@ -2,7 +2,8 @@
 (pg_propagate_p on its own graph handle) and in the mix, whatever it was
 merged with, whichever slot ran it and whenever it arrived; admission keeps
 the charged device memory within the budget; queued requests on one graph
-are merged; cancel and remove behave as documented."""
+are merged, and requests on graphs of one signature width run as a packed
+union; cancel and remove behave as documented."""
 import functools
 import threading
 import time
@@ -77,7 +78,7 @@ def test_queued_requests_on_one_graph_are_merged():
     g = _pool()[0]
     sets = [I.seeds(g.n, s, 100 + k) for k, s in enumerate((64, 100, 3, 256, 64))]
     sets[4] = sets[0].copy()  # identical seed set
-    with pg.Server(slots=1) as srv:
+    with pg.Server(slots=1, cross_graph=False) as srv:
         lg = srv.add_inputs(long_g)
         gid = srv.add_inputs(g)
         first = srv.submit(lg, I.seeds(long_g.n, 64, 5))
@@ -202,3 +203,34 @@ def test_server_rejects_bad_requests():
             srv.submit(gid + 17, np.array([0], np.int32))
         rid = srv.submit(gid, np.array([1, 2], np.int32))
         assert srv.wait(rid, 10_000)["state"] == _abi.PG_REQ_DONE
+
+
+def test_requests_on_different_graphs_run_as_one_union():
+    """One slot busy with a long propagation; requests queue behind it on
+    five graphs (a relabelled R-MAT, a digraph, a grid, an ER graph and a
+    small mixed one). Those of one signature width (two words) are merged
+    across graphs into a packed union; a wider request runs on its own.
+    Every answer equals the request alone."""
+    long_g = I.grid(800, 800, 0.05, 31)
+    graphs = [I.rmat(17, 8, 32, directed=False), I.rmat(12, 16, 33, directed=True),
+              I.grid(120, 90, 0.05, 34), I.er(5000, 6, 35), _pool()[1]]
+    reqs = []
+    for k, g in enumerate(graphs):
+        for j, sz in enumerate((100, 70)):  # two words each
+            reqs.append((k, I.seeds(g.n, sz, 40 + 10 * k + j)))
+    reqs.append((0, I.seeds(graphs[0].n, 300, 99)))  # five words: another width
+    with pg.Server(slots=1) as srv:
+        lg = srv.add_inputs(long_g)
+        gids = [srv.add_inputs(g) for g in graphs]
+        first = srv.submit(lg, I.seeds(long_g.n, 512, 5))
+        rids = [srv.submit(gids[k], sd) for k, sd in reqs]
+        srv.result(first)
+        merged = []
+        for rid, (k, sd) in zip(rids, reqs):
+            res, info = srv.result(rid)
+            merged.append(info["merged"])
+            _check_same(graphs[k], sd, res)
+        st = srv.stats()
+    assert max(merged[:-1]) > 2  # more requests in one run than any one graph had
+    assert st["propagations"] < 1 + len(reqs)
+    assert st["completed"] == 1 + len(reqs) and st["failed"] == 0
