@@ -218,6 +218,8 @@ def kernel_name(st: dict) -> str:
     """Name of the pull kernel instantiation a call used (words per gather,
     lanes per group, PROPAGATE-S passes as words), as ncu prints it."""
     wp, cw = st["words_per_row"], st["words_per_gather"]
+    if st.get("dense_tma"):  # dense rounds by TMA gathers (sparse ones by k_pull)
+        return f"k_pull_tma<{cw}, {1 if st.get('pass_words', 1) > 1 else 0}>"
     if cw == 0:  # the wide-row kernel: words per lane held in registers
         nw = 1 if wp <= 32 else 2 if wp <= 64 else 3 if wp <= 96 else 4 if wp <= 128 else 0
         return f"k_pull_wide<{nw}, {1 if st.get('pass_words', 1) > 1 else 0}>"
@@ -369,13 +371,26 @@ def run_ours(args):
             traffic_table = {k: v for k, v in tr.get("bytes_per_launch", {}).items()
                              if isinstance(hashes, dict) and hashes.get(k) == kernel_hash(k)}
 
+    def traffic_of(name):
+        """DRAM bytes per launch of this pull kernel, from the stored capture
+        of the same sources: the same instantiation, else one that differs
+        only in lanes per sparse-round piece (the dense sweep, which moves
+        almost all the bytes, is the same code)."""
+        if name in traffic_table:
+            return traffic_table[name]
+        fam = name.split(",")[0] + "," + name.split(",")[-1]
+        for k, v in traffic_table.items():
+            if k.split(",")[0] + "," + k.split(",")[-1] == fam:
+                return v
+        return None
+
     def roofline_of(name):
         ms, nl, design, alg, post = per_kernel[name]
         nl = max(nl, 1)
         ach = (alg / nl) / ((ms / nl) / 1e3) / 1e9
         design_ach = (design / nl) / ((ms / nl) / 1e3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": traffic_table.get(name), "kernel": name,
+                "traffic": traffic_of(name), "kernel": name,
                 "algorithmic_bytes_per_launch": alg / nl,
                 "bytes_basis": "per round |A_t|(8+s/4) + m_active(t)(4+s/8) + |F_t|*4 "
                                "(s = 64 per pass for PROPAGATE-S), from the library's own "
@@ -893,6 +908,8 @@ def kernel_hash(kernel: str) -> str:
     csrc = os.path.join(ROOT, "paper_2301_06499_gb300", "csrc")
     if kernel.startswith("k_pull_wide"):
         own = "pull_wide.cu"
+    elif kernel.startswith("k_pull_tma"):
+        own = "pull_tma.cu"
     else:
         m = re.match(r"k_pull<(\d+)", kernel)
         own = f"pull_cw{m.group(1)}.cu" if m else ""
@@ -1064,10 +1081,10 @@ def write_traffic(workload: str, csvs: list, out_path: str | None = None) -> dic
            "kernel_hash": {k: kernel_hash(k) for k in per},
            "bytes_per_launch": per,
            "commands": [
-               "python bench.py --profile-run p",
+               f"python bench.py --profile-run p --workload {workload}",
                "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                "--nvtx --nvtx-include bench_call/ --clock-control none -k regex:k_pull --csv "
-               "--log-file traffic_p.csv python bench.py --profile-run p",
+               f"--log-file traffic_p.csv python bench.py --profile-run p --workload {workload}",
                "(the same two lines with --profile-run s -> traffic_s.csv)",
                "python bench.py --workload " + workload +
                " --write-traffic traffic_p.csv traffic_s.csv"],
