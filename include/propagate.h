@@ -178,16 +178,20 @@ typedef struct {
                                loaded by each lane; 0 or 1 = per-lane loads
                                (the default: they measured faster on a 2^26-
                                node graph with 8-word rows) */
-  int32_t sparse_push;      /* sparse rounds: 2 = push, each row that changed
-                               in the previous round ORs its delta into its
-                               out-neighbours with atomics (their claims for
-                               m_active made on the way); 1 = pull, the post
+  int32_t sparse_push;      /* sparse rounds: 0 (default) or 2 = push, each
+                               row that changed in the previous round ORs
+                               its delta into its out-neighbours with
+                               atomics (their claims for m_active made on
+                               the way), where it applies: rows of up to 8
+                               words (s <= 512) gathered whole, PROPAGATE-P
+                               or PROPAGATE-S one pass at a time, one graph
+                               or a packed batch (pg_batch_run: its graphs
+                               below their dense threshold push while the
+                               others are swept whole); 1 = pull, the post
                                kernel claims the frontier's out-neighbours
-                               and the pull gathers their in-arcs; 0 = push
-                               where it applies: one graph with rows of up
-                               to 4 words (s <= 256) gathered whole,
-                               PROPAGATE-P or PROPAGATE-S one pass at a
-                               time; pull elsewhere */
+                               and the pull gathers their in-arcs (always
+                               for rows above 8 words and PROPAGATE-S
+                               passes run as words) */
 } pg_options;
 
 #define PG_DIR_AUTO 0
@@ -406,14 +410,16 @@ pg_status pg_last_stats(const pg_graph *g, pg_stats *out);
  * the GPU's free parameters are the lanes per work piece (group_lanes), the
  * signature words a lane gathers per arc (words_per_thread) and the
  * frontier density at which a round becomes a full sweep (dense_threshold),
- * plus whether changed bits are tested before delta gathers. pg_autotune
+ * whether changed bits are tested before delta gathers (test_changed) and
+ * whether sparse rounds push or pull (sparse_push). pg_autotune
  * times PROPAGATE-P (algorithm PG_ALG_P) or PROPAGATE-S (PG_ALG_S) on g
  * with these seeds under candidate values, one
  * parameter at a time starting from *inout (coordinate descent; a candidate
  * replaces the current value when it is at least 2% faster), and writes the
  * fastest options back to *inout. Every candidate's counts are compared
  * with the first run's; a difference returns PG_EDEVICE. max_trials bounds
- * the timed propagations (each candidate is run twice, the faster kept).
+ * the timed propagations (each candidate is run three times, the fastest
+ * kept).
  * Errors: as pg_propagate_p.
  */
 typedef struct {

@@ -130,6 +130,7 @@ struct Params {
   int32_t test_adapt;   // decide test_changed per round (ctrl->test, set by the post kernel)
   int32_t dense_tma;    // dense rounds are swept by k_pull_tma (launched before k_pull)
   int32_t push;         // sparse rounds push from the previous frontier (kModePush)
+  int32_t push_kernel;  // ... in k_push, launched after the pull (else inside k_pull)
   int32_t use_cond;     // launched inside a conditional while-graph
   int32_t iter_guard;   // post launches after which a pass is abandoned
   unsigned long long cond;  // cudaGraphConditionalHandle of that graph

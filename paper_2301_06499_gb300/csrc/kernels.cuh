@@ -309,6 +309,34 @@ __device__ __forceinline__ void frontier_append_n(const Params &p, Ctrl *ctrl, i
       nesum += (od + p.LE - 1) / p.LE;
     }
   if (!__any_sync(kFullMask, cnt != 0)) return;
+  if (p.gfsum) {  // a packed batch: each graph's own frontier out-arcs
+    // (a lane's rows are the out-neighbours of one row, so of one graph: one
+    // atomic per warp when the warp's rows are all of one graph)
+    unsigned long long *gf = p.gfsum + (size_t)(ctrl->t & 1) * (size_t)p.nseg;
+    int gid = -1;
+    unsigned long long gs = 0;
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+      if (app[q]) {
+        const unsigned long long od =
+            (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
+        const int gq = __ldg(p.node_graph + v[q]);
+        if (gid < 0) gid = gq;
+        if (gq == gid)
+          gs += od;
+        else if (od)
+          atomicAdd(gf + gq, od);
+      }
+    const unsigned has = __ballot_sync(kFullMask, gid >= 0);
+    const int g0 = __shfl_sync(kFullMask, gid, __ffs(has) - 1);
+    if (__all_sync(kFullMask, gid < 0 || gid == g0)) {
+      unsigned long long gtot;
+      warp_excl_scan64(gs, lane, &gtot);
+      if (lane == 0 && gtot) atomicAdd(gf + g0, gtot);
+    } else if (gs) {
+      atomicAdd(gf + gid, gs);
+    }
+  }
   unsigned long long tot;
   const unsigned long long ex =
       warp_excl_scan64(((unsigned long long)cnt << kFsumBits) + odsum, lane, &tot);
@@ -764,8 +792,16 @@ __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const Rou
     uint64_t d[CW];
 #pragma unroll
     for (int k = 0; k < CW; ++k) d[k] = 0ULL;
-    if (i < nEp) {
-      const unsigned long long it = Ep[i];
+    bool live = i < nEp;
+    unsigned long long it = 0;
+    if (live) {
+      it = Ep[i];
+      if (p.gfsum) {  // a packed batch: graphs swept whole this round take no push
+        const int gu = __ldg(p.node_graph + (int32_t)(it >> 32));
+        live = p.gfsum[(size_t)((t - 1) & 1) * (size_t)p.nseg + gu] <= __ldg(p.gthr + gu);
+      }
+    }
+    if (live) {
       const int32_t u = (int32_t)(it >> 32);
       const int64_t k = (int64_t)(it & 0xFFFFFFFFULL);
       const int64_t o1 = __ldg(p.out_ptr + u + 1);
@@ -868,16 +904,20 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   if (mode == kModeSparse || mode == kModeMixed)
     pull_sparse<CW, G, PW>(p, ctrl, rb, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
                            my_items, my_rows);
-  // push rounds for rows of up to 4 words (the 8-word kernel keeps its
-  // registers for the dense sweep)
+  // push rounds for rows of up to 4 words of one graph (8-word rows and
+  // packed batches push in k_push, launched after this kernel: the 8-word
+  // kernel keeps its registers for the dense sweep)
   if constexpr (!PW && CW <= 4)
-    if (mode == kModePush)
+    if (mode == kModePush && !p.push_kernel)
       pull_push<CW>(p, ctrl, rb, t, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
                     my_items, my_rows);
   pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 
 using PullFn = void (*)(Params);
+// Push rounds as a kernel of their own (k_push<CW>, push.cu): 8-word rows and
+// packed batches; it returns at once in rounds that are not pushed.
+PullFn push_fn(int CW);
 // Dense rounds with TMA-gathered deltas (pull_tma.cu), for rows of CW = 4 or
 // 8 words: the kernel, its dynamic shared memory, its launch, and the tensor
 // map (a CUtensorMap, 128 bytes) over a delta buffer of `rows` rows.

@@ -400,9 +400,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
       !p.gfsum && (p.direction == PG_DIR_DENSE ||
                    (p.direction == PG_DIR_AUTO &&
                     (double)fsum > (double)p.dense_threshold * (double)p.m));
-  // a push round reads this frontier's out-arcs itself: nothing to claim here
+  // a push round reads this frontier's out-arcs itself: nothing to claim
+  // here (a packed batch that pushes: its sparse graphs push, none expands)
   const bool next_push = !next_dense && p.push && !p.gfsum;
-  const bool expand = !next_dense && !next_push && nF > 0 && t + 1 <= p.max_rounds + 1;
+  const bool expand =
+      !next_dense && !next_push && !(p.gfsum && p.push) && nF > 0 && t + 1 <= p.max_rounds + 1;
   // a packed batch decides per graph: a graph whose frontier out-arcs exceed
   // its own threshold is swept whole in round t+1 and not expanded here
   const unsigned long long *gf_cur = p.gfsum ? p.gfsum + (size_t)(t & 1) * (size_t)p.nseg : nullptr;
@@ -605,6 +607,8 @@ struct Plan {
   bool post_wide = false;  // k_post's tiled part A (rows of 16+ words, one graph)
   bool pw = false;         // PROPAGATE-S passes as words
   bool tma = false;        // dense rounds by k_pull_tma (TMA-gathered deltas)
+  PullFn push = nullptr;   // k_push<CW>, launched after the pull (8-word rows, batches)
+  int grid_push = 0;
   int grid_tma = 0;
   CUtensorMap tm0, tm1;    // over D0 and D1 (n + 1 rows)
 };
@@ -715,7 +719,11 @@ static void launch_post(const Plan &pl, const Params &p, cudaStream_t st) {
 static void launch_pulls(const Plan &pl, const Params &p, cudaStream_t st) {
   if (pl.tma) launch_pull_tma(pl.CW, pl.pw, p, &pl.tm0, &pl.tm1, pl.grid_tma, st);
   pl.pull<<<pl.grid_pull, kBlock, 0, st>>>(p);
+  if (pl.push) pl.push<<<pl.grid_push, kBlock, 0, st>>>(p);
 }
+
+// kernel launches of one round: the pulls and the post kernel
+static int round_launches(const Plan &pl) { return 2 + (pl.tma ? 1 : 0) + (pl.push ? 1 : 0); }
 
 static void launch_round(const Plan &pl, const Params &p, cudaStream_t st) {
   launch_pulls(pl, p, st);
@@ -821,6 +829,8 @@ struct GraphCache {
   bool post_wide = false;
   bool tma = false;
   int grid_tma = 0;
+  PullFn push = nullptr;
+  int grid_push = 0;
   unsigned char tm[2][sizeof(CUtensorMap)] = {};
   cudaStream_t cap = nullptr;
 };
@@ -845,6 +855,7 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   if (c.exec && c.pull == pl.pull && c.grid_pull == pl.grid_pull &&
       c.grid_post == pl.grid_post && c.smem == pl.post_smem && c.smem_counts == pl.smem_counts &&
       c.post_wide == pl.post_wide && c.tma == pl.tma && c.grid_tma == pl.grid_tma &&
+      c.push == pl.push && c.grid_push == pl.grid_push &&
       (!pl.tma || (std::memcmp(c.tm[0], &pl.tm0, sizeof(CUtensorMap)) == 0 &&
                    std::memcmp(c.tm[1], &pl.tm1, sizeof(CUtensorMap)) == 0)) &&
       std::memcmp(&c.p, &key, sizeof(Params)) == 0) {
@@ -902,6 +913,8 @@ static pg_status ensure_while_graph(pg_graph *g, const Plan &pl, const Params &p
   c.post_wide = pl.post_wide;
   c.tma = pl.tma;
   c.grid_tma = pl.grid_tma;
+  c.push = pl.push;
+  c.grid_push = pl.grid_push;
   std::memcpy(c.tm[0], &pl.tm0, sizeof(CUtensorMap));
   std::memcpy(c.tm[1], &pl.tm1, sizeof(CUtensorMap));
   *out = c.exec;
@@ -983,12 +996,13 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     needs.push_back({&w.KW1, bm_bytes * (size_t)pl.Wp});
   }
   if (bs) needs.push_back({&w.seed_bits, sizeof(int32_t) * (size_t)sp});
-  // push rounds (one graph, rows gathered whole, PROPAGATE-P or one pass at
-  // a time): the frontier's out-arc pieces by round parity
-  // (the default for them: measured faster on the 4096^2 grid by 19%, on
-  // R-MAT 22 with s = 256 by 13% and on ER 10^6 with s = 128 by 11%)
-  const bool push = !bs && !pl.wide && !pw && pl.CW == pl.Wp && pl.CW <= 4 &&
-                    (cl.o.sparse_push == 2 || cl.o.sparse_push == 0);
+  // push rounds (rows of up to 8 words gathered whole, PROPAGATE-P or one
+  // pass at a time): the frontier's out-arc pieces by round parity. The
+  // default where they apply: measured faster on the 4096^2 grid by 19%, on
+  // R-MAT 22 with s = 256 by 13%, on ER 10^6 with s = 128 by 11%, on R-MAT
+  // 26 with s = 512 by 10% and on the 512-graph mix (batched) by 3%
+  const bool push_ok = !pl.wide && !pw && pl.CW == pl.Wp;
+  const bool push = push_ok && cl.o.sparse_push != 1;
   if (push) needs.push_back({&w.E1, sizeof(unsigned long long) * (size_t)e_cap});
   if (bs && g->nseg > 0) {
     needs.push_back({&w.gfsum, 2 * sizeof(unsigned long long) * (size_t)g->nseg});
@@ -1033,6 +1047,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.E = (unsigned long long *)w.E.p;
   p.E1 = push ? (unsigned long long *)w.E1.p : nullptr;
   p.push = push ? 1 : 0;
+  const bool push_kernel = push && (bs != nullptr || pl.CW == 8);
+  p.push_kernel = push_kernel ? 1 : 0;
+  pl.push = push_kernel ? push_fn(pl.CW) : nullptr;
   p.A = (ulonglong2 *)w.A.p;
   p.Pall = (const ulonglong2 *)g->pieces.list.p;
   p.nPall = g->pieces.count;
@@ -1103,6 +1120,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
 
   const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
+  if (pl.push) pl.grid_push = occupancy_grid((const void *)pl.push, 0, n + g->m / kExpandArcs + 1);
   // the wide part A has a warp per 32 rows x 16 words
   const int64_t post_threads =
       pl.post_wide ? (n + 31) / 32 * (int64_t)((pl.Wp + 15) / 16) * 32 : n;
@@ -1189,9 +1207,9 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       fin = c;
       finished = true;
     }
-    // every round of the loop is one pull and one post launch; iters counts
-    // the post launches of the pass, post(0) included
-    po.launches = 3 + (pl.tma ? 3 : 2) * (std::max(0, fin.iters) - 1);
+    // every round of the loop is its pull launches and one post launch;
+    // iters counts the post launches of the pass, post(0) included
+    po.launches = 3 + round_launches(pl) * (std::max(0, fin.iters) - 1);
   } else {
     // Host-driven loop: batches of K rounds; the host reads the control
     // block of the batch before last while the last one runs. A first batch
@@ -1213,7 +1231,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
           launch_round(pl, p, st);
         }
       }
-      po.launches += (pl.tma ? 3 : 2) * hint;
+      po.launches += round_launches(pl) * hint;
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
       Ctrl cnow;
       if ((rc = cuda_status(cudaMemcpyAsync(&w.ctrl_h[0], p.ctrl, sizeof(Ctrl),
@@ -1248,7 +1266,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
         }
       }
       enqueued += K;
-      po.launches += (pl.tma ? 3 : 2) * K;
+      po.launches += round_launches(pl) * K;
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
       cudaMemcpyAsync(&w.ctrl_h[slot], p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
       cudaEventRecord(w.ev[slot], st);
@@ -1654,8 +1672,10 @@ int64_t workspace_bytes_nm(int64_t n, int64_t m, int32_t s, int32_t max_rounds,
   const int64_t cap_rows =
       window_rows > 0 ? window_rows : std::max<int64_t>(64, (256LL << 20) / (4LL * s));
   const int64_t row_cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
-  return 4 * n * Wp * 8 + (5 + 2 * Wp) * nbm * 4 + 3 * n * 4 + (n + m / kExpandArcs + 1) * 8 +
-         pieces * 16 + row_cap * s * 4 + (row_cap + 2) * (int64_t)sizeof(RoundStats) +
+  // the frontier's out-arc pieces, twice for push rounds (rows of <= 8 words)
+  const int64_t e_bufs = W <= 8 ? 2 : 1;
+  return 4 * n * Wp * 8 + (5 + 2 * Wp) * nbm * 4 + 3 * n * 4 +
+         e_bufs * (n + m / kExpandArcs + 1) * 8 + pieces * 16 + row_cap * s * 4 + (row_cap + 2) * (int64_t)sizeof(RoundStats) +
          (int64_t)s * 8 + 4096;
 }
 

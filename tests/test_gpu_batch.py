@@ -158,3 +158,38 @@ def test_batch_forced_direction(direction):
             want = oracle.run(g, sd)
             got = b.result(len(items) + j)
             assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])
+
+
+@pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_SPARSE])
+def test_batch_push_rounds(direction):
+    """sparse_push = 2 in a packed batch: in each round the graphs below
+    their own dense threshold push (k_push, after the pull) while the others
+    are swept whole; counts and rounds equal the plain runs', the work is the
+    plain runs' work, and graphs of 8-word rows (s = 400, 512) push too."""
+    items = list(_mix()[:12])
+    extra = [(I.path(400, directed=True), np.array([0, 7, 399], np.int32)),
+             (I.grid(60, 60, 0.05, 73), I.seeds(3600, 512, 74)),
+             (I.rmat(11, 8, 75, directed=False), I.seeds(2048, 400, 76)),
+             (I.er(2500, 5, 77), I.seeds(2500, 500, 78))]
+    with pg.Batch() as b:
+        for it in items:
+            b.add_inputs(it.graph, it.seeds)
+        for g, sd in extra:
+            b.add_inputs(g, sd)
+        b.run(opts=pg.options(direction=direction, sparse_push=2))
+        work = b.stats()["seed_edge_traversals"]
+        plain_work = 0
+        for k, it in enumerate(items):
+            want, w = _plain(it)
+            plain_work += w
+            got = b.result(k)
+            assert got.rounds == want.rounds and np.array_equal(got.counts, want.counts)
+        for j, (g, sd) in enumerate(extra):
+            want = oracle.run(g, sd)
+            G = pg.Graph.from_inputs(g)
+            pg.propagate_p(G, sd)
+            plain_work += G.last_stats()["seed_edge_traversals"]
+            G.close()
+            got = b.result(len(items) + j)
+            assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])
+        assert work == plain_work

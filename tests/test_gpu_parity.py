@@ -569,6 +569,34 @@ def test_push_rounds_match_the_oracle(case):
                           _oracle_s_mactive(g, seeds, 64, want["rounds"])[:res_s.m_active.size])
 
 
+@pytest.mark.parametrize("s", [300, 512])
+def test_push_rounds_eight_words(s):
+    """sparse_push = 2 on rows of 8 words (s = 300 and 512): the push runs
+    in k_push, a kernel of its own launched after the pull; counts, m_active
+    and active rows equal the oracle's, with captured and plain launches and
+    with every round forced sparse."""
+    for g, sd in ((I.grid(70, 60, 0.05, 231), 232), (I.rmat(12, 8, 233, directed=False), 234)):
+        seeds = I.seeds(g.n, s, sd)
+        want = _oracle_p(g, seeds)
+        rows = int(_active_rows_from_distances(g, seeds).sum())
+        G = pg.Graph.from_inputs(g)
+        for direction in (pg.PG_DIR_AUTO, pg.PG_DIR_SPARSE):
+            for extra in (dict(), dict(use_graphs=0), dict(timing=1), dict(test_changed=1)):
+                res = pg.propagate_p(G, seeds, opts=pg.options(direction=direction,
+                                                               sparse_push=2, **extra))
+                _assert_same(res, want)
+                st = G.last_stats()
+                assert st["active_rows"] == rows
+                # zero, seed and post(0), then the pull, the push and the post
+                # kernel in rounds 1..T+1 (the host loop may run idle rounds)
+                full = 3 + 3 * (want["rounds"] + 1)
+                if extra.get("use_graphs", 1) and not extra.get("timing", 0):
+                    assert st["launches"] == full, (st["launches"], full)
+                else:
+                    assert st["launches"] >= full and (st["launches"] - 3) % 3 == 0
+        G.close()
+
+
 def test_push_rounds_reverse_and_relabelled():
     """Push rounds over the transpose (PG_REVERSE) of a relabelled digraph."""
     g = I.rmat(12, 8, 226, directed=True)
