@@ -182,16 +182,16 @@ typedef struct {
                                row that changed in the previous round ORs
                                its delta into its out-neighbours with
                                atomics (their claims for m_active made on
-                               the way), where it applies: rows of up to 8
-                               words (s <= 512) gathered whole, PROPAGATE-P
-                               or PROPAGATE-S one pass at a time, one graph
-                               or a packed batch (pg_batch_run: its graphs
-                               below their dense threshold push while the
-                               others are swept whole); 1 = pull, the post
-                               kernel claims the frontier's out-neighbours
-                               and the pull gathers their in-arcs (always
-                               for rows above 8 words and PROPAGATE-S
-                               passes run as words) */
+                               the way, per pass for PROPAGATE-S passes run
+                               as words), where it applies: rows of up to 8
+                               words (s <= 512, or up to 8 passes as words)
+                               gathered whole, one graph or a packed batch
+                               (pg_batch_run: its graphs below their dense
+                               threshold push while the others are swept
+                               whole); 1 = pull, the post kernel claims the
+                               frontier's out-neighbours and the pull
+                               gathers their in-arcs (always for rows above
+                               8 words) */
 } pg_options;
 
 #define PG_DIR_AUTO 0

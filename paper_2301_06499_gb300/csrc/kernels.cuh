@@ -776,7 +776,12 @@ __device__ __forceinline__ void pull_sparse(const Params &p, Ctrl *ctrl, const R
 // puts v in the frontier. Activity for m_active is the same claim as the
 // post kernel's for a pull round: the first pusher to reach an unsaturated v
 // claims it and counts its in-degree.
-template <int CW>
+//
+// PW (PROPAGATE-S passes as words): a row is active in pass k when a pusher's
+// delta has bits in word k and word k of the row's X is not full; the first
+// pusher to set the row's claim bit of pass k (Kw) counts it, as the pull's
+// count_pass_words does for a row cut into pieces.
+template <int CW, bool PW = false>
 __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const RoundBufs &rb, int t,
                                           int lane, int64_t warp, int64_t nwarps,
                                           uint32_t &my_mact, unsigned long long &my_work,
@@ -825,7 +830,25 @@ __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const Rou
       for (int q = 0; q < UNR; ++q) {
         app[q] = false;
         if (v[q] < 0) continue;
-        if (!test_bit_live(rb.Kcur, v[q]) && !set_bit(rb.Kcur, v[q])) {
+        if constexpr (PW) {
+          uint32_t indeg = 0;
+#pragma unroll
+          for (int k = 0; k < CW; ++k) {
+            if (!d[k]) continue;
+            uint32_t *Kw = rb.Kwcur + (size_t)k * (size_t)p.nbm;
+            if (test_bit_live(Kw, v[q]) || set_bit(Kw, v[q])) continue;
+            const uint64_t vm = valid_mask(k, p.s);
+            const uint64_t x =
+                __ldg(reinterpret_cast<const unsigned long long *>(p.X) + (size_t)v[q] * Wp + k);
+            if ((x | ~vm) != ~0ULL) {
+              if (!indeg)
+                indeg = (uint32_t)(__ldg(p.row_ptr + v[q] + 1) - __ldg(p.row_ptr + v[q]));
+              my_mact += indeg;
+              my_work += (unsigned long long)indeg * (unsigned long long)__popcll(vm);
+              ++my_rows;
+            }
+          }
+        } else if (!test_bit_live(rb.Kcur, v[q]) && !set_bit(rb.Kcur, v[q])) {
           const uint32_t indeg = (uint32_t)(__ldg(p.row_ptr + v[q] + 1) - __ldg(p.row_ptr + v[q]));
           my_mact += indeg;
           my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, v[q]);
@@ -915,9 +938,10 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
 }
 
 using PullFn = void (*)(Params);
-// Push rounds as a kernel of their own (k_push<CW>, push.cu): 8-word rows and
-// packed batches; it returns at once in rounds that are not pushed.
-PullFn push_fn(int CW);
+// Push rounds as a kernel of their own (k_push<CW, PW>, push.cu): 8-word
+// rows, PROPAGATE-S passes as words and packed batches; it returns at once in
+// rounds that are not pushed.
+PullFn push_fn(int CW, bool pw);
 // Dense rounds with TMA-gathered deltas (pull_tma.cu), for rows of CW = 4 or
 // 8 words: the kernel, its dynamic shared memory, its launch, and the tensor
 // map (a CUtensorMap, 128 bytes) over a delta buffer of `rows` rows.

@@ -996,12 +996,12 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     needs.push_back({&w.KW1, bm_bytes * (size_t)pl.Wp});
   }
   if (bs) needs.push_back({&w.seed_bits, sizeof(int32_t) * (size_t)sp});
-  // push rounds (rows of up to 8 words gathered whole, PROPAGATE-P or one
-  // pass at a time): the frontier's out-arc pieces by round parity. The
-  // default where they apply: measured faster on the 4096^2 grid by 19%, on
-  // R-MAT 22 with s = 256 by 13%, on ER 10^6 with s = 128 by 11%, on R-MAT
-  // 26 with s = 512 by 10% and on the 512-graph mix (batched) by 3%
-  const bool push_ok = !pl.wide && !pw && pl.CW == pl.Wp;
+  // push rounds (rows of up to 8 words gathered whole): the frontier's
+  // out-arc pieces by round parity. The default where they apply: measured
+  // faster on the 4096^2 grid by 19%, on R-MAT 22 with s = 256 by 13%, on ER
+  // 10^6 with s = 128 by 11%, on R-MAT 26 with s = 512 by 10% and on the
+  // 512-graph mix (batched) by 3%
+  const bool push_ok = !pl.wide && pl.CW == pl.Wp;
   const bool push = push_ok && cl.o.sparse_push != 1;
   if (push) needs.push_back({&w.E1, sizeof(unsigned long long) * (size_t)e_cap});
   if (bs && g->nseg > 0) {
@@ -1047,9 +1047,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.E = (unsigned long long *)w.E.p;
   p.E1 = push ? (unsigned long long *)w.E1.p : nullptr;
   p.push = push ? 1 : 0;
-  const bool push_kernel = push && (bs != nullptr || pl.CW == 8);
+  // k_pull pushes rows of up to 4 words of one graph, PROPAGATE-P or one
+  // pass at a time, itself; the rest push in k_push
+  const bool push_kernel = push && (bs != nullptr || pl.CW == 8 || pw);
   p.push_kernel = push_kernel ? 1 : 0;
-  pl.push = push_kernel ? push_fn(pl.CW) : nullptr;
+  pl.push = push_kernel ? push_fn(pl.CW, pw) : nullptr;
   p.A = (ulonglong2 *)w.A.p;
   p.Pall = (const ulonglong2 *)g->pieces.list.p;
   p.nPall = g->pieces.count;

@@ -1,6 +1,7 @@
-// Push rounds in a kernel of their own: rows of 8 words, and packed batches
-// (whose sparse graphs push while the graphs in a full sweep are swept by
-// k_pull in the same round). The round is pull_push in kernels.cuh: every row
+// Push rounds in a kernel of their own: rows of 8 words, PROPAGATE-S passes
+// run as words (m_active counted per pass), and packed batches (whose sparse
+// graphs push while the graphs in a full sweep are swept by k_pull in the
+// same round). The round is pull_push in kernels.cuh: every row
 // that changed in round t-1 ORs its delta into its unsaturated out-neighbours
 // with atomics, claiming them for m_active on the way. Launched after k_pull
 // in every round of a propagation that pushes; it returns at once in the
@@ -9,7 +10,7 @@
 
 namespace pg {
 
-template <int CW>
+template <int CW, bool PW>
 __global__ void __launch_bounds__(kBlock, 4) k_push(Params p) {
   Ctrl *ctrl = p.ctrl;
   if (*(volatile int32_t *)&ctrl->done) return;
@@ -27,17 +28,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_push(Params p) {
   const int lane = threadIdx.x & 31;
   uint32_t my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0, my_rows = 0;
   unsigned long long my_work = 0;
-  pull_push<CW>(p, ctrl, rb, t, lane, gtid >> 5, ((int64_t)gridDim.x * kBlock) >> 5, my_mact,
-                my_work, my_scan, my_gath, my_items, my_rows);
+  pull_push<CW, PW>(p, ctrl, rb, t, lane, gtid >> 5, ((int64_t)gridDim.x * kBlock) >> 5,
+                    my_mact, my_work, my_scan, my_gath, my_items, my_rows);
   pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 
-PullFn push_fn(int CW) {
+PullFn push_fn(int CW, bool pw) {
   switch (CW) {
-    case 1: return &k_push<1>;
-    case 2: return &k_push<2>;
-    case 4: return &k_push<4>;
-    case 8: return &k_push<8>;
+    case 1: return pw ? &k_push<1, true> : &k_push<1, false>;
+    case 2: return pw ? &k_push<2, true> : &k_push<2, false>;
+    case 4: return pw ? &k_push<4, true> : &k_push<4, false>;
+    case 8: return pw ? &k_push<8, true> : &k_push<8, false>;
   }
   return nullptr;
 }

@@ -101,8 +101,8 @@ pg_status tune_options(const TuneRun &run, int32_t s_bits, int32_t max_trials, p
     if ((rc = try_value(o))) return rc;
   }
   // sparse rounds pulled instead of pushed from the frontier (push rounds
-  // apply to rows of up to 8 words, not to PROPAGATE-S passes run as words)
-  if (W <= 8 && !(s_mode && W > 1)) {
+  // apply to rows of up to 8 words)
+  if (W <= 8) {
     pg_options o = cur;
     o.sparse_push = cur.sparse_push == 1 ? 0 : 1;
     if ((rc = try_value(o))) return rc;

@@ -230,15 +230,20 @@ def _pw_case(kind):
 @pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_DENSE, pg.PG_DIR_SPARSE])
 def test_s_pass_words_identical(kind, words, direction):
     """Passes side by side as signature words: counts and rounds as the
-    oracle's, m_active as the passes' own, summed (skip rule per pass)."""
+    oracle's, m_active as the passes' own, summed (skip rule per pass), with
+    sparse rounds pushed (k_push, claims per pass; rows gathered whole) and
+    pulled (the post kernel's claims)."""
     g, seeds, want, mact = _pw_case(kind)
     G = pg.Graph.from_inputs(g)
-    for lanes, wpt in ((0, 0), (1, 0), (1, 1), (4, 2)):  # lanes 1: many rows in pieces
+    # lanes 1: many rows in pieces; words_per_thread below the row: pulled
+    for lanes, wpt, push in ((0, 0, 0), (0, 0, 1), (1, 0, 0), (1, 0, 1), (1, 1, 0), (4, 2, 0)):
         res = pg.propagate_s(G, seeds, opts=pg.options(pass_words=words, direction=direction,
-                                                       group_lanes=lanes, words_per_thread=wpt))
-        assert res.rounds == want["rounds"], (lanes, wpt)
-        assert np.array_equal(res.counts, want["counts"]), (lanes, wpt)
-        assert np.array_equal(res.m_active, mact), (lanes, wpt)
+                                                       group_lanes=lanes, words_per_thread=wpt,
+                                                       sparse_push=push))
+        case = (lanes, wpt, push)
+        assert res.rounds == want["rounds"], case
+        assert np.array_equal(res.counts, want["counts"]), case
+        assert np.array_equal(res.m_active, mact), case
         assert G.last_stats()["passes"] == 5
 
 
