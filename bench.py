@@ -559,9 +559,11 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
     # per-kernel events (plain launches, library default schedule), per class
     batch.run(opts=pg.options(timing=1), stream=sptr)
     classes = []
+    members = [ng for ng, _ in batch.group_options()]
     for gi, st in enumerate(batch.group_stats()):
         s_cls = 64 * st["words_per_row"]
-        classes.append({"kernel": kernel_name(st), "s": s_cls, "ms_pull": st["ms_pull"],
+        classes.append({"kernel": kernel_name(st), "s": s_cls, "graphs": members[gi],
+                        "ms_pull": st["ms_pull"],
                         "pull_launches": st["pull_launches"], "ms_post": st["ms_post"],
                         "bytes": round_bytes(st, s_cls, False)})
     roofline = None
@@ -576,8 +578,9 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
                     "ms_per_launch": top["ms_pull"] / top["pull_launches"],
                     "launches": top["pull_launches"], "peak_source": peak_src,
                     "bytes_basis": "per round |A_t|(8+s/4) + m_active(t)(4+s/8) + |F_t|*4 "
-                                   "over the width class's packed union (s = the class's "
-                                   "seeds per graph), divided by its pull kernel's time",
+                                   "over the group (a width class's packed union, or one "
+                                   "large graph run alone; s = the class's seeds per graph), "
+                                   "divided by its pull kernel's time",
                     "note": "a run with per-launch events (plain launches, library default "
                             "schedule) after the timed steps"}
 
@@ -633,7 +636,7 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world} (independent mixes)"},
         "autotune": tuned,
-        "width_classes": classes,
+        "groups": classes,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / len(e2e_ms)},
@@ -677,7 +680,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": r["config"], "plain": r["plain"],
         "batched_over_plain": r["batched_over_plain"], "autotune": r["autotune"],
-        "width_classes": r["width_classes"], "roofline": r["roofline"], "e2e": r["e2e"],
+        "groups": r["groups"], "roofline": r["roofline"], "e2e": r["e2e"],
         "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "cpu_baseline": r["cpu_baseline"],
     }

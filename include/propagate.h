@@ -478,14 +478,19 @@ pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_t *col, int
  * and one post launch per round for all of its graphs. Each graph's counts
  * equal what pg_propagate_p gives for it alone (its bits never leave its own
  * nodes); only m_active is not kept per graph (pg_batch_result zero-fills
- * it). The paper runs one graph per call; batching is this library's
- * addition for workloads of many small graphs.
+ * it). A graph of at least 2^16 nodes whose four signature arrays (n x
+ * words x 8 bytes each) fill half of L2 or more runs alone instead, as
+ * pg_propagate_p would run it: it fills the GPU by itself, and alone it
+ * keeps part of its arrays in L2 from round to round. The paper runs one
+ * graph per call; batching is this library's addition for workloads of
+ * many small graphs.
  */
 typedef struct pg_batch pg_batch;
 
 typedef struct {
   int32_t graphs;                /* graphs in the batch */
-  int32_t groups;                /* width classes, one PROPAGATE-P each */
+  int32_t groups;                /* propagations: one per width class of
+                                    packed graphs, one per graph run alone */
   int32_t sweeps;                /* rounds of the longest class */
   int32_t launches;              /* kernels launched over all classes */
   uint64_t seed_edge_traversals; /* sum over graphs of their own
@@ -529,21 +534,23 @@ pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out);
 pg_status pg_batch_get_stats(pg_batch *b, pg_batch_stats *out);
 
 /*
- * Tunes each width class of the batch as pg_autotune does (each timed run
- * is a full run of that class; counts compared across candidates) and keeps
- * the chosen options per class; pg_batch_run with opt == NULL then uses
- * them. report (may be NULL) receives the sums over classes.
+ * Tunes each group of the batch as pg_autotune does (each timed run is a
+ * full run of that group; counts compared across candidates) and keeps the
+ * chosen options per group; pg_batch_run with opt == NULL then uses them.
+ * report (may be NULL) receives the sums over groups.
  */
 pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report, void *stream);
 
-/* pg_stats of width class `group` in the last pg_batch_run (kernel times
- * with opt->timing = 1). Errors: PG_EINVAL (no such class or no run). */
+/* pg_stats of group `group` in the last pg_batch_run (kernel times with
+ * opt->timing = 1). Groups are numbered by increasing width; within a width
+ * class the packed graphs come first, then the graphs run alone. Errors:
+ * PG_EINVAL (no such group or no run). */
 pg_status pg_batch_group_stats(pg_batch *b, int32_t group, pg_stats *out);
 
-/* Options a width class of the batch runs with (tuned, else the defaults);
- * classes are numbered by increasing width after the first run or tune;
- * *graphs (may be NULL) receives the class's graph count. Errors: PG_EINVAL
- * (no such class). */
+/* Options a group of the batch runs with (tuned, else the defaults); groups
+ * are numbered as for pg_batch_group_stats after the first run or tune;
+ * *graphs (may be NULL) receives the group's graph count. Errors: PG_EINVAL
+ * (no such group). */
 pg_status pg_batch_get_options(pg_batch *b, int32_t group, pg_options *out, int32_t *graphs);
 
 /*

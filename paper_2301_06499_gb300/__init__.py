@@ -333,7 +333,8 @@ class Batch:
         return {f: getattr(rep, f) for f, _ in _abi.TuneReport._fields_}
 
     def group_stats(self) -> list:
-        """pg_stats dict per width class of the last run, narrowest first."""
+        """pg_stats dict per group of the last run (one per width class of
+        packed graphs, one per graph run alone), narrowest first."""
         out, k = [], 0
         while True:
             st = _abi.Stats()
@@ -343,7 +344,7 @@ class Batch:
             k += 1
 
     def group_options(self) -> list:
-        """(graphs, options dict) per width class, narrowest first."""
+        """(graphs, options dict) per group, numbered as group_stats."""
         out, k = [], 0
         while True:
             o, ng = _abi.Options(), ctypes.c_int32(0)

@@ -84,6 +84,13 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+int64_t l2_bytes() {
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  return l2 > 0 ? l2 : (int64_t)128 << 20;
+}
+
 static int grid_for(int64_t work, int per_sm = 8) {
   int64_t cap = (int64_t)sm_count() * per_sm;
   int64_t need = (work + kBlock - 1) / kBlock;

@@ -112,6 +112,7 @@ pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, si
 int64_t workspace_held(const Workspace &w);
 pg_status cuda_status(cudaError_t e);
 int sm_count();
+int64_t l2_bytes();  // of the current device
 // Dense piece list of g for piece length L (cached in g).
 pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st);
 // Sliced-ELL copy of g's in-CSR for pieces of at most Lmax arcs (cached in g).

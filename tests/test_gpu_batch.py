@@ -193,3 +193,37 @@ def test_batch_push_rounds(direction):
             got = b.result(len(items) + j)
             assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])
         assert work == plain_work
+
+
+def test_batch_large_graph_runs_alone():
+    """A graph whose four signature arrays fill half of L2 (a 600^2 grid with
+    s = 300: 360,000 nodes x 8 words) runs alone, as a group of its own
+    through the single-graph path, beside the packed small graphs of the
+    batch: its counts equal the oracle's, every small graph's the plain
+    run's, and the batch's work is the plain runs' work."""
+    big = I.grid(600, 600, 0.05, 81)
+    sb = I.seeds(big.n, 300, 82)
+    items = list(_mix()[:8])
+    with pg.Batch() as b:
+        for it in items:
+            b.add_inputs(it.graph, it.seeds)
+        kb = b.add_inputs(big, sb)
+        b.run()
+        st = b.stats()
+        assert st["groups"] == len({_width_class(it.s) for it in items}) + 1
+        alone = [ng for ng, _ in b.group_options()]
+        assert alone.count(1) >= 1
+        hist, _ = oracle.seed_histograms(big, sb, cap=6000)
+        got = b.result(kb)
+        assert got.rounds == hist.shape[1] - 1
+        assert np.array_equal(got.counts, hist.T.astype(np.uint32))
+        work = 0
+        for k, it in enumerate(items):
+            want, w = _plain(it)
+            work += w
+            assert np.array_equal(b.result(k).counts, want.counts)
+        G = pg.Graph.from_inputs(big)
+        pg.propagate_p(G, sb)
+        work += G.last_stats()["seed_edge_traversals"]
+        G.close()
+        assert st["seed_edge_traversals"] == work
