@@ -556,8 +556,11 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
     plain_value = total_work / (p_total / 1e3)
 
     # the dominant pull kernel of the batched run: one more run with
-    # per-kernel events (plain launches, library default schedule), per class
+    # per-kernel events (plain launches, library default schedule), per
+    # group, the groups one after another so that each kernel time is its own
+    batch.set_streams(1)
     batch.run(opts=pg.options(timing=1), stream=sptr)
+    batch.set_streams(4)
     classes = []
     members = [ng for ng, _ in batch.group_options()]
     for gi, st in enumerate(batch.group_stats()):
@@ -582,7 +585,8 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
                                    "large graph run alone; s = the class's seeds per graph), "
                                    "divided by its pull kernel's time",
                     "note": "a run with per-launch events (plain launches, library default "
-                            "schedule) after the timed steps"}
+                            "schedule, groups one after another) after the timed steps, "
+                            "which run four groups at once"}
 
     # end to end with host buffers: pack, upload, run, read every result back
     h2d = sum(it.graph.row_ptr.nbytes + it.graph.col.nbytes + it.seeds.nbytes for it in items)

@@ -517,9 +517,15 @@ pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, 
 
 /*
  * Runs every graph of the batch to its last productive round and keeps each
- * graph's counts on the host. opt as for pg_propagate_p (planes_per_pass is
- * ignored); NULL = the options pg_batch_tune chose, else the defaults. Errors: PG_EINVAL (empty batch, malformed CSR), PG_ENOMEM,
- * PG_ECUDA; on error no result of this run is kept.
+ * graph's counts on the host. The groups (packed width classes and graphs
+ * run alone) run up to four at a time (pg_batch_set_streams), each on a
+ * stream the batch owns,
+ * driven by a host thread of its own; they start after the work already
+ * queued on `stream`, and the call returns when all of them are done. opt
+ * as for pg_propagate_p (planes_per_pass is ignored); NULL = the options
+ * pg_batch_tune chose, else the defaults. Errors: PG_EINVAL (empty batch,
+ * malformed CSR), PG_ENOMEM, PG_ECUDA; on error no result of this run is
+ * kept.
  */
 pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream);
 
@@ -540,6 +546,12 @@ pg_status pg_batch_get_stats(pg_batch *b, pg_batch_stats *out);
  * report (may be NULL) receives the sums over groups.
  */
 pg_status pg_batch_tune(pg_batch *b, int32_t max_trials, pg_tune_report *report, void *stream);
+
+/* Groups pg_batch_run runs at once (1..16, default 4), each on its own
+ * stream; 1 runs them one after another (kernel times of a group then
+ * measure that group alone). Errors: PG_EINVAL (b NULL, streams out of
+ * range). */
+pg_status pg_batch_set_streams(pg_batch *b, int32_t streams);
 
 /* pg_stats of group `group` in the last pg_batch_run (kernel times with
  * opt->timing = 1). Groups are numbered by increasing width; within a width

@@ -323,6 +323,10 @@ class Batch:
         return Result(rounds=T, counts=counts[:T + 1].copy(),
                       m_active=np.zeros(T + 2, dtype=np.uint64), s=s, n=n)
 
+    def set_streams(self, streams: int):
+        """pg_batch_set_streams: groups run at once (1 = one after another)."""
+        _abi.check(_abi.lib().pg_batch_set_streams(self._h, int(streams)), "pg_batch_set_streams")
+
     def tune(self, max_trials: int = 24, stream=None) -> dict:
         """pg_batch_tune: picks schedule options per width class; later
         run() calls without opts use them."""

@@ -157,6 +157,7 @@ SIGNATURES = {
     "pg_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(BatchStats)]),
     "pg_batch_tune": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(TuneReport), _vp]),
     "pg_batch_group_stats": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Stats)]),
+    "pg_batch_set_streams": (ctypes.c_int, [_vp, _i32]),
     "pg_batch_get_options": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(Options),
                                             ctypes.POINTER(_i32)]),
     "pg_server_default_config": (None, [ctypes.POINTER(ServerConfig)]),

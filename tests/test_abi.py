@@ -139,6 +139,13 @@ def test_argument_checks_before_any_device_work():
     assert L.pg_propagate_p(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
     assert L.pg_propagate_s(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
     assert L.pg_batch_create(None) == _abi.PG_EINVAL
+    bh = ctypes.c_void_p()
+    assert L.pg_batch_create(ctypes.byref(bh)) == _abi.PG_OK
+    for bad in (0, -1, 17):
+        assert L.pg_batch_set_streams(bh, bad) == _abi.PG_EINVAL
+    assert L.pg_batch_set_streams(bh, 1) == _abi.PG_OK
+    assert L.pg_batch_set_streams(None, 4) == _abi.PG_EINVAL
+    L.pg_batch_free(bh)
     assert L.pg_server_create(None, None) == _abi.PG_EINVAL
     assert L.pg_autotune(None, None, 1, 0, 1, None, None, None) == _abi.PG_EINVAL
     import torch

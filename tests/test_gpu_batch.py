@@ -227,3 +227,26 @@ def test_batch_large_graph_runs_alone():
         work += G.last_stats()["seed_edge_traversals"]
         G.close()
         assert st["seed_edge_traversals"] == work
+
+
+def test_batch_streams_give_the_same_counts():
+    """Groups run one after another, four at a time and sixteen at a time:
+    the same counts and work (each group's propagation is independent)."""
+    items = list(_mix()[:20])
+    extra = (I.grid(520, 520, 0.05, 91), I.seeds(270_400, 500, 92))  # runs alone
+    runs = []
+    with pg.Batch() as b:
+        for it in items:
+            b.add_inputs(it.graph, it.seeds)
+        b.add_inputs(*extra)
+        for k in (1, 4, 16):
+            b.set_streams(k)
+            b.run()
+            runs.append(([b.result(i).counts for i in range(len(items) + 1)],
+                         b.stats()["seed_edge_traversals"]))
+    for counts, work in runs[1:]:
+        assert work == runs[0][1]
+        for a, c in zip(runs[0][0], counts):
+            assert np.array_equal(a, c)
+    want, _ = _plain(items[0])
+    assert np.array_equal(runs[0][0][0], want.counts)
