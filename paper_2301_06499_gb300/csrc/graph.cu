@@ -2,6 +2,7 @@
 // and the dense work list (every row cut into pieces of at most L arcs).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include <vector>
 
@@ -13,6 +14,13 @@ pg_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return PG_OK;
   if (e == cudaErrorMemoryAllocation) return PG_ENOMEM;
   return PG_ECUDA;
+}
+
+// Sum over the warp (every lane gets it).
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFullMask, x, off);
+  return x;
 }
 
 pg_status ensure(DevBuf &b, size_t bytes) {
@@ -173,44 +181,58 @@ pg_status exclusive_scan_i64(int64_t *data, int64_t n, cudaStream_t st) {
 
 // ------------------------------------------------------------ validation
 // err bits: 1 row_ptr[0] != 0, 2 non-monotone / past m, 4 col out of range,
-// 8 row not strictly increasing, 16 row_ptr[n] != m.
-// CSR validation in two flat passes (all coalesced): rows, one thread each,
-// check their bounds and mark their first arc in a bitmap of m bits; arcs,
-// one thread each, check their column and, unless a row starts there, that
-// they follow the previous arc in increasing order.
-__global__ void k_validate_rows(const int64_t *rp, int64_t n, int64_t m, uint32_t *starts,
-                                int *err) {
+// 8 row not strictly increasing (set on the host), 16 row_ptr[n] != m.
+// CSR validation in two flat passes (coalesced) and a count: the arcs pass
+// counts descents (positions j > 0 with col[j-1] >= col[j]) into cnt[0]; the
+// rows pass checks each row's bounds and counts the nonempty rows whose
+// first arc is a descent into cnt[1]. The nonempty rows of a valid row_ptr
+// start at distinct positions, so the two counts are equal exactly when
+// every descent is the first arc of a row, i.e. when every row's columns
+// strictly increase.
+__global__ void k_validate_rows(const int64_t *rp, const int32_t *col, int64_t n, int64_t m,
+                                unsigned long long *cnt, int *err) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   if (gtid == 0) {
     if (rp[0] != 0) atomicOr(err, 1);
     if (rp[n] != m) atomicOr(err, 16);
   }
+  unsigned long long starts = 0;
   for (int64_t v = gtid; v < n; v += nth) {
     const int64_t b = rp[v], e = rp[v + 1];
     if (b > e || b < 0 || e > m)
       atomicOr(err, 2);
-    else if (b < e)
-      atomicOr(starts + (b >> 5), 1u << (b & 31));
+    else if (b < e && b > 0 && col[b - 1] >= col[b])
+      ++starts;
   }
+  const unsigned long long tot = warp_sum64(starts);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&cnt[1], tot);
 }
 
-__global__ void k_validate_arcs(const int32_t *col, int64_t n, int64_t m, const uint32_t *starts,
+__global__ void k_validate_arcs(const int32_t *col, int64_t n, int64_t m, unsigned long long *cnt,
                                 int *err) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  // whole warps iterate, so that the warp-wide OR sees every lane
-  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < m;
-       base += nth) {
-    const int64_t j = base + (threadIdx.x & 31);
-    int bad = 0;
-    if (j < m) {
-      const int32_t c = col[j];
-      if (c < 0 || c >= n) bad |= 4;
-      if (j > 0 && !((starts[j >> 5] >> (j & 31)) & 1u) && col[j - 1] >= c) bad |= 8;
-    }
-    bad = __reduce_or_sync(kFullMask, (unsigned)bad);
-    if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
+  const int64_t nq = m / 4;  // whole quads, read as int4 (the array is 256-byte aligned)
+  const int4 *q4 = reinterpret_cast<const int4 *>(col);
+  unsigned long long desc = 0;
+  bool out = false;
+  for (int64_t q = gtid; q < nq; q += nth) {
+    const int4 c = q4[q];
+    const int32_t prev = q > 0 ? col[4 * q - 1] : INT32_MIN;
+    out |= c.x < 0 || c.x >= n || c.y < 0 || c.y >= n || c.z < 0 || c.z >= n || c.w < 0 ||
+           c.w >= n;
+    desc += (q > 0 && prev >= c.x) + (c.x >= c.y) + (c.y >= c.z) + (c.z >= c.w);
   }
+  if (gtid == 0)  // the last m % 4 arcs
+    for (int64_t j = nq * 4; j < m; ++j) {
+      const int32_t c = col[j];
+      out |= c < 0 || c >= n;
+      desc += j > 0 && col[j - 1] >= c;
+    }
+  if (out) atomicOr(err, 4);
+  const unsigned long long tot = warp_sum64(desc);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&cnt[0], tot);
 }
 
 // --------------------------------------------------------------- transpose
@@ -321,17 +343,6 @@ pg_status ensure_pieces(pg_graph *g, int32_t L, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ sliced ELL
-// Piece lengths histogram (bucket Lmax - len, so that a forward scan lists
-// the longest pieces first).
-__global__ void k_sell_hist(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
-                            unsigned long long *hist) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int len = (int)(pieces[i].y & 0x7FFFFFFFULL);
-    atomicAdd(&hist[Lmax - len], 1ULL);
-  }
-}
-
 // Packed batch: bucket (graph, Lmax - len), so that each graph's pieces are
 // contiguous (longest first) and can be padded to whole chunks.
 __global__ void k_sell_hist_seg(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
@@ -357,13 +368,59 @@ __global__ void k_sell_scatter_seg(const ulonglong2 *pieces, int64_t np, int32_t
   }
 }
 
-__global__ void k_sell_scatter(const ulonglong2 *pieces, int64_t np, int32_t Lmax,
-                               unsigned long long *cursor, ulonglong2 *sorted) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const ulonglong2 it = pieces[i];
-    const int len = (int)(it.y & 0x7FFFFFFFULL);
-    sorted[atomicAdd(&cursor[Lmax - len], 1ULL)] = it;
+// One graph: a counting sort of the pieces by length, longest first, with
+// block-local counters. Block b takes a contiguous range of the (row-ordered)
+// piece list; k_sell_bhist counts its pieces per length into bh[len' * B + b]
+// (len' = Lmax - len), whose exclusive scan is where block b's pieces of each
+// length start; k_sell_bscatter places them there, the lanes of a warp with
+// equal lengths taking consecutive slots with one shared-memory atomic. (One
+// global atomic per piece on a handful of bucket counters serialised at the
+// L2: 62 ms for the ~10^8 pieces of a scale-26 R-MAT.)
+__global__ void __launch_bounds__(kBlock) k_sell_bhist(const ulonglong2 *pieces, int64_t np,
+                                                       int32_t Lmax, int64_t per_block,
+                                                       int64_t *bh) {
+  __shared__ uint32_t h[kSellPiece + 1];
+  for (int k = threadIdx.x; k <= Lmax; k += kBlock) h[k] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t lo = (int64_t)blockIdx.x * per_block, hi = min(np, lo + per_block);
+  for (int64_t base = lo; base < hi; base += kBlock) {  // block-uniform trip count
+    const int64_t i = base + threadIdx.x;
+    const int key = i < hi ? Lmax - (int)(pieces[i].y & 0x7FFFFFFFULL) : -1;
+    const unsigned peers = __match_any_sync(kFullMask, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k <= Lmax; k += kBlock) bh[(int64_t)k * gridDim.x + blockIdx.x] = h[k];
+}
+
+__global__ void __launch_bounds__(kBlock) k_sell_bscatter(const ulonglong2 *pieces, int64_t np,
+                                                          int32_t Lmax, int64_t per_block,
+                                                          const int64_t *bh,
+                                                          ulonglong2 *sorted) {
+  __shared__ int64_t start[kSellPiece + 1];
+  __shared__ uint32_t used[kSellPiece + 1];
+  for (int k = threadIdx.x; k <= Lmax; k += kBlock) {
+    start[k] = bh[(int64_t)k * gridDim.x + blockIdx.x];
+    used[k] = 0u;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t lo = (int64_t)blockIdx.x * per_block, hi = min(np, lo + per_block);
+  for (int64_t base = lo; base < hi; base += kBlock) {
+    const int64_t i = base + threadIdx.x;
+    ulonglong2 it = make_ulonglong2(0ULL, 0ULL);
+    int key = -1;
+    if (i < hi) {
+      it = pieces[i];
+      key = Lmax - (int)(it.y & 0x7FFFFFFFULL);
+    }
+    const unsigned peers = __match_any_sync(kFullMask, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t at = 0;
+    if (key >= 0 && lane == leader) at = atomicAdd(&used[key], (uint32_t)__popc(peers));
+    at = __shfl_sync(kFullMask, at, leader);
+    if (key >= 0) sorted[start[key] + at + __popc(peers & ((1u << lane) - 1u))] = it;
   }
 }
 
@@ -397,6 +454,7 @@ __global__ void k_sell_fill(const ulonglong2 *sorted, int64_t nchunks, const int
 pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
   SellList &sl = g->sell;
   if (sl.Lmax == Lmax && sl.items.p) return PG_OK;
+  if (Lmax < 1 || Lmax > kSellPiece) return PG_EINVAL;  // the sort's shared counters
   // pieces of at most Lmax arcs, in row order (the cached piece list is reused
   // as scratch and rebuilt on its next use)
   PieceList saved;
@@ -475,20 +533,27 @@ pg_status ensure_sell(pg_graph *g, int32_t Lmax, cudaStream_t st) {
   } else {
     release(sl.seg);
     release(sl.chunk0);
-    rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(unsigned long long) * (Lmax + 2), st));
+    // blocks of the counting sort: contiguous ranges of >= 4096 pieces
+    const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 8,
+                                                                (np + 4095) / 4096));
+    const int64_t per_block = (np + nblk - 1) / nblk;
+    const int64_t nbh = (int64_t)(Lmax + 1) * nblk + 1;
+    rc = cuda_status(cudaMallocAsync((void **)&hist, sizeof(int64_t) * nbh, st));
     if (rc == PG_OK) rc = ensure(sl.items, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1));
     if (rc == PG_OK) rc = ensure(sl.off, sizeof(int64_t) * (size_t)(nchunks + 1));
     if (rc == PG_OK) rc = ensure(sl.len, sizeof(int32_t) * (size_t)std::max<int64_t>(nchunks, 1));
     if (rc == PG_OK) {
-      cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (Lmax + 2), st);
+      cudaMemsetAsync(hist, 0, sizeof(int64_t) * nbh, st);
       // padding slots: zero-length items of row 0 (never active)
       cudaMemsetAsync(sl.items.p, 0, sizeof(ulonglong2) * (size_t)std::max<int64_t>(nchunks * 32, 1), st);
-      k_sell_hist<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist);
-      rc = exclusive_scan_i64((int64_t *)hist, Lmax + 2, st);
+      k_sell_bhist<<<(unsigned)nblk, kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax,
+                                                      per_block, (int64_t *)hist);
+      rc = exclusive_scan_i64((int64_t *)hist, nbh, st);
     }
     if (rc == PG_OK) {
-      k_sell_scatter<<<grid_for(np), kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax, hist,
-                                                      (ulonglong2 *)sl.items.p);
+      k_sell_bscatter<<<(unsigned)nblk, kBlock, 0, st>>>((const ulonglong2 *)tmp.list.p, np, Lmax,
+                                                         per_block, (const int64_t *)hist,
+                                                         (ulonglong2 *)sl.items.p);
       k_sell_chunks<<<grid_for(nchunks), kBlock, 0, st>>>((const ulonglong2 *)sl.items.p, np,
                                                           nchunks, (int32_t *)sl.len.p,
                                                           (int64_t *)sl.off.p);
@@ -541,6 +606,29 @@ pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, si
     if (!nd.first->p || nd.first->bytes < std::max<size_t>(nd.second, 16)) fits = false;
   if (fits) return PG_OK;
   std::vector<DevBuf *> parts = workspace_parts(w);
+  if (w.arena.p) {
+    // only parts the layout does not have yet: placed after it, in the
+    // arena's slack, when they fit (the other parts keep their place)
+    size_t off = w.used;
+    bool extra_ok = true;
+    std::vector<std::pair<DevBuf *, size_t>> add;
+    for (const auto &nd : needs) {
+      const size_t want = std::max<size_t>(nd.second, 16);
+      if (nd.first->p && nd.first->bytes >= want) continue;
+      if (nd.first->p) extra_ok = false;  // a part that has to grow
+      add.push_back({nd.first, want});
+      off += (want + kAlign - 1) / kAlign * kAlign;
+    }
+    if (extra_ok && off <= w.arena.bytes) {
+      char *base = (char *)w.arena.p;
+      for (auto &a : add) {
+        a.first->p = base + w.used;
+        a.first->bytes = a.second;
+        w.used += (a.second + kAlign - 1) / kAlign * kAlign;
+      }
+      return PG_OK;
+    }
+  }
   std::vector<size_t> cap(parts.size());
   for (size_t i = 0; i < parts.size(); ++i) cap[i] = parts[i]->p ? parts[i]->bytes : 0;
   for (const auto &nd : needs) {
@@ -556,7 +644,10 @@ pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, si
     b->p = nullptr;
     b->bytes = 0;
   }
-  pg_status rc = ensure(w.arena, total);
+  w.used = 0;
+  // 1/32 of slack, so that parts a later call adds (PROPAGATE-S's per-pass
+  // claim bits after a PROPAGATE-P call) need no new arena
+  pg_status rc = ensure(w.arena, total + total / 32);
   if (rc) return rc;
   char *base = (char *)w.arena.p;
   size_t off = 0;
@@ -566,11 +657,13 @@ pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, si
     parts[i]->bytes = cap[i];
     off += (cap[i] + kAlign - 1) / kAlign * kAlign;
   }
+  w.used = off;
   return PG_OK;
 }
 
 void release_workspace(Workspace &w) {
   release(w.arena);
+  w.used = 0;
   for (DevBuf *b : workspace_parts(w)) {  // they pointed into the arena
     b->p = nullptr;
     b->bytes = 0;
@@ -699,28 +792,60 @@ __global__ void k_relabel_degrees(const int64_t *rp, const int32_t *old_of, int6
   if (blockIdx.x == 0 && threadIdx.x == 0) nrp[n] = 0;
 }
 
-// A warp per new row (new ids in order, so the longest rows start first):
-// its arcs in the original order, each source renamed.
+// New rows four at a time per warp (new ids in order, so the longest rows
+// come first): four rows of at most 64 arcs take 8 lanes each, otherwise the
+// whole warp takes the four rows one after another. Each row's arcs keep
+// their original order, each source renamed. (A warp per row left most lanes
+// idle on the short rows that make up most of a power-law graph.)
 __global__ void __launch_bounds__(kBlock) k_relabel_arcs(const int64_t *rp, const int32_t *col,
                                                          const int32_t *new_of,
                                                          const int32_t *old_of, int64_t n,
                                                          const int64_t *nrp, int32_t *ncol) {
   const int lane = threadIdx.x & 31;
+  const int q = lane >> 3, l = lane & 7;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
-    const int32_t v = old_of[r];
-    const int64_t b = rp[v], d = rp[v + 1] - b, o = nrp[r];
-    int64_t k = lane;
-    for (; k + 96 < d; k += 128) {  // four independent renames in flight
-      const int32_t a0 = col[b + k], a1 = col[b + k + 32], a2 = col[b + k + 64],
-                    a3 = col[b + k + 96];
-      const int32_t c0 = new_of[a0], c1 = new_of[a1], c2 = new_of[a2], c3 = new_of[a3];
-      ncol[o + k] = c0;
-      ncol[o + k + 32] = c1;
-      ncol[o + k + 64] = c2;
-      ncol[o + k + 96] = c3;
+  for (int64_t r0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 4; r0 < n;
+       r0 += nw * 4) {
+    const int64_t r = r0 + q;
+    int64_t o = 0, d = 0;
+    if (r < n) {
+      o = nrp[r];
+      d = nrp[r + 1] - o;
     }
-    for (; k < d; k += 32) ncol[o + k] = new_of[col[b + k]];
+    if (__all_sync(kFullMask, d <= 64)) {
+      if (d > 0) {
+        const int64_t b = rp[old_of[r]];
+        int64_t k = l;
+        for (; k + 24 < d; k += 32) {  // four independent renames in flight
+          const int32_t a0 = col[b + k], a1 = col[b + k + 8], a2 = col[b + k + 16],
+                        a3 = col[b + k + 24];
+          const int32_t c0 = new_of[a0], c1 = new_of[a1], c2 = new_of[a2], c3 = new_of[a3];
+          ncol[o + k] = c0;
+          ncol[o + k + 8] = c1;
+          ncol[o + k + 16] = c2;
+          ncol[o + k + 24] = c3;
+        }
+        for (; k < d; k += 8) ncol[o + k] = new_of[col[b + k]];
+      }
+      continue;
+    }
+    for (int qq = 0; qq < 4; ++qq) {
+      const int64_t oo = __shfl_sync(kFullMask, o, qq * 8);
+      const int64_t dd = __shfl_sync(kFullMask, d, qq * 8);
+      if (dd == 0) continue;  // warp-uniform (also rows past n)
+      const int64_t b = rp[old_of[r0 + qq]];
+      int64_t k = lane;
+      for (; k + 96 < dd; k += 128) {  // four independent renames in flight
+        const int32_t a0 = col[b + k], a1 = col[b + k + 32], a2 = col[b + k + 64],
+                      a3 = col[b + k + 96];
+        const int32_t c0 = new_of[a0], c1 = new_of[a1], c2 = new_of[a2], c3 = new_of[a3];
+        ncol[oo + k] = c0;
+        ncol[oo + k + 32] = c1;
+        ncol[oo + k + 64] = c2;
+        ncol[oo + k + 96] = c3;
+      }
+      for (; k < dd; k += 32) ncol[oo + k] = new_of[col[b + k]];
+    }
   }
 }
 
@@ -751,8 +876,8 @@ static pg_status relabel_by_degree(pg_graph *g, cudaStream_t st) {
   }
   if (!rc) rc = exclusive_scan_i64(nrp, n + 1, st);
   if (!rc && m > 0) {
-    k_relabel_arcs<<<grid_for(n * 32), kBlock, 0, st>>>(g->row_ptr, g->col, (const int32_t *)g->perm.p,
-                                                        old_of, n, nrp, ncol);
+    k_relabel_arcs<<<grid_for(n * 8), kBlock, 0, st>>>(g->row_ptr, g->col, (const int32_t *)g->perm.p,
+                                                       old_of, n, nrp, ncol);
     rc = cuda_status(cudaGetLastError());
   }
   if (H) cudaFreeAsync(H, st);
@@ -965,34 +1090,24 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
     if (rc == PG_OK && m > 0)
       rc = cuda_status(cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, kind, st));
   }
-  int *err = nullptr;
-  unsigned long long *mx = nullptr;
-  if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&err, sizeof(int) + 16, st));
-  if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&mx, sizeof(unsigned long long), st));
+  // one small block: [0] error bits, [1] max degree, [2..3] the two counts
+  unsigned long long *vb = nullptr;
+  if (rc == PG_OK) rc = cuda_status(cudaMallocAsync((void **)&vb, 4 * sizeof(unsigned long long), st));
   if (rc == PG_OK) {
-    cudaMemsetAsync(err, 0, sizeof(int), st);
-    cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
-    uint32_t *starts = nullptr;
-    const int64_t swords = (m + 31) / 32 + 1;
-    rc = cuda_status(cudaMallocAsync((void **)&starts, sizeof(uint32_t) * swords, st));
-    if (rc == PG_OK) {
-      cudaMemsetAsync(starts, 0, sizeof(uint32_t) * swords, st);
-      k_validate_rows<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, m, starts, err);
-      k_validate_arcs<<<grid_for(m), kBlock, 0, st>>>(g->col, n, m, starts, err);
-      cudaFreeAsync(starts, st);
-    }
-    if (rc == PG_OK) {
-      k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, mx);
-      rc = cuda_status(cudaGetLastError());
-    }
+    cudaMemsetAsync(vb, 0, 4 * sizeof(unsigned long long), st);
+    int *err = reinterpret_cast<int *>(vb);
+    k_validate_rows<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, g->col, n, m, vb + 2, err);
+    k_validate_arcs<<<grid_for((m + 3) / 4), kBlock, 0, st>>>(g->col, n, m, vb + 2, err);
+    k_max_degree<<<grid_for(n), kBlock, 0, st>>>(g->row_ptr, n, vb + 1);
+    rc = cuda_status(cudaGetLastError());
   }
-  int err_h = 0;
-  unsigned long long mx_h = 0;
-  if (rc == PG_OK) rc = cuda_status(cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (rc == PG_OK) rc = cuda_status(cudaMemcpyAsync(&mx_h, mx, sizeof(mx_h), cudaMemcpyDeviceToHost, st));
+  unsigned long long vb_h[4] = {0, 0, 0, 0};
+  if (rc == PG_OK) rc = cuda_status(cudaMemcpyAsync(vb_h, vb, sizeof(vb_h), cudaMemcpyDeviceToHost, st));
   if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
-  if (err) cudaFreeAsync(err, st);
-  if (mx) cudaFreeAsync(mx, st);
+  if (vb) cudaFreeAsync(vb, st);
+  int err_h = (int)(vb_h[0] & 0xFFFFFFFFULL);
+  if (!(err_h & 2) && vb_h[2] != vb_h[3]) err_h |= 8;  // a descent inside a row
+  const unsigned long long mx_h = vb_h[1];
   if (rc == PG_OK && err_h) rc = PG_EINVAL;
   g->max_degree = (int64_t)mx_h;
   g->mean_degree = (double)m / (double)n;

@@ -22,6 +22,7 @@ struct DevBuf {
 // by carve_workspace; each buffer's p points into the arena.
 struct Workspace {
   DevBuf arena;
+  size_t used = 0;  // end of the laid-out parts in the arena
   DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, KW0, KW1, F0, F1, E, A, counts, rs, ctrl, seeds,
       seed_bits, gfsum, gthr, dlist, dpref, E1;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
@@ -104,9 +105,10 @@ void release(DevBuf &b);
 // Frees every buffer, event and pinned block of a workspace.
 void release_workspace(Workspace &w);
 // Gives each listed buffer of w at least the listed bytes: one device
-// allocation per workspace, carved 256-byte aligned. Capacities only grow;
-// when one must, the whole workspace is laid out again (contents are not
-// kept), else every buffer keeps its address.
+// allocation per workspace (with 1/32 of slack), carved 256-byte aligned.
+// Buffers the layout lacks go into the slack when they fit; when a buffer
+// must grow, or the slack is too small, the whole workspace is laid out
+// again (contents are not kept); otherwise every buffer keeps its address.
 pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, size_t>> &needs);
 // Device bytes a workspace holds.
 int64_t workspace_held(const Workspace &w);

@@ -256,6 +256,42 @@ def test_invalid_csr_rejected(what):
     assert e.value.status == _abi.PG_EINVAL
 
 
+def _big_valid_csr(seed):
+    """A larger CSR (rows of 0-40 arcs, many empty) whose columns strictly
+    increase within each row and descend at most row starts."""
+    rng = np.random.default_rng(seed)
+    n = 5000
+    deg = rng.integers(0, 41, n)
+    deg[rng.random(n) < 0.2] = 0
+    rows = [np.sort(rng.choice(n, int(d), replace=False)).astype(np.int32) for d in deg]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum(deg)
+    return rp, np.concatenate(rows), n
+
+
+@pytest.mark.parametrize("pos", [0, 1, 2, 3, 4, 5, 6, 7])
+def test_invalid_csr_descent_anywhere_in_a_row(pos):
+    """The column check counts descents (col[j-1] >= col[j]) against the rows
+    starting on one: a single swap inside any row, at any offset of the
+    4-arc groups the check reads, is rejected; the unswapped CSR (descents
+    only at row starts, empty rows between) is accepted."""
+    rp, col, n = _big_valid_csr(61)
+    G = pg.Graph.from_csr(rp, col, n)  # valid
+    G.close()
+    rows = [v for v in range(n) if rp[v + 1] - rp[v] >= 2]
+    # a row whose second arc sits at the requested offset within a quad
+    v = next(v for v in rows if (rp[v] + 1) % 8 == pos)
+    bad = col.copy()
+    bad[rp[v]], bad[rp[v] + 1] = bad[rp[v] + 1], bad[rp[v]]
+    with pytest.raises(pg.PropagateError) as e:
+        pg.Graph.from_csr(rp, bad, n)
+    assert e.value.status == _abi.PG_EINVAL
+    dup = col.copy()
+    dup[rp[v] + 1] = dup[rp[v]]  # a repeated arc
+    with pytest.raises(pg.PropagateError):
+        pg.Graph.from_csr(rp, dup, n)
+
+
 def test_device_pointer_graph_equals_host_graph():
     torch = pytest.importorskip("torch")
     g = I.rmat(12, 8, 21, directed=True)
