@@ -920,7 +920,7 @@ def kernel_hash(kernel: str) -> str:
     else:
         m = re.match(r"k_pull<(\d+)", kernel)
         own = f"pull_cw{m.group(1)}.cu" if m else ""
-    for name in ("common.cuh", "kernels.cuh", own):
+    for name in ("common.cuh", "kernels.cuh", "push.cu", own):
         path = os.path.join(csrc, name)
         if name and os.path.exists(path):
             h.update(open(path, "rb").read())
@@ -1081,24 +1081,34 @@ def write_traffic(workload: str, csvs: list, out_path: str | None = None) -> dic
     (dram__bytes_read.sum and dram__bytes_write.sum): mean bytes per launch
     of each kernel, with the hash of the sources it was built from."""
     import ncu_summary
-    per = {}
+    per, push = {}, {}
     for path in csvs:
-        per.update(ncu_summary.traffic(path))
+        tot = ncu_summary.traffic_totals(path)
+        pushed = sum(b for k, (b, _) in tot.items() if k.startswith("k_push"))
+        for k, (b, nl) in tot.items():
+            if k.startswith("k_push"):
+                push[k] = b / nl
+            elif k.startswith("k_pull"):
+                # a round's pull time includes its push kernel: so do its bytes
+                per[k] = (b + pushed) / nl
     out = {"workload": workload,
            "kernel_hash": {k: kernel_hash(k) for k in per},
            "bytes_per_launch": per,
+           "push_bytes_per_launch": push,
            "commands": [
                f"python bench.py --profile-run p --workload {workload}",
                "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-               "--nvtx --nvtx-include bench_call/ --clock-control none -k regex:k_pull --csv "
+               "--nvtx --nvtx-include bench_call/ --clock-control none -k regex:'k_pu(ll|sh)' --csv "
                f"--log-file traffic_p.csv python bench.py --profile-run p --workload {workload}",
                "(the same two lines with --profile-run s -> traffic_s.csv)",
                "python bench.py --workload " + workload +
                " --write-traffic traffic_p.csv traffic_s.csv"],
-           "note": "mean dram__bytes_read.sum + dram__bytes_write.sum per launch over the pull "
-                   "launches of the call the bench times (NVTX range bench_call), with the "
-                   "autotuned schedule; a kernel's figure applies while the hash of its "
-                   "sources (common.cuh, kernels.cuh and its pull_*.cu) is unchanged"}
+           "note": "dram__bytes_read.sum + dram__bytes_write.sum of the pull launches, and of "
+                   "the push launches that follow them in push rounds, over the call the bench "
+                   "times (NVTX range bench_call, autotuned schedule), per pull launch (the "
+                   "library's pull time of a round spans both kernels); a kernel's figure "
+                   "applies while the hash of its sources (common.cuh, kernels.cuh, push.cu "
+                   "and its pull_*.cu) is unchanged"}
     with open(out_path or os.path.join(ROOT, "profiles", "pull_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(per))

@@ -53,6 +53,18 @@ def launches(path):
             for k, v in sorted(tot.items(), key=lambda kv: -kv[1][1])}
 
 
+def traffic_totals(path):
+    """{kernel: (total DRAM bytes read + written, launches)} of one capture."""
+    per = collections.defaultdict(lambda: collections.defaultdict(float))
+    for r in _rows(path):
+        m = r.get("Metric Name")
+        if m not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        b = float(r["Metric Value"].replace(",", "")) * _UNIT_B.get(r["Metric Unit"], 1.0)
+        per[short_name(r["Kernel Name"])][int(r["ID"])] += b
+    return {k: (sum(v.values()), len(v)) for k, v in per.items()}
+
+
 def traffic(path, skip: int = 0):
     per = collections.defaultdict(lambda: collections.defaultdict(float))
     for r in _rows(path):
