@@ -458,8 +458,10 @@ pg_status pg_autotune(pg_graph *g, const int32_t *seeds, int32_t s, int32_t algo
  * 0..max_rounds written, *rounds = max_rounds + 1), PG_ECUDA (a launch or
  * copy failed). The call waits on the stream after validation and after every
  * round (it reads the round's changed flag back to the host).
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. All calls share
+ * Because it waits on the stream every round, the call cannot be captured
+ * into a CUDA graph: do not make it while its stream (or, for the legacy
+ * stream, any stream) is capturing. The first call on a device also looks
+ * up the array's device address (once per device). All calls share
  * the array and each clears what it uses; calls whose GPU work overlaps (on
  * different streams) race on it, so order them on one stream.
  */
