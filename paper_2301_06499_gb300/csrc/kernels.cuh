@@ -291,95 +291,6 @@ __device__ __forceinline__ void frontier_append(const Params &p, Ctrl *ctrl, int
   warp_append_pieces(E_of(p, ctrl->t), &ctrl->nE, v, ne, lane);
 }
 
-// frontier_append for up to N rows per lane (app[q] marks row v[q]): one
-// reservation in F_t (with the rows' out-degree sum) and one in E_t per warp.
-template <int N>
-__device__ __forceinline__ void frontier_append_n(const Params &p, Ctrl *ctrl, int32_t *F,
-                                                  const int32_t (&v)[N], const bool (&app)[N],
-                                                  int lane) {
-  uint32_t cnt = 0;
-  unsigned long long odsum = 0, nesum = 0;
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-    if (app[q]) {
-      const unsigned long long od =
-          (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
-      ++cnt;
-      odsum += od;
-      nesum += (od + p.LE - 1) / p.LE;
-    }
-  if (!__any_sync(kFullMask, cnt != 0)) return;
-  if (p.gfsum) {  // a packed batch: each graph's own frontier out-arcs
-    // (a lane's rows are the out-neighbours of one row, so of one graph: one
-    // atomic per warp when the warp's rows are all of one graph)
-    unsigned long long *gf = p.gfsum + (size_t)(ctrl->t & 1) * (size_t)p.nseg;
-    int gid = -1;
-    unsigned long long gs = 0;
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-      if (app[q]) {
-        const unsigned long long od =
-            (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
-        const int gq = __ldg(p.node_graph + v[q]);
-        if (gid < 0) gid = gq;
-        if (gq == gid)
-          gs += od;
-        else if (od)
-          atomicAdd(gf + gq, od);
-      }
-    const unsigned has = __ballot_sync(kFullMask, gid >= 0);
-    const int g0 = __shfl_sync(kFullMask, gid, __ffs(has) - 1);
-    if (__all_sync(kFullMask, gid < 0 || gid == g0)) {
-      unsigned long long gtot;
-      warp_excl_scan64(gs, lane, &gtot);
-      if (lane == 0 && gtot) atomicAdd(gf + g0, gtot);
-    } else if (gs) {
-      atomicAdd(gf + gid, gs);
-    }
-  }
-  unsigned long long tot;
-  const unsigned long long ex =
-      warp_excl_scan64(((unsigned long long)cnt << kFsumBits) + odsum, lane, &tot);
-  unsigned long long basep = 0;
-  if (lane == 0) basep = atomicAdd(&ctrl->fpack, tot);
-  basep = __shfl_sync(kFullMask, basep, 0);
-  unsigned long long at = (basep >> kFsumBits) + (ex >> kFsumBits);
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-    if (app[q]) F[at++] = v[q];
-  unsigned long long tote;
-  const unsigned long long exe = warp_excl_scan64(nesum, lane, &tote);
-  if (tote == 0) return;
-  unsigned long long basee = 0;
-  if (lane == 0) basee = atomicAdd(&ctrl->nE, tote);
-  basee = __shfl_sync(kFullMask, basee, 0);
-  unsigned long long *E = E_of(p, ctrl->t);
-  unsigned long long ate = basee + exe;
-#pragma unroll
-  for (int q = 0; q < N; ++q) {
-    unsigned long long ne = 0;
-    if (app[q]) {
-      const unsigned long long od =
-          (unsigned long long)(__ldg(p.out_ptr + v[q] + 1) - __ldg(p.out_ptr + v[q]));
-      ne = (od + p.LE - 1) / p.LE;
-    }
-    const unsigned long long head = ne < 4 ? ne : 4;
-    for (unsigned long long k = 0; k < head; ++k)
-      E[ate + k] = ((unsigned long long)(uint32_t)v[q] << 32) | k;
-    unsigned big = __ballot_sync(kFullMask, ne > 4);
-    while (big) {  // long lists are written by the whole warp
-      const int src = __ffs(big) - 1;
-      big &= big - 1;
-      const unsigned long long c = __shfl_sync(kFullMask, ne, src);
-      const unsigned long long a = __shfl_sync(kFullMask, ate, src);
-      const int32_t r = __shfl_sync(kFullMask, v[q], src);
-      for (unsigned long long k = 4 + lane; k < c; k += 32)
-        E[a + k] = ((unsigned long long)(uint32_t)r << 32) | k;
-    }
-    ate += ne;
-  }
-}
-
 
 // Finishes one row piece after its deltas are ORed into acc (words
 // [c*CW, c*CW+CW) of the row): a row of one piece compares with X[v] and
@@ -442,7 +353,7 @@ __device__ __forceinline__ void count_pass_words(const Params &p, int32_t v, int
   }
 }
 
-// Staged frontier appends. Every warp of a pull keeps the rows it appends
+// Staged frontier appends. Every warp of a pull or push keeps the rows it appends
 // in a buffer of its own in shared memory and moves them to F_t (and their
 // out-arc pieces to E_t) kStageRows at a time, with one atomicAdd on each of
 // the two round counters per flush. Appending straight to F_t costs those two
@@ -542,6 +453,14 @@ __device__ __forceinline__ int stage_flush(const Params &p, Ctrl *ctrl, int32_t 
   }
   __syncwarp();
   return 0;
+}
+
+// Stages the rows whose lane has app set, without a flush (the caller made
+// room for 32 more); returns the new stage count (warp-uniform).
+__device__ __forceinline__ int stage_put(int32_t *stage, int cnt, int32_t v, bool app, int lane) {
+  const unsigned mask = __ballot_sync(kFullMask, app);
+  if (app) stage[cnt + __popc(mask & ((1u << lane) - 1u))] = v;
+  return cnt + __popc(mask);
 }
 
 // Stages the rows whose lane has app set (flushing first when the buffer
@@ -901,7 +820,8 @@ __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const Rou
                                           int lane, int64_t warp, int64_t nwarps,
                                           uint32_t &my_mact, unsigned long long &my_work,
                                           uint32_t &my_scan, uint32_t &my_gath,
-                                          uint32_t &my_items, uint32_t &my_rows) {
+                                          uint32_t &my_items, uint32_t &my_rows,
+                                          int32_t *stage, int &scnt) {
   constexpr int UNR = 4;
   const unsigned long long *Ep = E_of(p, t - 1);
   const int64_t nEp = (int64_t)ctrl->nE_prev;
@@ -980,7 +900,9 @@ __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const Rou
           }
         app[q] = changed && !set_bit(rb.Ccur, v[q]);
       }
-      frontier_append_n<UNR>(p, ctrl, rb.F, v, app, lane);
+      if (scnt > kStageRows - 32 * UNR) scnt = stage_flush(p, ctrl, rb.F, stage, scnt, lane);
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) scnt = stage_put(stage, scnt, v[q], app[q], lane);
     }
   }
 }
@@ -1046,14 +968,14 @@ __global__ void __launch_bounds__(kBlock, CW <= 4 ? PG_PULL_MIN_BLOCKS : PG_PULL
   if (mode == kModeSparse || mode == kModeMixed)
     pull_sparse<CW, G, PW>(p, ctrl, rb, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
                            my_items, my_rows, stage, scnt);
-  if (scnt) stage_flush(p, ctrl, rb.F, stage, scnt, lane);
   // push rounds for rows of up to 4 words of one graph (8-word rows and
   // packed batches push in k_push, launched after this kernel: the 8-word
   // kernel keeps its registers for the dense sweep)
   if constexpr (!PW && CW <= 4)
     if (mode == kModePush && !p.push_kernel)
       pull_push<CW>(p, ctrl, rb, t, lane, warp, nwarps, my_mact, my_work, my_scan, my_gath,
-                    my_items, my_rows);
+                    my_items, my_rows, stage, scnt);
+  if (scnt) stage_flush(p, ctrl, rb.F, stage, scnt, lane);
   pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 

@@ -28,8 +28,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_push(Params p) {
   const int lane = threadIdx.x & 31;
   uint32_t my_mact = 0, my_scan = 0, my_gath = 0, my_items = 0, my_rows = 0;
   unsigned long long my_work = 0;
+  __shared__ int32_t s_stage[kBlock / 32][kStageRows];  // staged frontier rows per warp
+  int32_t *stage = s_stage[threadIdx.x >> 5];
+  int scnt = 0;
   pull_push<CW, PW>(p, ctrl, rb, t, lane, gtid >> 5, ((int64_t)gridDim.x * kBlock) >> 5,
-                    my_mact, my_work, my_scan, my_gath, my_items, my_rows);
+                    my_mact, my_work, my_scan, my_gath, my_items, my_rows, stage, scnt);
+  if (scnt) stage_flush(p, ctrl, rb.F, stage, scnt, lane);
   pull_end(p, ctrl, t, my_mact, my_work, my_scan, my_gath, my_items, my_rows);
 }
 
