@@ -292,6 +292,37 @@ def test_invalid_csr_descent_anywhere_in_a_row(pos):
         pg.Graph.from_csr(rp, dup, n)
 
 
+def test_pinned_host_csr_upload_is_exact():
+    """A CSR in pinned host memory (the end-to-end leg's input): the device
+    copy equals the input, with an arc count whose bytes are not a multiple
+    of 16 and from a source 16-byte aligned or starting mid-buffer; counts
+    equal those of the same graph uploaded from pageable memory."""
+    torch = pytest.importorskip("torch")
+    g = I.er(400_000, 48, 71)
+    rp, col = np.array(g.row_ptr), np.array(g.col)
+    drop = 1 + (int(col.size) % 4 == 1)  # leave m % 4 != 0
+    rp = rp.copy()
+    rp[-1] -= drop
+    col = col[:col.size - drop]
+    assert (col.size * 4) % 16 != 0 and col.size * 4 >= 64 << 20
+    rp_p = torch.from_numpy(rp).pin_memory()
+    big = torch.empty(col.size + 3, dtype=torch.int32).pin_memory()  # source at +12 bytes
+    big[3:] = torch.from_numpy(col)
+    col_p = big[3:]
+    assert col_p.data_ptr() % 16 != 0
+    big4 = torch.empty(col.size, dtype=torch.int32).pin_memory()
+    big4.copy_(torch.from_numpy(col))
+    seeds = I.seeds(g.n, 64, 72)
+    want = pg.propagate_p(pg.Graph.from_csr(rp, col, g.n, directed=True), seeds)
+    for c in (big4, col_p):
+        G = pg.Graph.from_csr(rp_p.numpy(), c.numpy(), g.n, directed=True, relabel=False)
+        r2, c2 = G.csr()
+        assert np.array_equal(r2, rp) and np.array_equal(c2, col)
+        res = pg.propagate_p(G, seeds)
+        assert np.array_equal(res.counts, want.counts)
+        G.close()
+
+
 def test_device_pointer_graph_equals_host_graph():
     torch = pytest.importorskip("torch")
     g = I.rmat(12, 8, 21, directed=True)
