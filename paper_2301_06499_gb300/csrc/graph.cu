@@ -1153,6 +1153,9 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
       }
       if (cursor) cudaFreeAsync(cursor, st);
       if (rc == PG_OK) rc = cuda_status(cudaStreamSynchronize(st));
+      release(g->pieces.list);  // scratch of the scatter, not a cached list
+      g->pieces.L = 0;
+      g->pieces.count = 0;
     }
   }
   if (rc == PG_OK && (flags & PG_REVERSE) && directed) {

@@ -966,8 +966,11 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     pl.smem_counts = ncols <= kSmemCountMax;
     pl.post_smem = pl.smem_counts ? sizeof(uint32_t) * (size_t)ncols : 0;
   }
-  rc = ensure_pieces(g, pl.L, st);
-  if (rc) return rc;
+  // the list of every row's pieces is read only by the wide-row pull (its
+  // dense rounds); the others take their dense rounds from the sliced-ELL
+  // copy and size the sparse work list by a bound on the piece count
+  if (pl.wide && (rc = ensure_pieces(g, pl.L, st))) return rc;
+  const int64_t npieces = pl.wide ? g->pieces.count : g->n + g->m / pl.L + 1;
   if (cl.o.direction != PG_DIR_SPARSE && !pl.wide && (rc = ensure_sell(g, kSellPiece, st)))
     return rc;
   const int64_t n = g->n;
@@ -986,7 +989,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
       {&w.Sat, bm_bytes},
       {&w.F0, sizeof(int32_t) * (size_t)n}, {&w.F1, sizeof(int32_t) * (size_t)n},
       {&w.E, sizeof(unsigned long long) * (size_t)e_cap},
-      {&w.A, sizeof(ulonglong2) * (size_t)std::max<int64_t>(g->pieces.count, 1)},
+      {&w.A, sizeof(ulonglong2) * (size_t)std::max<int64_t>(npieces, 1)},
       {&w.counts, sizeof(uint32_t) * (size_t)row_cap * (size_t)ncols},
       {&w.rs, sizeof(RoundStats) * (size_t)(row_cap + 2)},
       {&w.ctrl, sizeof(Ctrl)}, {&w.seeds, sizeof(int32_t) * (size_t)sp}};
@@ -1053,8 +1056,8 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.push_kernel = push_kernel ? 1 : 0;
   pl.push = push_kernel ? push_fn(pl.CW, pw) : nullptr;
   p.A = (ulonglong2 *)w.A.p;
-  p.Pall = (const ulonglong2 *)g->pieces.list.p;
-  p.nPall = g->pieces.count;
+  p.Pall = pl.wide ? (const ulonglong2 *)g->pieces.list.p : nullptr;
+  p.nPall = pl.wide ? g->pieces.count : 0;
   p.sell_items = (const ulonglong2 *)g->sell.items.p;
   p.sell_col = (const int32_t *)g->sell.col.p;
   p.sell_off = (const int64_t *)g->sell.off.p;
@@ -1120,7 +1123,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   }
   p.dense_tma = pl.tma ? 1 : 0;
 
-  const int64_t pull_threads = std::max<int64_t>({p.nPall * pl.G, nbm, p.sell_chunks * 32});
+  const int64_t pull_threads = std::max<int64_t>({npieces * pl.G, nbm, p.sell_chunks * 32});
   pl.grid_pull = occupancy_grid((const void *)pl.pull, 0, pull_threads);
   if (pl.push) pl.grid_push = occupancy_grid((const void *)pl.push, 0, n + g->m / kExpandArcs + 1);
   // the wide part A has a warp per 32 rows x 16 words
