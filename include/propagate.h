@@ -354,7 +354,7 @@ pg_status pg_graph_generate(const pg_generator *gen, unsigned flags, void *strea
  * written). Errors: PG_EINVAL, PG_ECUDA. */
 pg_status pg_graph_copy_csr(const pg_graph *g, int64_t *row_ptr, int32_t *col, void *stream);
 
-/* n and m of a graph. *//* n and m of a graph. */
+/* n and m of a graph. */
 pg_status pg_graph_info(const pg_graph *g, int64_t *n, int64_t *m);
 
 /* A safe max_rounds: every eccentricity is at most n - 1. */
