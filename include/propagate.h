@@ -479,8 +479,9 @@ pg_status pg_propagate_p_noalloc(const int64_t *row_ptr, const int32_t *col, int
  * one disjoint union and runs each class as a single PROPAGATE-P: one pull
  * and one post launch per round for all of its graphs. Each graph's counts
  * equal what pg_propagate_p gives for it alone (its bits never leave its own
- * nodes); only m_active is not kept per graph (pg_batch_result zero-fills
- * it). A graph of at least 2^16 nodes whose four signature arrays (n x
+ * nodes), and so does its m_active (the kernels add each active row's
+ * in-degree to its own graph's slot of the round as well). A graph of at
+ * least 2^16 nodes whose four signature arrays (n x
  * words x 8 bytes each) fill half of L2 or more runs alone instead, as
  * pg_propagate_p would run it: it fills the GPU by itself, and alone it
  * keeps part of its arrays in L2 from round to round. The paper runs one
@@ -533,7 +534,9 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream);
 
 /*
  * Copies graph index's counts of the last run into out (out->s must equal
- * the graph's s; rows 0..min(T, out->max_rounds)). Errors: PG_EINVAL (no run,
+ * the graph's s; rows 0..min(T, out->max_rounds)) and, when out->m_active is
+ * set, its own m_active as pg_propagate_p writes it (entries
+ * 0..min(T + 1, out->max_rounds + 1), zero beyond). Errors: PG_EINVAL (no run,
  * bad index or s), PG_ERANGE (T > out->max_rounds; out->rounds = T).
  */
 pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out);

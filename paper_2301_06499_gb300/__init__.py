@@ -305,14 +305,15 @@ class Batch:
         _abi.check(_abi.lib().pg_batch_run(self._h, o, st), "pg_batch_run")
 
     def result(self, index: int) -> Result:
-        """Counts of graph `index` from the last run (m_active is not kept
-        per graph in a batch and reads as zeros)."""
+        """Counts and m_active of graph `index` from the last run (its own
+        m_active, as if it had run alone)."""
         s, n = self._s[index], self._n[index]
         cap = min(max(n - 1, 0), 64)
         while True:
             counts = np.zeros((cap + 1, s), dtype=np.uint32)
+            mact = np.zeros(cap + 2, dtype=np.uint64)
             c = _abi.Counts(s=s, max_rounds=cap, rounds=0, reserved=0,
-                            counts=counts.ctypes.data, m_active=None)
+                            counts=counts.ctypes.data, m_active=mact.ctypes.data)
             rc = _abi.lib().pg_batch_result(self._h, int(index), ctypes.byref(c))
             if rc == _abi.PG_ERANGE and c.rounds > cap:
                 cap = int(c.rounds)  # the exact size, known now
@@ -320,8 +321,8 @@ class Batch:
             _abi.check(rc, "pg_batch_result")
             break
         T = int(c.rounds)
-        return Result(rounds=T, counts=counts[:T + 1].copy(),
-                      m_active=np.zeros(T + 2, dtype=np.uint64), s=s, n=n)
+        return Result(rounds=T, counts=counts[:T + 1].copy(), m_active=mact[:T + 2].copy(),
+                      s=s, n=n)
 
     def set_streams(self, streams: int):
         """pg_batch_set_streams: groups run at once (1 = one after another)."""

@@ -44,6 +44,7 @@ struct pg_batch {
     int directed = 0;
     int32_t rounds = -1;
     std::vector<uint32_t> counts;  // (rounds+1) x s after a run
+    std::vector<uint64_t> m_active;  // by round after a run (rows 0..rounds+1 at least)
     bool open = true;              // still receiving rows during a run
   };
   struct Group {
@@ -105,16 +106,18 @@ pg_status build_solo(pg_batch *b, int32_t i, cudaStream_t st) {
   return PG_OK;
 }
 
-// One propagation of group gr into sink (counts windows).
+// One propagation of group gr into sink (counts windows); mact (optional):
+// m_active by round, one column per member ([round][member]).
 pg_status run_group(pg_batch::Group &gr, WindowSink sink, void *ctx, int32_t *T,
-                    const pg_options *o, void *stream, pg_stats *st) {
+                    const pg_options *o, void *stream, pg_stats *st,
+                    std::vector<unsigned long long> *mact = nullptr) {
   if (gr.solo)
     return propagate_columns(gr.g, gr.seeds.data(), (int32_t)gr.seeds.size(), gr.max_rounds, sink,
-                             ctx, T, o, stream, st);
+                             ctx, T, o, stream, st, mact);
   return propagate_batch_group(gr.g, gr.seeds.data(), gr.seed_bit.data(), (int32_t)gr.seeds.size(),
                                (const int32_t *)gr.node_graph.p, (const int32_t *)gr.graph_s.p,
                                (const int32_t *)gr.graph_col0.p, gr.graph_m.data(), gr.ncols,
-                               gr.s_bits, gr.max_rounds, sink, ctx, T, o, stream, st);
+                               gr.s_bits, gr.max_rounds, sink, ctx, T, o, stream, st, mact);
 }
 
 void free_groups(pg_batch *b) {
@@ -323,6 +326,7 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
   if (rc) return rc;
   for (auto &it : b->items) {
     it.counts.clear();
+    it.m_active.clear();
     it.rounds = -1;
     it.open = true;
   }
@@ -348,11 +352,20 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
       pg_stats st1{};
       const pg_options *o = opt ? opt : (gr.tuned ? &gr.opt : nullptr);
       const auto t0 = std::chrono::steady_clock::now();
-      const pg_status e = run_group(gr, &take_window, &ctx, &T, o, b->streams[w], &st1);
+      std::vector<unsigned long long> mact;
+      const pg_status e = run_group(gr, &take_window, &ctx, &T, o, b->streams[w], &st1, &mact);
       if (e) {
         errs[w] = e;
         failed.store(1);
         return;
+      }
+      // each member's own m_active: its column of the group's
+      const size_t cols = gr.members.size();
+      const size_t rows = mact.size() / cols;
+      for (size_t k = 0; k < cols; ++k) {
+        auto &it = b->items[gr.members[k]];
+        it.m_active.resize(rows);
+        for (size_t t = 0; t < rows; ++t) it.m_active[t] = mact[t * cols + k];
       }
       gr.last_ms =
           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -369,6 +382,7 @@ pg_status pg_batch_run(pg_batch *b, const pg_options *opt, void *stream) {
   if (rc) {
     for (auto &it : b->items) {
       it.counts.clear();
+      it.m_active.clear();
       it.rounds = -1;
     }
     return rc;
@@ -463,7 +477,12 @@ pg_status pg_batch_result(pg_batch *b, int32_t index, pg_counts *out) {
   const int32_t rows = std::min(it.rounds, out->max_rounds) + 1;
   std::memcpy(out->counts, it.counts.data(), sizeof(uint32_t) * (size_t)rows * out->s);
   out->rounds = it.rounds;
-  if (out->m_active) std::memset(out->m_active, 0, sizeof(uint64_t) * ((size_t)out->max_rounds + 2));
+  if (out->m_active) {  // as pg_propagate_p: rounds 0..min(T + 1, max_rounds + 1)
+    std::memset(out->m_active, 0, sizeof(uint64_t) * ((size_t)out->max_rounds + 2));
+    const int32_t last = std::min(it.rounds + 1, out->max_rounds + 1);
+    for (int32_t t = 0; t <= last && t < (int32_t)it.m_active.size(); ++t)
+      out->m_active[t] = it.m_active[(size_t)t];
+  }
   return it.rounds > out->max_rounds ? PG_ERANGE : PG_OK;
 }
 

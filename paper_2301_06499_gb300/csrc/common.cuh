@@ -117,6 +117,9 @@ struct Params {
   const int64_t *seg_chunk0;
   int32_t *dlist;
   int64_t *dpref;
+  // batch, on request: m_active of each graph by round, [row_cap + 2][nseg],
+  // slot = round - row_base like rs (else null)
+  unsigned long long *gmact;
   const int32_t *perm;  // relabelled graph: caller id -> internal id (else null)
   int64_t perm_n;       // nodes of the relabelled graph (replicas: a seed k*perm_n + x
                         // of copy k maps to k*perm_n + perm[x])

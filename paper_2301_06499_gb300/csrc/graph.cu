@@ -596,7 +596,7 @@ static std::vector<DevBuf *> workspace_parts(Workspace &w) {
   return {&w.X,  &w.Y,  &w.D0,     &w.D1, &w.C0,   &w.C1,   &w.K0,    &w.K1,
           &w.Sat, &w.RB, &w.KW0,   &w.KW1, &w.F0,  &w.F1,   &w.E,     &w.A,
           &w.counts, &w.rs, &w.ctrl, &w.seeds, &w.seed_bits, &w.gfsum, &w.gthr,
-          &w.dlist, &w.dpref, &w.E1};
+          &w.dlist, &w.dpref, &w.E1, &w.gm};
 }
 
 pg_status carve_workspace(Workspace &w, const std::vector<std::pair<DevBuf *, size_t>> &needs) {

@@ -24,7 +24,7 @@ struct Workspace {
   DevBuf arena;
   size_t used = 0;  // end of the laid-out parts in the arena
   DevBuf X, Y, D0, D1, C0, C1, K0, K1, Sat, RB, KW0, KW1, F0, F1, E, A, counts, rs, ctrl, seeds,
-      seed_bits, gfsum, gthr, dlist, dpref, E1;
+      seed_bits, gfsum, gthr, dlist, dpref, E1, gm;
   Ctrl *ctrl_h = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;  // timing events
@@ -133,12 +133,15 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
                                 const int64_t *graph_m, int32_t ncols, int32_t s_bits,
                                 int32_t max_rounds, WindowSink sink, void *sink_ctx,
                                 int32_t *rounds, const pg_options *opt, void *stream,
-                                pg_stats *st_out);
+                                pg_stats *st_out, std::vector<unsigned long long> *mact = nullptr);
 // Seeds of several requests merged on one graph: seed i owns bit and count
 // column i, and a node may carry several seeds; windows go to the sink.
+// mact (optional): m_active by round, rows 0..rounds+1 (a packed batch: one
+// column per graph of the union, [round][graph]; else one column).
 pg_status propagate_columns(pg_graph *g, const int32_t *seeds, int32_t nseeds, int32_t max_rounds,
                             WindowSink sink, void *sink_ctx, int32_t *rounds,
-                            const pg_options *opt, void *stream, pg_stats *st_out);
+                            const pg_options *opt, void *stream, pg_stats *st_out,
+                            std::vector<unsigned long long> *mact = nullptr);
 // A handle sharing master's device CSR, out-CSR and sliced-ELL copy (built
 // first if missing) with its own workspace, piece list and CUDA graphs, so
 // that several propagations on one graph can run at once on different

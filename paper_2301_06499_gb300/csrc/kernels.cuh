@@ -494,6 +494,23 @@ __device__ __forceinline__ int stage_append(const Params &p, Ctrl *ctrl, int32_t
 #define PG_DENSE_UNROLL_WIDE 4
 #endif
 
+// A packed batch: adds a warp's m_active of round t (x on each lane whose
+// row v is active) to the graph of those rows with one atomic. The rows of a
+// sliced-ELL chunk are one graph's; every lane of the warp calls it.
+__device__ __forceinline__ void gm_add_chunk(const Params &p, const Ctrl *ctrl, int32_t v,
+                                             uint32_t x) {
+  const unsigned am = __ballot_sync(kFullMask, x != 0u);
+  if (!am) return;
+  const int32_t va = __shfl_sync(kFullMask, v, __ffs(am) - 1);
+  unsigned long long sum = x;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFullMask, sum, off);
+  if ((threadIdx.x & 31) == 0)
+    atomicAdd(p.gmact + (size_t)(ctrl->t - ctrl->row_base) * (size_t)p.nseg +
+                  __ldg(p.node_graph + va),
+              sum);
+}
+
 // Dense round over the sliced-ELL copy: a warp per chunk of 32 pieces, lane
 // l owns piece l; step k reads arc k of all 32 pieces in one coalesced load,
 // and the U deltas of a lane's U steps are gathered together. The sweep is
@@ -637,6 +654,7 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       my_scan += (uint32_t)len;
     }
     act = act && any_delta;  // no changed in-neighbour: not active in round t
+    uint32_t gdeg = 0;       // this lane's m_active of the chunk
     if (PW && act) {
       if (pw_words) {
         const uint32_t deg =
@@ -656,7 +674,9 @@ __device__ __forceinline__ void pull_dense(const Params &p, Ctrl *ctrl, const ui
       }
       my_mact += deg;
       my_work += (unsigned long long)deg * (unsigned long long)seeds_of(p, v);
+      gdeg = deg;
     }
+    if (p.gmact) gm_add_chunk(p, ctrl, v, gdeg);  // a packed batch: per graph
     bool app = false;
     if (act && row_changed) {
       if (whole) {
@@ -888,6 +908,10 @@ __device__ __forceinline__ void pull_push(const Params &p, Ctrl *ctrl, const Rou
           my_mact += indeg;
           my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, v[q]);
           ++my_rows;
+          if (p.gmact)  // a packed batch: the claimed row's own graph
+            atomicAdd(p.gmact + (size_t)(t - ctrl->row_base) * (size_t)p.nseg +
+                          __ldg(p.node_graph + v[q]),
+                      (unsigned long long)indeg);
         }
         bool changed = false;
 #pragma unroll

@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(kBlock) k_zero(Params p, int64_t count_words, 
   for (int64_t i = gtid; i < count_words; i += nth) p.counts[i] = 0u;
   unsigned long long *rsw = reinterpret_cast<unsigned long long *>(p.rs);
   for (int64_t i = gtid; i < rs_words; i += nth) rsw[i] = 0ULL;
+  if (p.gmact)
+    for (int64_t i = gtid; i < (int64_t)(p.row_cap + 2) * p.nseg; i += nth) p.gmact[i] = 0ULL;
   if (gtid == 0) {
     Ctrl *c = p.ctrl;
     c->t = 0;
@@ -458,6 +460,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_post(Params p) {
               my_mact += (unsigned long long)indeg;
               my_work += (unsigned long long)indeg * (unsigned long long)seeds_of(p, x[q]);
               ++my_rows;
+              if (p.gmact)  // a packed batch: the claimed row's own graph, round t+1
+                atomicAdd(p.gmact + (size_t)(row + 1) * (size_t)p.nseg + __ldg(p.node_graph + x[q]),
+                          (unsigned long long)indeg);
             }
             np[q] = (uint32_t)((indeg + p.L - 1) / p.L);
           }
@@ -589,6 +594,12 @@ __global__ void k_window_shift(Params p, int64_t count_words, int32_t rs_slots) 
         p.rs[i] = RoundStats{};
     }
   }
+  if (p.gmact)  // per graph: the next round's slot to slot 0, the rest cleared
+    for (int64_t k = gtid; k < p.nseg; k += nth) {
+      const unsigned long long c = p.gmact[(size_t)p.row_cap * p.nseg + k];
+      for (int32_t i = 1; i < rs_slots; ++i) p.gmact[(size_t)i * p.nseg + k] = 0ULL;
+      p.gmact[k] = c;
+    }
   if (gtid == 0) {
     p.ctrl->row_base += p.row_cap;
     p.ctrl->status = 0;
@@ -770,6 +781,8 @@ struct Call {
   std::vector<uint32_t> stage;
   const int32_t *perm = nullptr;  // relabelled graph: caller id -> internal id
   int64_t perm_n = 0;
+  // a packed batch, on request: m_active of each graph by round ([round][graph])
+  std::vector<unsigned long long> *gm_h = nullptr;
 };
 
 static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_base, int32_t rows,
@@ -809,6 +822,17 @@ static pg_status copy_window(Call &cl, const Params &p, int col0, int32_t row_ba
       d.changed += tmp[i].changed;
       d.fsum += tmp[i].fsum;
       d.rows += tmp[i].rows;
+    }
+    if (p.gmact && cl.gm_h) {
+      const size_t ns = (size_t)p.nseg;
+      std::vector<unsigned long long> g((size_t)rs_rows * ns);
+      e = cudaMemcpyAsync(g.data(), p.gmact, sizeof(unsigned long long) * g.size(),
+                          cudaMemcpyDeviceToHost, cl.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cl.st);
+      if (e != cudaSuccess) return cuda_status(e);
+      std::vector<unsigned long long> &h = *cl.gm_h;
+      if (h.size() < ((size_t)row_base + rs_rows) * ns) h.resize(((size_t)row_base + rs_rows) * ns, 0ULL);
+      for (size_t i = 0; i < g.size(); ++i) h[(size_t)row_base * ns + i] += g[i];
     }
   }
   return cuda_status(cudaStreamSynchronize(cl.st));
@@ -1013,6 +1037,10 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
     needs.push_back({&w.dlist, sizeof(int32_t) * (size_t)g->nseg});
     needs.push_back({&w.dpref, sizeof(int64_t) * ((size_t)g->nseg + 1)});
   }
+  // a packed batch whose caller asked for each graph's m_active: its window
+  const bool gm_on = bs && g->nseg > 0 && bs->graph_m && !pw && cl.gm_h;
+  if (gm_on)
+    needs.push_back({&w.gm, sizeof(unsigned long long) * (size_t)(row_cap + 2) * (size_t)g->nseg});
   if ((rc = carve_workspace(w, needs))) return rc;
   if (!w.ctrl_h) {
     if (cudaMallocHost((void **)&w.ctrl_h, 2 * sizeof(Ctrl)) != cudaSuccess) {
@@ -1083,6 +1111,7 @@ static pg_status run_pass(Call &cl, const int32_t *seeds_h, int sp, int col0, bo
   p.seg_chunk0 = dl ? (const int64_t *)g->sell.chunk0.p : nullptr;
   p.dlist = dl ? (int32_t *)w.dlist.p : nullptr;
   p.dpref = dl ? (int64_t *)w.dpref.p : nullptr;
+  p.gmact = gm_on ? (unsigned long long *)w.gm.p : nullptr;
   p.perm = cl.perm;
   p.perm_n = cl.perm_n;
   p.rs = (RoundStats *)w.rs.p;
@@ -1572,10 +1601,13 @@ static pg_status propagate(pg_graph *g, const int32_t *seeds, int32_t s, pg_coun
 // One PROPAGATE-P pass whose counts windows go to a sink: the seeds of a
 // packed batch (bs set) or of several requests merged on one graph (seed i
 // owns bit and column i; a node may carry several bits).
+// mact (optional): m_active by round, rows 0..rounds+1, one column per graph
+// of a packed batch (else one column).
 static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseeds,
                                 const BatchSeg *bs, int32_t max_rounds, WindowSink sink,
                                 void *sink_ctx, int32_t *rounds, const pg_options *opt,
-                                void *stream, pg_stats *st_out) {
+                                void *stream, pg_stats *st_out,
+                                std::vector<unsigned long long> *mact) {
   const int32_t ncols = bs ? bs->ncols : nseeds;
   if (!g || !seeds || nseeds < 1 || ncols < 1 || max_rounds < 0 || !sink || !rounds)
     return PG_EINVAL;
@@ -1602,6 +1634,10 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
   int64_t cap_rows = std::max<int64_t>(64, (256LL << 20) / (4LL * ncols));
   if (cl.o.window_rows > 0) cap_rows = cl.o.window_rows;
   cl.row_cap = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)max_rounds + 1, cap_rows));
+  // each graph's m_active of a packed batch comes from the kernels' window
+  const bool per_graph = mact && bs && bs->graph_m && g->nseg > 0;
+  std::vector<unsigned long long> gm;
+  if (per_graph) cl.gm_h = &gm;
   PassOut po;
   pg_status rc = run_pass(cl, seeds, nseeds, 0, false, g->hint_p, po, bs);
   if (rc) {
@@ -1613,6 +1649,14 @@ static pg_status propagate_sink(pg_graph *g, const int32_t *seeds, int32_t nseed
   pg_stats st{};
   const int32_t last_stats = std::min(po.rounds + 1, max_rounds + 1);
   if (cl.rs_h.size() < (size_t)last_stats + 1) cl.rs_h.resize((size_t)last_stats + 1, RoundStats{});
+  if (per_graph) {
+    const size_t cols = (size_t)g->nseg;
+    gm.resize(((size_t)last_stats + 1) * cols, 0ULL);
+    mact->assign(gm.begin(), gm.begin() + ((size_t)last_stats + 1) * cols);
+  } else if (mact) {
+    mact->resize((size_t)last_stats + 1);
+    for (int32_t t = 0; t <= last_stats; ++t) (*mact)[t] = cl.rs_h[t].m_active;
+  }
   for (int32_t t = 0; t <= last_stats; ++t) {
     const RoundStats &r = cl.rs_h[t];
     st.m_active_total += r.m_active;
@@ -1655,11 +1699,11 @@ pg_status propagate_batch_group(pg_graph *g, const int32_t *seeds, const int32_t
                                 const int64_t *graph_m, int32_t ncols, int32_t s_bits,
                                 int32_t max_rounds, WindowSink sink, void *sink_ctx,
                                 int32_t *rounds, const pg_options *opt, void *stream,
-                                pg_stats *st_out) {
+                                pg_stats *st_out, std::vector<unsigned long long> *mact) {
   if (!seed_bit || !node_graph_d || !graph_s_d || !graph_col0_d || s_bits < 1) return PG_EINVAL;
   BatchSeg bs{node_graph_d, graph_s_d, graph_col0_d, seed_bit, ncols, s_bits, graph_m};
   return propagate_sink(g, seeds, nseeds, &bs, max_rounds, sink, sink_ctx, rounds, opt, stream,
-                        st_out);
+                        st_out, mact);
 }
 
 int64_t workspace_bytes(const pg_graph *g, int32_t s, int32_t max_rounds, int32_t window_rows) {
@@ -1686,9 +1730,10 @@ int64_t workspace_bytes_nm(int64_t n, int64_t m, int32_t s, int32_t max_rounds,
 
 pg_status propagate_columns(pg_graph *g, const int32_t *seeds, int32_t nseeds, int32_t max_rounds,
                             WindowSink sink, void *sink_ctx, int32_t *rounds,
-                            const pg_options *opt, void *stream, pg_stats *st_out) {
+                            const pg_options *opt, void *stream, pg_stats *st_out,
+                            std::vector<unsigned long long> *mact) {
   return propagate_sink(g, seeds, nseeds, nullptr, max_rounds, sink, sink_ctx, rounds, opt,
-                        stream, st_out);
+                        stream, st_out, mact);
 }
 
 }  // namespace pg

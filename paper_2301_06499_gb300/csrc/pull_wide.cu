@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_pull_wide(Params p) {
         }
         my_mact += deg;
         my_work += deg * (unsigned long long)seeds_of(p, v);
+        if (p.gmact && deg)  // a packed batch: the row's own graph
+          atomicAdd(p.gmact + (size_t)(t - ctrl->row_base) * (size_t)p.nseg + __ldg(p.node_graph + v),
+                    deg);
       }
       if (row_changed && (dense ? any_delta : true)) {
         if (whole) {

@@ -1,7 +1,8 @@
 """Batched PROPAGATE-P (pg_batch_*): every graph's per-round, per-seed counts
-in a batch are bit-exact with the oracle and with the same graph run alone
-through pg_propagate_p; the batch is credited exactly the work of the plain
-runs (the work measure is defined by the method, not the schedule)."""
+and its own m_active in a batch are bit-exact with the oracle and with the
+same graph run alone through pg_propagate_p; the batch is credited exactly
+the work of the plain runs (the work measure is defined by the method, not
+the schedule)."""
 import functools
 
 import numpy as np
@@ -53,6 +54,7 @@ def test_batch_equals_plain_and_oracle():
             plain_work += work
             assert got.rounds == want.rounds, (it.graph.name, got.rounds, want.rounds)
             assert np.array_equal(got.counts, want.counts), it.graph.name
+            assert np.array_equal(got.m_active, want.m_active), it.graph.name
         assert st["graphs"] == len(items)
         assert st["groups"] == len({_width_class(it.s) for it in items})
         assert st["seed_edge_traversals"] == plain_work
@@ -64,6 +66,14 @@ def test_batch_equals_plain_and_oracle():
             got = b1.result(0)
         assert got.rounds == want["rounds"]
         assert np.array_equal(got.counts, want["counts"])
+        assert np.array_equal(got.m_active, want["m_active"])
+    # each graph's own m_active inside a packed batch, against the oracle
+    with pg.Batch() as b:
+        for it in items[:8]:
+            b.add_inputs(it.graph, it.seeds)
+        b.run()
+        for k, it in enumerate(items[:8]):
+            assert np.array_equal(b.result(k).m_active, oracle.run(it.graph, it.seeds)["m_active"])
 
 
 def test_batch_result_independent_of_company():
@@ -79,6 +89,7 @@ def test_batch_result_independent_of_company():
     for k in range(10):
         assert runs[0][k].rounds == runs[1][k].rounds
         assert np.array_equal(runs[0][k].counts, runs[1][k].counts)
+        assert np.array_equal(runs[0][k].m_active, runs[1][k].m_active)
 
 
 def test_batch_edge_cases():
@@ -99,6 +110,7 @@ def test_batch_edge_cases():
             got = b.result(k)
             assert got.rounds == want["rounds"], g.name
             assert np.array_equal(got.counts, want["counts"]), g.name
+            assert np.array_equal(got.m_active, want["m_active"]), g.name
         g2 = I.cycle(40)
         k2 = b.add_inputs(g2, np.array([3, 17], np.int32))
         b.run()
@@ -121,6 +133,7 @@ def test_batch_wide_signatures():
         for k, (gg, ss) in enumerate(((g, sd), (g2, sd2))):
             want = oracle.run(gg, ss)
             assert np.array_equal(b.result(k).counts, want["counts"])
+            assert np.array_equal(b.result(k).m_active, want["m_active"])
 
 
 def test_batch_rejects_bad_input():
@@ -154,10 +167,12 @@ def test_batch_forced_direction(direction):
             want, _ = _plain(it)
             got = b.result(k)
             assert got.rounds == want.rounds and np.array_equal(got.counts, want.counts)
+            assert np.array_equal(got.m_active, want.m_active)
         for j, (g, sd) in enumerate(extra):
             want = oracle.run(g, sd)
             got = b.result(len(items) + j)
             assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])
+            assert np.array_equal(got.m_active, want["m_active"])
 
 
 @pytest.mark.parametrize("direction", [pg.PG_DIR_AUTO, pg.PG_DIR_SPARSE])
@@ -184,6 +199,7 @@ def test_batch_push_rounds(direction):
             plain_work += w
             got = b.result(k)
             assert got.rounds == want.rounds and np.array_equal(got.counts, want.counts)
+            assert np.array_equal(got.m_active, want.m_active)
         for j, (g, sd) in enumerate(extra):
             want = oracle.run(g, sd)
             G = pg.Graph.from_inputs(g)
@@ -192,6 +208,7 @@ def test_batch_push_rounds(direction):
             G.close()
             got = b.result(len(items) + j)
             assert got.rounds == want["rounds"] and np.array_equal(got.counts, want["counts"])
+            assert np.array_equal(got.m_active, want["m_active"])
         assert work == plain_work
 
 
@@ -223,10 +240,11 @@ def test_batch_large_graph_runs_alone():
             work += w
             assert np.array_equal(b.result(k).counts, want.counts)
         G = pg.Graph.from_inputs(big)
-        pg.propagate_p(G, sb)
+        alone_res = pg.propagate_p(G, sb)
         work += G.last_stats()["seed_edge_traversals"]
         G.close()
         assert st["seed_edge_traversals"] == work
+        assert np.array_equal(got.m_active, alone_res.m_active)  # the solo group's own
 
 
 def test_batch_streams_give_the_same_counts():
@@ -243,10 +261,39 @@ def test_batch_streams_give_the_same_counts():
             b.set_streams(k)
             b.run()
             runs.append(([b.result(i).counts for i in range(len(items) + 1)],
-                         b.stats()["seed_edge_traversals"]))
-    for counts, work in runs[1:]:
+                         b.stats()["seed_edge_traversals"],
+                         [b.result(i).m_active for i in range(len(items) + 1)]))
+    for counts, work, mact in runs[1:]:
         assert work == runs[0][1]
         for a, c in zip(runs[0][0], counts):
             assert np.array_equal(a, c)
+        for a, c in zip(runs[0][2], mact):
+            assert np.array_equal(a, c)
     want, _ = _plain(items[0])
     assert np.array_equal(runs[0][0][0], want.counts)
+
+
+@pytest.mark.parametrize("window_rows", [5, 64])
+def test_batch_m_active_across_window_shifts(window_rows):
+    """Each graph's m_active in a packed batch whose counts window holds only
+    a few rounds at a time (the per-graph slots move with it, the next
+    round's claims carried over), in pull and push rounds, against the oracle:
+    a 400-node path (400 rounds) beside short graphs, a grid, an R-MAT with
+    hub rows cut into pieces, and graphs whose last rounds differ."""
+    cases = [(I.path(400, directed=True), np.array([0, 7, 399], np.int32)),
+             (I.grid(50, 40, 0.05, 101), I.seeds(2000, 64, 102)),
+             (I.rmat(12, 8, 103, directed=True), I.seeds(4096, 64, 104)),
+             (I.er(3000, 4, 105), I.seeds(3000, 50, 106)),
+             (I.cycle(90), np.array([3, 40], np.int32))]
+    wants = [oracle.run(g, sd) for g, sd in cases]
+    for push in (1, 2):
+        with pg.Batch() as b:
+            for g, sd in cases:
+                b.add_inputs(g, sd)
+            b.run(opts=pg.options(window_rows=window_rows, sparse_push=push))
+            assert b.stats()["groups"] == 1
+            for k, ((g, _), want) in enumerate(zip(cases, wants)):
+                got = b.result(k)
+                assert got.rounds == want["rounds"], g.name
+                assert np.array_equal(got.counts, want["counts"]), g.name
+                assert np.array_equal(got.m_active, want["m_active"]), (g.name, push)
