@@ -523,9 +523,11 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
     for _ in range(warmup):
         res_p, work, plain_launches = plain()
         bst = batched()
+    mact_same = 0  # graphs whose own m_active in the batch equals the plain run's
     for k, r in enumerate(res_p):
         rb = batch.result(k)
         assert rb.rounds == r.rounds and np.array_equal(rb.counts, r.counts), items[k].graph.name
+        mact_same += int(np.array_equal(rb.m_active, r.m_active))
     assert bst["seed_edge_traversals"] == work, (bst["seed_edge_traversals"], work)
 
     def timed(fn):
@@ -628,6 +630,7 @@ def measure_batch(workload, rank, world, dev, steps, warmup, tune, tune_trials, 
                   "gpu_launches": int(plain_launches)},
         "batched_over_plain": plain_value and value / plain_value,
         "counts_identical": True,
+        "m_active_identical_graphs": f"{mact_same} of {len(items)}",
         "config": {"workload": workload,
                    "description": f"{count} graphs, n log-uniform in [{n_lo:g}, {n_hi:g}], "
                                   f"ER/R-MAT/grid (RNG {seed}), s from eps in {{0.1, 0.2}}",
