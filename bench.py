@@ -686,7 +686,8 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": r["config"], "plain": r["plain"],
-        "batched_over_plain": r["batched_over_plain"], "autotune": r["autotune"],
+        "batched_over_plain": r["batched_over_plain"], "counts_identical": r["counts_identical"],
+        "m_active_identical_graphs": r["m_active_identical_graphs"], "autotune": r["autotune"],
         "groups": r["groups"], "roofline": r["roofline"], "e2e": r["e2e"],
         "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "cpu_baseline": r["cpu_baseline"],
