@@ -294,8 +294,10 @@ void pg_default_options(pg_options *opt);
  *           0: the caller asserts the CSR is symmetric (in = out)
  *  flags    PG_DEVICE_PTRS / PG_BORROW / PG_REVERSE; host arrays are copied
  *  stream   cudaStream_t for the copies and validation kernels
- * Errors: PG_EINVAL for n < 1, n >= 2^31, m < 0, or a malformed CSR (checked
- * on the device); PG_ENOMEM; PG_ECUDA.
+ * Errors: PG_EINVAL for n < 1, n >= 2^27 or m >= 2^37 (the largest graph
+ * whose rounds the kernels can count: one 64-bit counter holds a round's
+ * changed rows in 27 bits and their out-arcs in 37), m < 0, or a malformed
+ * CSR (checked on the device); PG_ENOMEM; PG_ECUDA.
  */
 pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t m,
                             int directed, unsigned flags, void *stream, pg_graph **out);
@@ -327,7 +329,8 @@ pg_status pg_graph_is_relabelled(const pg_graph *g, int32_t *relabelled);
  * built on the device (a radix sort of the arc keys, a scan for the unique
  * ones) and becomes the graph as pg_graph_from_csr would make it (flags as
  * there, except PG_DEVICE_PTRS, PG_BORROW and PG_HOST_CSR). Errors: PG_EINVAL
- * (sizes, probabilities), PG_ENOMEM, PG_ECUDA.
+ * (sizes, probabilities; n >= 2^27 as for pg_graph_from_csr), PG_ENOMEM,
+ * PG_ECUDA.
  */
 #define PG_GEN_ER 0
 #define PG_GEN_RMAT 1
@@ -338,7 +341,7 @@ typedef struct {
   uint64_t seed;
   int64_t n;           /* PG_GEN_ER: nodes */
   double avg_degree;   /* PG_GEN_ER */
-  int32_t scale;       /* PG_GEN_RMAT: 2^scale nodes (1..30) */
+  int32_t scale;       /* PG_GEN_RMAT: 2^scale nodes (1..26) */
   int32_t reserved;
   double edge_factor;  /* PG_GEN_RMAT */
   double a, b, c;      /* PG_GEN_RMAT quadrant probabilities */
@@ -512,7 +515,9 @@ void pg_batch_free(pg_batch *b);
  * its seeds (host int32[s], distinct, in [0, n)). *index (may be NULL)
  * receives the graph's position, used by pg_batch_result. Adding after a run
  * repacks the batch on the next run. Errors: PG_EINVAL (arguments, seeds,
- * row_ptr ends); the CSR's columns are checked on the device at the run.
+ * row_ptr ends, n >= 2^27 or m >= 2^37 as for pg_graph_from_csr); the CSR's
+ * columns are checked on the device at the run. A width class whose graphs
+ * together pass those sizes is packed into several unions.
  */
 pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, int64_t n,
                        int64_t m, int directed, const int32_t *seeds, int32_t s,

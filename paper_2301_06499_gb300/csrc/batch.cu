@@ -139,78 +139,81 @@ pg_status build_groups(pg_batch *b, cudaStream_t st) {
   }
   std::sort(classes.begin(), classes.end());
   for (int c : classes) {
-    pg_batch::Group gr;
-    int64_t n = 0, m = 0;
-    int directed = 0;
-    std::vector<int32_t> alone;
+    std::vector<int32_t> packed, alone;
     for (int32_t i = 0; i < (int32_t)b->items.size(); ++i) {
       const auto &it = b->items[i];
       if (width_class((int32_t)it.seeds.size()) != c) continue;
-      if (runs_alone(it)) {
-        alone.push_back(i);
-        continue;
-      }
-      gr.members.push_back(i);
-      n += it.n;
-      m += it.m;
-      directed |= it.directed;
+      (runs_alone(it) ? alone : packed).push_back(i);
     }
     for (int32_t i : alone)
       if (pg_status rc = build_solo(b, i, st)) return rc;
-    if (gr.members.empty()) continue;
-    if (n >= 0x7FFFFFFFLL) return PG_EINVAL;
-    std::vector<int64_t> rp((size_t)n + 1);
-    std::vector<int32_t> col((size_t)std::max<int64_t>(m, 1));
-    std::vector<int32_t> node_graph((size_t)n), graph_s, graph_col0;
-    int64_t v0 = 0, a0 = 0;
-    int32_t ncols = 0, s_bits = 0, maxr = 0;
-    for (size_t k = 0; k < gr.members.size(); ++k) {
-      const auto &it = b->items[gr.members[k]];
-      for (int64_t v = 0; v < it.n; ++v) {
-        rp[(size_t)(v0 + v)] = a0 + it.row_ptr[(size_t)v];
-        node_graph[(size_t)(v0 + v)] = (int32_t)k;
+    // one union per class, or several where the class's graphs together pass
+    // the node or arc count one propagation can hold (kMaxNodes, kMaxArcs)
+    for (size_t k0 = 0; k0 < packed.size();) {
+      pg_batch::Group gr;
+      int64_t n = 0, m = 0;
+      int directed = 0;
+      for (; k0 < packed.size(); ++k0) {
+        const auto &it = b->items[packed[k0]];
+        if (!gr.members.empty() && (n + it.n > kMaxNodes || m + it.m > kMaxArcs)) break;
+        gr.members.push_back(packed[k0]);
+        n += it.n;
+        m += it.m;
+        directed |= it.directed;
       }
-      for (int64_t j = 0; j < it.m; ++j) col[(size_t)(a0 + j)] = (int32_t)(it.col[(size_t)j] + v0);
-      const int32_t s = (int32_t)it.seeds.size();
-      for (int32_t i = 0; i < s; ++i) {
-        gr.seeds.push_back((int32_t)(it.seeds[(size_t)i] + v0));
-        gr.seed_bit.push_back(i);
+      std::vector<int64_t> rp((size_t)n + 1);
+      std::vector<int32_t> col((size_t)std::max<int64_t>(m, 1));
+      std::vector<int32_t> node_graph((size_t)n), graph_s, graph_col0;
+      int64_t v0 = 0, a0 = 0;
+      int32_t ncols = 0, s_bits = 0, maxr = 0;
+      for (size_t k = 0; k < gr.members.size(); ++k) {
+        const auto &it = b->items[gr.members[k]];
+        for (int64_t v = 0; v < it.n; ++v) {
+          rp[(size_t)(v0 + v)] = a0 + it.row_ptr[(size_t)v];
+          node_graph[(size_t)(v0 + v)] = (int32_t)k;
+        }
+        for (int64_t j = 0; j < it.m; ++j) col[(size_t)(a0 + j)] = (int32_t)(it.col[(size_t)j] + v0);
+        const int32_t s = (int32_t)it.seeds.size();
+        for (int32_t i = 0; i < s; ++i) {
+          gr.seeds.push_back((int32_t)(it.seeds[(size_t)i] + v0));
+          gr.seed_bit.push_back(i);
+        }
+        graph_s.push_back(s);
+        graph_col0.push_back(ncols);
+        gr.graph_m.push_back(it.m);
+        ncols += s;
+        s_bits = std::max(s_bits, s);
+        maxr = std::max<int32_t>(maxr, (int32_t)std::min<int64_t>(it.n - 1, 0x3FFFFFFF));
+        v0 += it.n;
+        a0 += it.m;
       }
-      graph_s.push_back(s);
-      graph_col0.push_back(ncols);
-      gr.graph_m.push_back(it.m);
-      ncols += s;
-      s_bits = std::max(s_bits, s);
-      maxr = std::max<int32_t>(maxr, (int32_t)std::min<int64_t>(it.n - 1, 0x3FFFFFFF));
-      v0 += it.n;
-      a0 += it.m;
+      rp[(size_t)n] = a0;
+      // the union keeps its node order: each graph's nodes stay one block
+      pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, PG_KEEP_ORDER, st,
+                                       &gr.g);
+      if (rc) return rc;
+      rc = ensure(gr.node_graph, sizeof(int32_t) * (size_t)n);
+      if (!rc) {  // the packed graph knows its parts (sliced-ELL chunks per graph)
+        gr.g->seg_of = (const int32_t *)gr.node_graph.p;
+        gr.g->nseg = (int32_t)gr.members.size();
+      }
+      if (!rc) rc = ensure(gr.graph_s, sizeof(int32_t) * graph_s.size());
+      if (!rc) rc = ensure(gr.graph_col0, sizeof(int32_t) * graph_col0.size());
+      if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.node_graph.p, node_graph.data(),
+                                                sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+      if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_s.p, graph_s.data(),
+                                                sizeof(int32_t) * graph_s.size(), cudaMemcpyHostToDevice, st));
+      if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_col0.p, graph_col0.data(),
+                                                sizeof(int32_t) * graph_col0.size(),
+                                                cudaMemcpyHostToDevice, st));
+      if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+      gr.col0 = graph_col0;
+      gr.ncols = ncols;
+      gr.s_bits = s_bits;
+      gr.max_rounds = maxr;
+      b->groups.push_back(std::move(gr));
+      if (rc) return rc;
     }
-    rp[(size_t)n] = a0;
-    // the union keeps its node order: each graph's nodes stay one block
-    pg_status rc = pg_graph_from_csr(rp.data(), col.data(), n, m, directed, PG_KEEP_ORDER, st,
-                                     &gr.g);
-    if (rc) return rc;
-    rc = ensure(gr.node_graph, sizeof(int32_t) * (size_t)n);
-    if (!rc) {  // the packed graph knows its parts (sliced-ELL chunks per graph)
-      gr.g->seg_of = (const int32_t *)gr.node_graph.p;
-      gr.g->nseg = (int32_t)gr.members.size();
-    }
-    if (!rc) rc = ensure(gr.graph_s, sizeof(int32_t) * graph_s.size());
-    if (!rc) rc = ensure(gr.graph_col0, sizeof(int32_t) * graph_col0.size());
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.node_graph.p, node_graph.data(),
-                                              sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_s.p, graph_s.data(),
-                                              sizeof(int32_t) * graph_s.size(), cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(gr.graph_col0.p, graph_col0.data(),
-                                              sizeof(int32_t) * graph_col0.size(),
-                                              cudaMemcpyHostToDevice, st));
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
-    gr.col0 = graph_col0;
-    gr.ncols = ncols;
-    gr.s_bits = s_bits;
-    gr.max_rounds = maxr;
-    b->groups.push_back(std::move(gr));
-    if (rc) return rc;
   }
   b->built = true;
   return PG_OK;
@@ -278,7 +281,7 @@ pg_status pg_batch_add(pg_batch *b, const int64_t *row_ptr, const int32_t *col, 
                        int64_t m, int directed, const int32_t *seeds, int32_t s,
                        int32_t *index) {
   if (!b || !row_ptr || (m > 0 && !col) || !seeds || n < 1 || m < 0 || s < 1 || s > n ||
-      n >= 0x7FFFFFFFLL || row_ptr[0] != 0 || row_ptr[n] != m)
+      n > kMaxNodes || m > kMaxArcs || row_ptr[0] != 0 || row_ptr[n] != m)
     return PG_EINVAL;
   std::lock_guard<std::mutex> lk(b->mu);
   pg_batch::Item it;

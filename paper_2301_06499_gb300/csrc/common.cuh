@@ -19,6 +19,10 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 // two consistent, so every frontier row gets its out-arc prefix).
 constexpr int kFsumBits = 37;
 constexpr unsigned long long kFsumMask = (1ULL << kFsumBits) - 1ULL;
+// Size limits that follow: a round's frontier has at most n rows, counted in
+// the 64 - kFsumBits high bits, and its out-arc sum is at most m.
+constexpr int64_t kMaxNodes = (1LL << (64 - kFsumBits)) - 1;  // 134,217,727
+constexpr int64_t kMaxArcs = (1LL << kFsumBits) - 1;
 
 // kModeMixed (packed batches): each graph of the union picks its own kind
 // of round from its own frontier (see Params::gfsum).

@@ -241,6 +241,7 @@ extern "C" pg_status pg_graph_generate(const pg_generator *gen, unsigned flags, 
   } else {
     return PG_EINVAL;
   }
+  if (n > kMaxNodes || total > kMaxArcs) return PG_EINVAL;  // as pg_graph_from_csr
   int lg = 1;
   while ((1LL << lg) < n) ++lg;
   const int bits = 2 * lg;

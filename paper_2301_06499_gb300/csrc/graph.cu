@@ -904,7 +904,7 @@ pg_status make_replicas(pg_graph *g, int K, cudaStream_t st) {
   if (g->rep && g->rep_K == K) return PG_OK;
   drop_replicas(g);
   const int64_t n = g->n, m = g->m, Kn = (int64_t)K * n, Km = (int64_t)K * m;
-  if (K < 2 || Kn >= 0x7FFFFFFFLL || Km >= (1LL << kFsumBits)) return PG_EINVAL;
+  if (K < 2 || Kn > kMaxNodes || Km > kMaxArcs) return PG_EINVAL;
   pg_graph *r = new pg_graph();
   r->n = Kn;
   r->m = Km;
@@ -1058,8 +1058,7 @@ pg_status pg_graph_from_csr(const int64_t *row_ptr, const int32_t *col, int64_t 
                             int directed, unsigned flags, void *stream, pg_graph **out) {
   if (!out) return PG_EINVAL;
   *out = nullptr;
-  if (n < 1 || n >= 0x7FFFFFFFLL || m < 0 || m >= (1LL << kFsumBits) || !row_ptr ||
-      (m > 0 && !col))
+  if (n < 1 || n > kMaxNodes || m < 0 || m > kMaxArcs || !row_ptr || (m > 0 && !col))
     return PG_EINVAL;
   if ((flags & PG_BORROW) && !(flags & PG_DEVICE_PTRS)) return PG_EINVAL;
   if ((flags & PG_HOST_CSR) && (flags & PG_BORROW)) return PG_EINVAL;

@@ -1386,8 +1386,8 @@ static int passes_together(const pg_graph *g, int npasses, const pg_options &o) 
   const int64_t csr = (g->n + 1) * 8 + g->m * 4;
   // in/out CSR, sliced-ELL and piece lists, and a one-word workspace
   const int64_t per_copy = csr * (g->directed ? 2 : 1) + g->m * 5 + g->n * 64;
-  while (K > 1 && ((int64_t)K * per_copy > (int64_t)(fr / 4) || (int64_t)K * g->n >= 0x7FFFFFFFLL ||
-                   (int64_t)K * g->m >= (1LL << kFsumBits)))
+  while (K > 1 && ((int64_t)K * per_copy > (int64_t)(fr / 4) || (int64_t)K * g->n > kMaxNodes ||
+                   (int64_t)K * g->m > kMaxArcs))
     --K;
   return K;
 }

@@ -135,6 +135,14 @@ def test_argument_checks_before_any_device_work():
                                ctypes.byref(out)) == _abi.PG_EINVAL
     assert L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, 2, -1, 1, 0, None,
                                ctypes.byref(out)) == _abi.PG_EINVAL
+    # past the largest graph whose rounds one 64-bit counter holds (changed
+    # rows in 27 bits, their out-arcs in 37): refused before the arrays are read
+    for n, m in ((1 << 27, 2), (2, 1 << 37)):
+        assert L.pg_graph_from_csr(rp.ctypes.data, col.ctypes.data, n, m, 1, 0, None,
+                                   ctypes.byref(out)) == _abi.PG_EINVAL
+    gen = _abi.Generator(kind=1, directed=0, seed=1, scale=27, edge_factor=1.0,
+                         a=0.57, b=0.19, c=0.19)
+    assert L.pg_graph_generate(ctypes.byref(gen), 0, None, ctypes.byref(out)) == _abi.PG_EINVAL
     c = _abi.Counts(s=1, max_rounds=0, rounds=0, reserved=0, counts=None, m_active=None)
     assert L.pg_propagate_p(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
     assert L.pg_propagate_s(None, None, 1, ctypes.byref(c), None, None) == _abi.PG_EINVAL
@@ -145,6 +153,9 @@ def test_argument_checks_before_any_device_work():
         assert L.pg_batch_set_streams(bh, bad) == _abi.PG_EINVAL
     assert L.pg_batch_set_streams(bh, 1) == _abi.PG_OK
     assert L.pg_batch_set_streams(None, 4) == _abi.PG_EINVAL
+    sd = np.array([0], np.int32)
+    assert L.pg_batch_add(bh, rp.ctypes.data, col.ctypes.data, 1 << 27, 2, 1, sd.ctypes.data, 1,
+                          None) == _abi.PG_EINVAL
     L.pg_batch_free(bh)
     assert L.pg_server_create(None, None) == _abi.PG_EINVAL
     assert L.pg_autotune(None, None, 1, 0, 1, None, None, None) == _abi.PG_EINVAL
