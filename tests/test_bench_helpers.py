@@ -59,3 +59,26 @@ def test_round_bytes_follow_the_per_round_formula():
     assert bench.round_bytes(st, 512, False) == 10 * (8 + 128) + 100 * (4 + 64) + 7 * 4
     assert bench.round_bytes(st, 512, True) == 10 * (8 + 16) + 100 * (4 + 8) + 7 * 4
     assert bench.round_bytes(st, 32, True) == 10 * (8 + 8) + 100 * (4 + 4) + 7 * 4
+
+
+def test_load_traffic_keeps_only_figures_of_the_current_sources(tmp_path):
+    """A stored DRAM figure counts as this build's traffic only while the
+    kernel's sources hash as they did at the capture; otherwise it is kept
+    apart as an earlier build's, with both hashes."""
+    cur = bench.kernel_hash("k_pull<8, 16, 0>")
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps({
+        "workload": "w",
+        "kernel_hash": {"k_pull<8, 16, 0>": cur, "k_pull<8, 16, 1>": "0123456789ab"},
+        "bytes_per_launch": {"k_pull<8, 16, 0>": 4.0e10, "k_pull<8, 16, 1>": 4.2e10}}))
+    table, earlier = bench.load_traffic("w", str(path))
+    assert table == {"k_pull<8, 16, 0>": 4.0e10}
+    assert earlier == {"k_pull<8, 16, 1>": {"bytes_per_launch": 4.2e10,
+                                            "sources_hash": "0123456789ab",
+                                            "current_sources_hash":
+                                                bench.kernel_hash("k_pull<8, 16, 1>")}}
+    assert bench.load_traffic("other", str(path)) == ({}, {})
+    assert bench.load_traffic("w", str(tmp_path / "missing.json")) == ({}, {})
+    # the committed table: each figure lands on exactly one side
+    t2, e2 = bench.load_traffic("rmat26_undirected_s512")
+    assert set(t2) | set(e2) and not set(t2) & set(e2)
