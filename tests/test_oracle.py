@@ -124,6 +124,30 @@ def test_directed_path_connectivity_half(n):
     assert m["avg_distance"] == pytest.approx((n + 1) / 3, rel=1e-13)
 
 
+@pytest.mark.parametrize("n", [2, 3, 8, 25])
+def test_directed_star_closed_form(n):
+    """Arcs from a centre to n-1 leaves (and the same arcs reversed), every
+    node a seed: the centre's ball holds every leaf at distance 1 (out-star)
+    or no other node (in-star), a leaf's ball the reverse. Either way
+    R = [n, 2n-1]: diameter 1, mean distance 1, alpha = (n-1)/(n(n-1)) = 1/n,
+    reachable pairs 2n-1, and the interpolated 90% effective diameter
+    (0.9(2n-1) - n)/(n-1)."""
+    leaves = np.arange(1, n, dtype=np.int32)
+    centre = np.zeros(n - 1, dtype=np.int32)
+    for src, dst, centre_row in ((centre, leaves, [1, n - 1]), (leaves, centre, [1, 0])):
+        hist, m = _exact(I.from_arcs(n, src, dst))
+        assert list(hist[0]) == centre_row
+        assert all(list(hist[v]) == [1, 1 - centre_row[1] // (n - 1)] for v in range(1, n))
+        assert m["diameter"] == 1 and m["eff_diameter"] == 1
+        assert m["R_last"] == 2 * n - 1
+        assert m["avg_distance"] == 1.0
+        assert m["avg_distance_incl_self"] == pytest.approx((n - 1) / (2 * n - 1), rel=1e-15)
+        assert m["connectivity_rate"] == pytest.approx(1.0 / n, rel=1e-15)
+        assert m["reachable_pairs"] == 2 * n - 1
+        assert m["eff_diameter_interp"] == pytest.approx((0.9 * (2 * n - 1) - n) / (n - 1),
+                                                         rel=1e-13)
+
+
 def test_isolated_nodes():
     g = I.from_arcs(5, np.array([], np.int32), np.array([], np.int32))
     hist, m = _exact(g)
