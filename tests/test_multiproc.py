@@ -79,3 +79,55 @@ def test_gloo_two_ranks_gather_equals_whole(tmp_path, s):
         mx, sm = np.load(tmp_path / f"red{r}.npy")
         assert mx == 2.0 and sm == 3.0
 
+
+
+def _failing_worker(rank, world, port, out_dir):
+    """Rank 1 fails between its propagation and the final gather (an
+    exception on the host, no device work in flight); rank 0 must learn of
+    it from the gather, as an error within the process group's timeout, not
+    hang in it."""
+    import datetime
+    import time
+
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2301_06499_gb300 import inputs as I
+    from paper_2301_06499_gb300.shard import gather_counts
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    g = I.rmat(9, 8, 63, directed=True)
+    lo, hi = seed_shard(128, rank, world)
+    res = oracle.run(g, I.seeds(g.n, 128, 64)[lo:hi])
+    if rank == 1:
+        raise RuntimeError("rank 1 fails before the gather")
+    t0 = time.monotonic()
+    try:
+        gather_counts(res["counts"], world)
+        outcome = "no error"
+    except Exception as e:  # the backend's error type varies by version
+        outcome = "error: " + type(e).__name__
+    with open(os.path.join(out_dir, "rank0.txt"), "w") as f:
+        f.write(f"{outcome}\n{time.monotonic() - t0:.3f}\n")
+
+
+def test_gloo_peer_failure_surfaces_as_an_error(tmp_path):
+    world = 2
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, world, port, str(tmp_path)))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        if p.is_alive():  # never expected: stop it and fail the test
+            p.kill()
+            p.join()
+            pytest.fail("a rank hung after its peer failed")
+    assert procs[1].exitcode != 0
+    outcome, secs = (tmp_path / "rank0.txt").read_text().split("\n")[:2]
+    assert outcome.startswith("error"), outcome
+    assert float(secs) < 60.0
